@@ -1,0 +1,213 @@
+/*
+ * hodlr.h - C ABI of libhodlr, a GPU direct solver for HODLR matrices
+ * (hierarchically off-diagonal low-rank; Chen & Martinsson, arXiv 2208.06290).
+ *
+ * The operator (Sec. 2, Def. 1-2, Eq. e:rank, Sec. 3.2 Eq. e:u)
+ * ----------------------------------------------------------------
+ * A is N x N with N = m * 2^L. The cluster tree is uniform: level c has 2^c
+ * nodes, node i of level c owns rows [i*N/2^c, (i+1)*N/2^c). Leaves (level L)
+ * own m rows. A is given by three device arrays, all FP64, all column-major:
+ *   D  2^L consecutive m x m blocks, block b (rows b*m..b*m+m-1) at D + b*m*m,
+ *      element (i, j) of a block at offset j*m + i      (the leaf blocks D_b);
+ *   U  N x (r*L), leading dimension ldu >= N             (U_big of Eq. e:u);
+ *   V  N x (r*L), leading dimension ldv >= N             (V_big).
+ * Column block j (columns j*r .. j*r+r-1) of U and V holds the bases of the
+ * level-(j+1) nodes on their own rows. For siblings alpha (left) and beta
+ * (right) at level c: A(I_alpha, I_beta) = U_alpha V_beta^T and
+ * A(I_beta, I_alpha) = U_beta V_alpha^T (Eq. e:rank). Only real FP64 input
+ * is accepted; every rank is the same r (1 <= r <= 64, r <= m), m <= 256.
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - All matrix pointers are DEVICE pointers. Right-hand sides B / X / Y are
+ *   N x k column-major with a leading dimension >= N.
+ * - The library allocates no device memory. Calls that need scratch take a
+ *   caller-owned device workspace; its size comes from the matching
+ *   *_workspace_size query and it must be 256-byte aligned. A workspace may be
+ *   reused once the stream work that used it has finished.
+ * - Work is enqueued on the given stream (NULL = legacy default stream) and
+ *   returns without waiting, except where a function says it synchronizes.
+ * - Errors found on the host (bad sizes, null or misaligned pointers, a small
+ *   workspace) are returned before anything is enqueued. Errors found on the
+ *   device (a zero pivot, a non-finite input) are recorded in the factor and
+ *   returned by hodlr_factor_status / hodlr_logdet / the refined solvers; the
+ *   computation still runs to completion (LAPACK getrf "info" convention), and
+ *   no kernel traps.
+ */
+#ifndef HODLR_H
+#define HODLR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HODLR_API __attribute__((visibility("default")))
+#else
+#define HODLR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* hodlr_stream_t;
+
+typedef enum {
+  HODLR_OK = 0,
+  HODLR_ERR_ARG = 1,               /* bad size, pointer, alignment or precision */
+  HODLR_ERR_WORKSPACE = 2,         /* workspace too small or not 256-byte aligned */
+  HODLR_ERR_CUDA = 3,              /* a CUDA runtime call failed */
+  HODLR_ERR_SINGULAR_LEAF = 4,     /* exact zero pivot in a leaf LU (where = leaf, detail = column) */
+  HODLR_ERR_SINGULAR_COUPLING = 5, /* exact zero pivot in a 2r x 2r coupling LU (where = heap node, detail = column) */
+  HODLR_ERR_NONFINITE = 6,         /* NaN or Inf in D (where = leaf) */
+  HODLR_ERR_NOT_CONVERGED = 7      /* refinement / GMRES hit its iteration limit */
+} hodlr_status;
+
+/* Arithmetic of the factorization (not of the input, which is always FP64).
+ *   FP64: everything in FP64.
+ *   FP32: leaf LU, leaf solves and panel products in FP32 (FP32 accumulate).
+ *   BF16: as FP32, but Y_big and V_big are stored in bfloat16 and the panel
+ *         products read them as such (FP32 accumulate).
+ * In every precision the 2r x 2r coupling matrices are formed, factored and
+ * solved in FP64, and log-determinants are accumulated in FP64. A low-precision
+ * factor is meant as the preconditioner of hodlr_solve_refined / hodlr_gmres. */
+typedef enum {
+  HODLR_PREC_FP64 = 0,
+  HODLR_PREC_FP32 = 1,
+  HODLR_PREC_BF16 = 3
+} hodlr_prec;
+
+typedef struct {
+  int64_t N;    /* matrix order, N = m << L */
+  int32_t L;    /* number of levels below the root, 1 <= L <= 24 */
+  int32_t m;    /* leaf size, 1 <= m <= 256 */
+  int32_t r;    /* off-diagonal rank, 1 <= r <= min(m, 64) */
+  int32_t reserved;  /* must be 0 */
+  int64_t ldu;  /* leading dimension of U, >= N */
+  int64_t ldv;  /* leading dimension of V, >= N */
+} hodlr_desc;
+
+typedef struct hodlr_factor_s* hodlr_factor_t;
+
+/* Human-readable name of a status code (static string). */
+HODLR_API const char* hodlr_strerror(hodlr_status s);
+
+/* ---------------------------------------------------------------- factor --
+ * Factorization stage of the level-by-level algorithm (Alg. 1; GPU form
+ * Alg. 3): LU with partial pivoting of every leaf block; Y_big = D^{-1} U_big
+ * leaf by leaf; then for child levels c = L..1: projections V^T Y of every
+ * child on its own and ancestor columns, the 2r x 2r coupling matrix
+ * K~ = [[I, V_beta^T Y_beta], [V_alpha^T Y_alpha, I]] of every parent (the
+ * identity-diagonal variant given after Alg. 4) factored by LU with partial
+ * pivoting, its solve with the ancestor projections as right-hand side
+ * (Eq. e:node1), and the ancestor update Y(:, 1:r(c-1)) -= Y_own W (Eq. e:node2).
+ *
+ * hodlr_factor_workspace_size: bytes of device workspace hodlr_factor needs.
+ * hodlr_factor: enqueues the factorization. D, U, V are read only and are not
+ *   referenced after the call returns, except that in FP64 the factor keeps
+ *   using V: the caller must keep V unchanged while the factor is in use. The
+ *   workspace holds the factor and must stay allocated until hodlr_free.
+ *   *out receives a host handle (owned by the caller, release with hodlr_free).
+ */
+HODLR_API hodlr_status hodlr_factor_workspace_size(const hodlr_desc* desc, hodlr_prec prec, size_t* bytes);
+HODLR_API hodlr_status hodlr_factor(const hodlr_desc* desc, const double* D, const double* U, const double* V,
+                          hodlr_prec prec, void* workspace, size_t workspace_bytes,
+                          hodlr_stream_t stream, hodlr_factor_t* out);
+
+/* Synchronizes the factor's stream and returns the first device-side error
+ * (HODLR_OK if none). where / detail (may be NULL) locate it: leaf index and
+ * column for a leaf, heap node number (root = 1) and column for a coupling. */
+HODLR_API hodlr_status hodlr_factor_status(hodlr_factor_t f, int64_t* where, int64_t* detail);
+
+/* Releases the host handle (not the caller's workspace). */
+HODLR_API void hodlr_free(hodlr_factor_t f);
+
+/* ----------------------------------------------------------------- solve --
+ * hodlr_solve: B <- A^{-1} B in place for k columns (Alg. 2; GPU form Alg. 4):
+ *   leaf solves with the stored LUs, then for child levels c = L..1 the
+ *   projections V^T x, the stored coupling LU solve (Eq. e:node3) and the
+ *   update x -= Y w (Eq. e:node4). In a low-precision factor the right-hand
+ *   side is rounded to FP32 on entry and the result widened to FP64 on exit.
+ * hodlr_solve_adjoint: B <- A^{-T} B in place. Uses the same factor read as
+ *   A = F_0 F_L ... F_1 (Sec. 3.5, F_0 = blockdiag(D_b), F_c the 2x2-block
+ *   factors of level c), so A^{-T} = F_0^{-T} F_L^{-T} ... F_1^{-T}: for
+ *   c = 1..L (top-down) s = [Y_alpha^T x_alpha; Y_beta^T x_beta],
+ *   K~^T t = s, x_alpha -= V_alpha t_2, x_beta -= V_beta t_1; then the leaf
+ *   solves with D_b^T.
+ * Workspace: hodlr_solve_workspace_size(f, k) bytes (same for both).
+ */
+HODLR_API hodlr_status hodlr_solve_workspace_size(hodlr_factor_t f, int32_t k, size_t* bytes);
+HODLR_API hodlr_status hodlr_solve(hodlr_factor_t f, double* B, int64_t ldb, int32_t k,
+                         void* workspace, size_t workspace_bytes, hodlr_stream_t stream);
+HODLR_API hodlr_status hodlr_solve_adjoint(hodlr_factor_t f, double* B, int64_t ldb, int32_t k,
+                                 void* workspace, size_t workspace_bytes, hodlr_stream_t stream);
+
+/* ---------------------------------------------------------------- logdet --
+ * (sign, log|det A|) from the factorization (Sec. 3.5): sum over leaves of
+ * log|u_ii| of the leaf LUs plus, by Sylvester's determinant theorem, the
+ * log|det K~| of every coupling matrix; sign = product of the signs with the
+ * pivot-swap parities. Accumulated in FP64 in a fixed order (deterministic).
+ * Synchronizes the stream. Returns the factor's device status (a singular
+ * factor gives log|det| = -inf). */
+HODLR_API hodlr_status hodlr_logdet(hodlr_factor_t f, hodlr_stream_t stream, double* sign, double* logabsdet);
+
+/* ---------------------------------------------------------------- matvec --
+ * Y = A X in FP64 from the unfactored (D, U, V), straight from the block
+ * definition (Eq. e:rank): leaf products D_b X_b, then for every pair of
+ * siblings U_alpha (V_beta^T X_beta) and U_beta (V_alpha^T X_alpha). X and Y
+ * must not overlap. This is the residual operator of relres = |b - Ax| / |b|
+ * (Sec. 4, Table t:notation2). */
+HODLR_API hodlr_status hodlr_matvec_workspace_size(const hodlr_desc* desc, int32_t k, size_t* bytes);
+HODLR_API hodlr_status hodlr_matvec(const hodlr_desc* desc, const double* D, const double* U, const double* V,
+                          const double* X, int64_t ldx, double* Y, int64_t ldy, int32_t k,
+                          void* workspace, size_t workspace_bytes, hodlr_stream_t stream);
+
+/* ------------------------------------------------------- refined solvers --
+ * Mixed-precision solves recovered to FP64 accuracy. The factor f (any
+ * precision) of the HODLR matrix (desc, D, U, V) is the preconditioner; the
+ * residual uses the FP64 hodlr_matvec on the unfactored D, U, V.
+ *
+ * hodlr_solve_refined: iterative refinement, X <- X + f^{-1}(B - A X),
+ *   starting from X = f^{-1} B, until max_j |b_j - A x_j| / |b_j| <= tol or
+ *   max_iter corrections. Stops early when the residual grows twice in a row.
+ * hodlr_gmres: flexible GMRES (restart length `restart`, at most max_iter
+ *   inner iterations in total, per column) right-preconditioned by f, started
+ *   from X = f^{-1} B, stopping on the true FP64 residual <= tol.
+ * Both write the solution to X (N x k, ldx), leave B unchanged, return
+ * HODLR_ERR_NOT_CONVERGED if tol was not reached, report the iteration count
+ * (refinement corrections or total GMRES inner iterations) in *iters and the
+ * final max relative residual in *relres. They synchronize the stream once per
+ * iteration to read residual norms.
+ */
+HODLR_API hodlr_status hodlr_refine_workspace_size(hodlr_factor_t f, int32_t k, int32_t restart, size_t* bytes);
+HODLR_API hodlr_status hodlr_solve_refined(hodlr_factor_t f, const double* D, const double* U, const double* V,
+                                 const double* B, int64_t ldb, double* X, int64_t ldx, int32_t k,
+                                 double tol, int32_t max_iter, void* workspace, size_t workspace_bytes,
+                                 hodlr_stream_t stream, int32_t* iters, double* relres);
+HODLR_API hodlr_status hodlr_gmres(hodlr_factor_t f, const double* D, const double* U, const double* V,
+                         const double* B, int64_t ldb, double* X, int64_t ldx, int32_t k,
+                         double tol, int32_t restart, int32_t max_iter,
+                         void* workspace, size_t workspace_bytes, hodlr_stream_t stream,
+                         int32_t* iters, double* relres);
+
+/* ------------------------------------------------------------ diagnostics --
+ * Accounting of the library's own kernel launches, for benchmarks; not part
+ * of the method. hodlr_launch_count: kernels enqueued by this library since
+ * it was loaded (all threads). hodlr_profile_enable(1): from then on every
+ * launch is bracketed by CUDA events recorded on the launching stream, and
+ * hodlr_profile_read synchronizes the device, folds the elapsed times into
+ * per-kernel-class totals, copies up to n of them (milliseconds and launch
+ * counts, in class order) and returns the number of classes;
+ * hodlr_profile_name gives a class's name, hodlr_profile_reset clears the
+ * totals. Profiling is process-wide and not thread-safe; it is off by default. */
+HODLR_API int64_t hodlr_launch_count(void);
+HODLR_API void hodlr_profile_enable(int32_t on);
+HODLR_API void hodlr_profile_reset(void);
+HODLR_API int32_t hodlr_profile_read(double* ms, int64_t* launches, int32_t n);
+HODLR_API const char* hodlr_profile_name(int32_t cls);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HODLR_H */

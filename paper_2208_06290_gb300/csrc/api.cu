@@ -1,0 +1,641 @@
+// C ABI of libhodlr: argument checks, workspace layout and the host-side
+// sequencing of the level-by-level factorization (Alg. 1 / Alg. 3) and solves
+// (Alg. 2 / Alg. 4), the FP64 matvec and the refined solvers.
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "hodlr_internal.cuh"
+
+namespace hodlr {
+
+cudaError_t launch_coupling_factor_apply(const Factor& F, int c, cudaStream_t s);
+
+// ---------------------------------------------------------------- launch accounting
+namespace {
+std::atomic<long long> g_launches{0};
+std::atomic<bool> g_prof{false};
+thread_local int t_bracket = 0;
+struct PendingBracket {
+  int cls;
+  cudaEvent_t a, b;
+  int n;
+};
+std::mutex g_mu;
+std::vector<PendingBracket> g_pending;
+std::vector<cudaEvent_t> g_pool;
+double g_ms[KC_COUNT];
+long long g_n[KC_COUNT];
+const char* kClassName[KC_COUNT] = {"leaf_lu", "leaf_solve", "project", "coupling", "coupling_apply",
+                                    "update", "reduce_chunks", "leaf_matvec", "vector", "logdet"};
+
+cudaEvent_t pool_get() {
+  std::lock_guard<std::mutex> g(g_mu);
+  if (!g_pool.empty()) {
+    cudaEvent_t e = g_pool.back();
+    g_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+}  // namespace
+
+void note_launches(int n) {
+  g_launches += n;
+  t_bracket += n;
+}
+
+ProfScope::ProfScope(int c, cudaStream_t st) : cls(c), s(st), a(nullptr) {
+  if (!g_prof.load(std::memory_order_relaxed)) return;
+  t_bracket = 0;
+  cudaEvent_t e = pool_get();
+  if (e && cudaEventRecord(e, s) == cudaSuccess) a = e;
+}
+
+ProfScope::~ProfScope() {
+  if (!a) return;
+  cudaEvent_t e0 = static_cast<cudaEvent_t>(a);
+  if (t_bracket == 0) {
+    std::lock_guard<std::mutex> g(g_mu);
+    g_pool.push_back(e0);
+    return;
+  }
+  cudaEvent_t e1 = pool_get();
+  if (!e1 || cudaEventRecord(e1, s) != cudaSuccess) return;
+  std::lock_guard<std::mutex> g(g_mu);
+  g_pending.push_back({cls, e0, e1, t_bracket});
+}
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+  size_t status, ld_out, leaf_ld, node_ld, lu, perm, Y, Vp, K, P, total;
+};
+
+size_t panel_elem_bytes(hodlr_prec p) {
+  switch (p) {
+    case HODLR_PREC_FP64: return 8;
+    case HODLR_PREC_FP32: return 4;
+    default: return 2;
+  }
+}
+
+size_t max_partial_elems(const hodlr_desc& d, int ncols_per_level_factor, int k) {
+  // factor: slot r x (r c) at level c; solve/matvec: slot r x k
+  size_t best = 0;
+  for (int c = 1; c <= d.L; ++c) {
+    const size_t cols = ncols_per_level_factor ? (size_t)d.r * c : (size_t)k;
+    const size_t e = (size_t)num_chunks(d.N, c) * d.r * cols;
+    if (e > best) best = e;
+  }
+  return best;
+}
+
+Layout factor_layout(const hodlr_desc& d, hodlr_prec prec) {
+  Layout l{};
+  const size_t nleaf = (size_t)1 << d.L;
+  const size_t N = (size_t)d.N;
+  const size_t rL = (size_t)d.r * d.L;
+  const size_t tl = prec == HODLR_PREC_FP64 ? 8 : 4;
+  const size_t tp = panel_elem_bytes(prec);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes); return o; };
+  l.status = take(sizeof(DevStatus));
+  l.ld_out = take(2 * sizeof(double));
+  l.leaf_ld = take(nleaf * 2 * sizeof(double));
+  l.node_ld = take((nleaf - 1) * 2 * sizeof(double) + 16);
+  l.lu = take(nleaf * d.m * d.m * tl);
+  l.perm = take(N * sizeof(int));
+  l.Y = take(N * rL * tp);
+  l.Vp = prec == HODLR_PREC_FP64 ? 0 : take(N * rL * tp);
+  l.K = take((nleaf - 1) * 4 * (size_t)d.r * d.r * sizeof(double) + 16);
+  l.P = take(max_partial_elems(d, 1, 0) * sizeof(double));
+  l.total = off;
+  return l;
+}
+
+hodlr_status check_desc(const hodlr_desc* d) {
+  if (!d) return HODLR_ERR_ARG;
+  if (d->L < 1 || d->L > 24 || d->m < 1 || d->m > 256 || d->r < 1 || d->r > 64 || d->r > d->m) return HODLR_ERR_ARG;
+  if (d->reserved != 0) return HODLR_ERR_ARG;
+  if (d->N != ((int64_t)d->m << d->L)) return HODLR_ERR_ARG;
+  if (d->ldu < d->N || d->ldv < d->N) return HODLR_ERR_ARG;
+  return HODLR_OK;
+}
+
+bool prec_ok(hodlr_prec p) {
+  return p == HODLR_PREC_FP64 || p == HODLR_PREC_FP32 || p == HODLR_PREC_BF16;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+#define HODLR_CUDA(...)                            \
+  do {                                             \
+    cudaError_t e_ = (__VA_ARGS__);                \
+    if (e_ != cudaSuccess) return HODLR_ERR_CUDA;  \
+  } while (0)
+
+template <typename TP>
+hodlr_status factor_levels(Factor& F, cudaStream_t s) {
+  const hodlr_desc& d = F.d;
+  TP* Y = static_cast<TP*>(F.Y);
+  const TP* Vp = static_cast<const TP*>(F.Vp);
+  for (int c = d.L; c >= 1; --c) {
+    const int rc = d.r * c;
+    const int anc = d.r * (c - 1);
+    HODLR_CUDA(launch_project<TP, TP>(d.N, d.r, c, Vp, F.ldvp, c - 1, Y, d.N, rc, F.P, 0, s));
+    HODLR_CUDA(launch_coupling_factor(F, c, s));
+    if (anc > 0) {
+      HODLR_CUDA(launch_coupling_factor_apply(F, c, s));
+      const int64_t wstride = chunks_per_node(d.N, c) * (int64_t)d.r * rc;
+      HODLR_CUDA(launch_update<TP, TP>(d.N, d.r, c, Y, d.N, c - 1, Y, d.N, anc, F.P, wstride, 0, -1.0, 0, s));
+    }
+  }
+  return HODLR_OK;
+}
+
+size_t solve_partials_bytes(const hodlr_desc& d, int k) {
+  return align_up(max_partial_elems(d, 0, k) * sizeof(double));
+}
+
+// In-place solve on x (N x k, ld ldx) in type TX with the factor's panels TP.
+template <typename TP, typename TX>
+hodlr_status solve_core(const Factor& F, TX* x, int64_t ldx, int k, double* Ps, int trans, cudaStream_t s) {
+  const hodlr_desc& d = F.d;
+  const TP* Y = static_cast<const TP*>(F.Y);
+  const TP* Vp = static_cast<const TP*>(F.Vp);
+  if (!trans) {
+    HODLR_CUDA((launch_leaf_solve<TX, TX>(F, x, ldx, x, ldx, k, 0, s)));
+    for (int c = d.L; c >= 1; --c) {
+      HODLR_CUDA((launch_project<TP, TX>(d.N, d.r, c, Vp, F.ldvp, c - 1, x, ldx, k, Ps, 0, s)));
+      HODLR_CUDA(launch_coupling_solve(F, c, Ps, k, 0, s));
+      const int64_t wstride = chunks_per_node(d.N, c) * (int64_t)d.r * k;
+      HODLR_CUDA((launch_update<TP, TX>(d.N, d.r, c, Y, d.N, c - 1, x, ldx, k, Ps, wstride, 0, -1.0, 0, s)));
+    }
+  } else {
+    for (int c = 1; c <= d.L; ++c) {
+      HODLR_CUDA((launch_project<TP, TX>(d.N, d.r, c, Y, d.N, c - 1, x, ldx, k, Ps, 0, s)));
+      HODLR_CUDA(launch_coupling_solve(F, c, Ps, k, 1, s));
+      const int64_t wstride = chunks_per_node(d.N, c) * (int64_t)d.r * k;
+      HODLR_CUDA((launch_update<TP, TX>(d.N, d.r, c, Vp, F.ldvp, c - 1, x, ldx, k, Ps, wstride, 1, -1.0, 0, s)));
+    }
+    HODLR_CUDA((launch_leaf_solve<TX, TX>(F, x, ldx, x, ldx, k, 1, s)));
+  }
+  return HODLR_OK;
+}
+
+hodlr_status solve_any(const Factor& F, double* B, int64_t ldb, int k, void* work, int trans, cudaStream_t s) {
+  const hodlr_desc& d = F.d;
+  double* Ps = static_cast<double*>(work);
+  if (F.prec == HODLR_PREC_FP64) return solve_core<double, double>(F, B, ldb, k, Ps, trans, s);
+  float* xw = reinterpret_cast<float*>(static_cast<char*>(work) + solve_partials_bytes(d, k));
+  HODLR_CUDA((launch_copy_cols<float, double>(d.N, k, B, ldb, xw, d.N, s)));
+  hodlr_status st = F.prec == HODLR_PREC_FP32
+                        ? solve_core<float, float>(F, xw, d.N, k, Ps, trans, s)
+                        : solve_core<__nv_bfloat16, float>(F, xw, d.N, k, Ps, trans, s);
+  if (st != HODLR_OK) return st;
+  HODLR_CUDA((launch_copy_cols<double, float>(d.N, k, xw, d.N, B, ldb, s)));
+  return HODLR_OK;
+}
+
+size_t solve_ws_bytes(const Factor& F, int k) {
+  size_t b = solve_partials_bytes(F.d, k);
+  if (F.prec != HODLR_PREC_FP64) b += align_up((size_t)F.d.N * k * sizeof(float));
+  return b;
+}
+
+size_t matvec_ws_bytes(const hodlr_desc& d, int k) { return solve_partials_bytes(d, k); }
+
+hodlr_status matvec_core(const hodlr_desc& d, const double* D, const double* U, const double* V, const double* X,
+                         int64_t ldx, double* Y, int64_t ldy, int k, void* work, cudaStream_t s) {
+  double* Ps = static_cast<double*>(work);
+  HODLR_CUDA(launch_leaf_matvec(d, D, X, ldx, Y, ldy, k, s));
+  for (int c = 1; c <= d.L; ++c) {
+    HODLR_CUDA((launch_project<double, double>(d.N, d.r, c, V, d.ldv, c - 1, X, ldx, k, Ps, 1, s)));
+    HODLR_CUDA(launch_reduce_chunks(d.N, d.r, c, Ps, k, s));
+    const int64_t wstride = chunks_per_node(d.N, c) * (int64_t)d.r * k;
+    HODLR_CUDA((launch_update<double, double>(d.N, d.r, c, U, d.ldu, c - 1, Y, ldy, k, Ps, wstride, 1, 1.0, 1, s)));
+  }
+  return HODLR_OK;
+}
+
+bool valid_factor(const Factor* F) { return F != nullptr; }
+
+}  // namespace
+
+size_t factor_workspace_bytes(const hodlr_desc& d, hodlr_prec prec) { return factor_layout(d, prec).total; }
+
+}  // namespace hodlr
+
+using namespace hodlr;
+
+struct hodlr_factor_s : public hodlr::Factor {};
+
+extern "C" {
+
+const char* hodlr_strerror(hodlr_status s) {
+  switch (s) {
+    case HODLR_OK: return "ok";
+    case HODLR_ERR_ARG: return "invalid argument";
+    case HODLR_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case HODLR_ERR_CUDA: return "CUDA runtime error";
+    case HODLR_ERR_SINGULAR_LEAF: return "singular leaf block";
+    case HODLR_ERR_SINGULAR_COUPLING: return "singular coupling matrix";
+    case HODLR_ERR_NONFINITE: return "non-finite input";
+    case HODLR_ERR_NOT_CONVERGED: return "iteration did not converge";
+  }
+  return "unknown status";
+}
+
+hodlr_status hodlr_factor_workspace_size(const hodlr_desc* desc, hodlr_prec prec, size_t* bytes) {
+  hodlr_status st = check_desc(desc);
+  if (st != HODLR_OK) return st;
+  if (!prec_ok(prec) || !bytes) return HODLR_ERR_ARG;
+  *bytes = factor_layout(*desc, prec).total;
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_factor(const hodlr_desc* desc, const double* D, const double* U, const double* V,
+                          hodlr_prec prec, void* workspace, size_t workspace_bytes, hodlr_stream_t stream,
+                          hodlr_factor_t* out) {
+  hodlr_status st = check_desc(desc);
+  if (st != HODLR_OK) return st;
+  if (!prec_ok(prec) || !D || !U || !V || !out) return HODLR_ERR_ARG;
+  if (!aligned(D, 8) || !aligned(U, 8) || !aligned(V, 8)) return HODLR_ERR_ARG;
+  const Layout lay = factor_layout(*desc, prec);
+  if (!workspace || !aligned(workspace, kAlign) || workspace_bytes < lay.total) return HODLR_ERR_WORKSPACE;
+  hodlr_factor_s* F = new (std::nothrow) hodlr_factor_s();
+  if (!F) return HODLR_ERR_ARG;
+  char* w = static_cast<char*>(workspace);
+  const hodlr_desc& d = *desc;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  F->d = d;
+  F->prec = prec;
+  F->stream = s;
+  F->status = reinterpret_cast<DevStatus*>(w + lay.status);
+  F->ld_out = reinterpret_cast<double*>(w + lay.ld_out);
+  F->leaf_ld = reinterpret_cast<double*>(w + lay.leaf_ld);
+  F->node_ld = reinterpret_cast<double*>(w + lay.node_ld);
+  F->lu = w + lay.lu;
+  F->perm = reinterpret_cast<int*>(w + lay.perm);
+  F->Y = w + lay.Y;
+  F->K = reinterpret_cast<double*>(w + lay.K);
+  F->P = reinterpret_cast<double*>(w + lay.P);
+  F->P_elems = max_partial_elems(d, 1, 0);
+  for (int c = 0; c < 26; ++c) F->Koff[c] = 0;
+  for (int c = 1; c <= d.L; ++c) F->Koff[c] = ((int64_t)1 << (c - 1)) - 1;
+  if (prec == HODLR_PREC_FP64) {
+    F->Vp = V;
+    F->ldvp = d.ldv;
+  } else {
+    F->Vp = w + lay.Vp;
+    F->ldvp = d.N;
+  }
+  auto fail = [&](hodlr_status e) { delete F; return e; };
+  if (cudaMemsetAsync(F->status, 0, sizeof(DevStatus), s) != cudaSuccess) return fail(HODLR_ERR_CUDA);
+  if (launch_leaf_lu(*F, D, s) != cudaSuccess) return fail(HODLR_ERR_CUDA);
+  const int rL = d.r * d.L;
+  hodlr_status r = HODLR_OK;
+  if (prec == HODLR_PREC_FP64) {
+    if (launch_leaf_solve<double, double>(*F, U, d.ldu, static_cast<double*>(F->Y), d.N, rL, 0, s) != cudaSuccess)
+      return fail(HODLR_ERR_CUDA);
+    r = factor_levels<double>(*F, s);
+  } else if (prec == HODLR_PREC_FP32) {
+    if (launch_copy_cols<float, double>(d.N, rL, V, d.ldv, static_cast<float*>(const_cast<void*>(F->Vp)), d.N, s) !=
+        cudaSuccess)
+      return fail(HODLR_ERR_CUDA);
+    if (launch_leaf_solve<double, float>(*F, U, d.ldu, static_cast<float*>(F->Y), d.N, rL, 0, s) != cudaSuccess)
+      return fail(HODLR_ERR_CUDA);
+    r = factor_levels<float>(*F, s);
+  } else {
+    if (launch_copy_cols<__nv_bfloat16, double>(d.N, rL, V, d.ldv,
+                                                static_cast<__nv_bfloat16*>(const_cast<void*>(F->Vp)), d.N,
+                                                s) != cudaSuccess)
+      return fail(HODLR_ERR_CUDA);
+    if (launch_leaf_solve<double, __nv_bfloat16>(*F, U, d.ldu, static_cast<__nv_bfloat16*>(F->Y), d.N, rL, 0, s) !=
+        cudaSuccess)
+      return fail(HODLR_ERR_CUDA);
+    r = factor_levels<__nv_bfloat16>(*F, s);
+  }
+  if (r != HODLR_OK) return fail(r);
+  *out = F;
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_factor_status(hodlr_factor_t f, int64_t* where, int64_t* detail) {
+  if (!valid_factor(f)) return HODLR_ERR_ARG;
+  DevStatus h{};
+  if (cudaStreamSynchronize(f->stream) != cudaSuccess) return HODLR_ERR_CUDA;
+  if (cudaMemcpy(&h, f->status, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return HODLR_ERR_CUDA;
+  if (where) *where = h.where;
+  if (detail) *detail = h.detail;
+  return static_cast<hodlr_status>(h.code);
+}
+
+void hodlr_free(hodlr_factor_t f) { delete f; }
+
+hodlr_status hodlr_solve_workspace_size(hodlr_factor_t f, int32_t k, size_t* bytes) {
+  if (!valid_factor(f) || k < 1 || !bytes) return HODLR_ERR_ARG;
+  *bytes = solve_ws_bytes(*f, k);
+  return HODLR_OK;
+}
+
+static hodlr_status solve_entry(hodlr_factor_t f, double* B, int64_t ldb, int32_t k, void* work, size_t bytes,
+                                hodlr_stream_t stream, int trans) {
+  if (!valid_factor(f) || !B || k < 1 || ldb < f->d.N || !aligned(B, 8)) return HODLR_ERR_ARG;
+  if (!work || !aligned(work, kAlign) || bytes < solve_ws_bytes(*f, k)) return HODLR_ERR_WORKSPACE;
+  return solve_any(*f, B, ldb, k, work, trans, reinterpret_cast<cudaStream_t>(stream));
+}
+
+hodlr_status hodlr_solve(hodlr_factor_t f, double* B, int64_t ldb, int32_t k, void* workspace,
+                         size_t workspace_bytes, hodlr_stream_t stream) {
+  return solve_entry(f, B, ldb, k, workspace, workspace_bytes, stream, 0);
+}
+
+hodlr_status hodlr_solve_adjoint(hodlr_factor_t f, double* B, int64_t ldb, int32_t k, void* workspace,
+                                 size_t workspace_bytes, hodlr_stream_t stream) {
+  return solve_entry(f, B, ldb, k, workspace, workspace_bytes, stream, 1);
+}
+
+hodlr_status hodlr_logdet(hodlr_factor_t f, hodlr_stream_t stream, double* sign, double* logabsdet) {
+  if (!valid_factor(f) || !sign || !logabsdet) return HODLR_ERR_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (launch_logdet_reduce(*f, s) != cudaSuccess) return HODLR_ERR_CUDA;
+  double h[2];
+  if (cudaMemcpyAsync(h, f->ld_out, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return HODLR_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return HODLR_ERR_CUDA;
+  *sign = h[0];
+  *logabsdet = h[1];
+  DevStatus st{};
+  if (cudaMemcpy(&st, f->status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) return HODLR_ERR_CUDA;
+  return static_cast<hodlr_status>(st.code);
+}
+
+hodlr_status hodlr_matvec_workspace_size(const hodlr_desc* desc, int32_t k, size_t* bytes) {
+  hodlr_status st = check_desc(desc);
+  if (st != HODLR_OK) return st;
+  if (k < 1 || !bytes) return HODLR_ERR_ARG;
+  *bytes = matvec_ws_bytes(*desc, k);
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_matvec(const hodlr_desc* desc, const double* D, const double* U, const double* V,
+                          const double* X, int64_t ldx, double* Y, int64_t ldy, int32_t k, void* workspace,
+                          size_t workspace_bytes, hodlr_stream_t stream) {
+  hodlr_status st = check_desc(desc);
+  if (st != HODLR_OK) return st;
+  if (!D || !U || !V || !X || !Y || k < 1 || ldx < desc->N || ldy < desc->N) return HODLR_ERR_ARG;
+  if (X == Y) return HODLR_ERR_ARG;
+  if (!workspace || !aligned(workspace, kAlign) || workspace_bytes < matvec_ws_bytes(*desc, k))
+    return HODLR_ERR_WORKSPACE;
+  return matvec_core(*desc, D, U, V, X, ldx, Y, ldy, k, workspace, reinterpret_cast<cudaStream_t>(stream));
+}
+
+// ------------------------------------------------------------ refined solvers
+namespace {
+
+struct RefineLayout {
+  size_t R, solve, mv, dots, scal, V, Z, w, total;
+};
+
+RefineLayout refine_layout(const Factor& F, int k, int restart) {
+  RefineLayout l{};
+  const size_t N = (size_t)F.d.N;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes); return o; };
+  const int kk = k > 1 ? k : 1;
+  l.R = take(N * kk * sizeof(double));
+  l.solve = take(solve_ws_bytes(F, kk));
+  l.mv = take(matvec_ws_bytes(F.d, kk));
+  l.dots = take(dot_scratch_elems(F.d.N, (kk > restart + 1 ? kk : restart + 1)) * sizeof(double));
+  l.scal = take((size_t)(kk > restart + 2 ? kk : restart + 2) * 2 * sizeof(double));
+  if (restart > 0) {
+    l.V = take(N * (restart + 1) * sizeof(double));
+    l.Z = take(N * restart * sizeof(double));
+    l.w = take(N * sizeof(double));
+  }
+  l.total = off;
+  return l;
+}
+
+hodlr_status col_norms2(int64_t N, int k, const double* x, int64_t ldx, double* dev_out, double* scratch,
+                        double* host_out, cudaStream_t s) {
+  HODLR_CUDA(launch_dots(N, k, x, ldx, x, ldx, dev_out, scratch, s));
+  HODLR_CUDA(cudaMemcpyAsync(host_out, dev_out, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, s));
+  HODLR_CUDA(cudaStreamSynchronize(s));
+  return HODLR_OK;
+}
+
+}  // namespace
+
+hodlr_status hodlr_refine_workspace_size(hodlr_factor_t f, int32_t k, int32_t restart, size_t* bytes) {
+  if (!valid_factor(f) || k < 1 || restart < 0 || !bytes) return HODLR_ERR_ARG;
+  *bytes = refine_layout(*f, k, restart).total;
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_solve_refined(hodlr_factor_t f, const double* D, const double* U, const double* V,
+                                 const double* B, int64_t ldb, double* X, int64_t ldx, int32_t k, double tol,
+                                 int32_t max_iter, void* workspace, size_t workspace_bytes, hodlr_stream_t stream,
+                                 int32_t* iters, double* relres) {
+  if (!valid_factor(f) || !D || !U || !V || !B || !X || k < 1 || ldb < f->d.N || ldx < f->d.N || max_iter < 0 ||
+      !(tol > 0.0))
+    return HODLR_ERR_ARG;
+  const RefineLayout lay = refine_layout(*f, k, 0);
+  if (!workspace || !aligned(workspace, kAlign) || workspace_bytes < lay.total) return HODLR_ERR_WORKSPACE;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(workspace);
+  double* R = reinterpret_cast<double*>(w + lay.R);
+  void* sw = w + lay.solve;
+  void* mw = w + lay.mv;
+  double* scratch = reinterpret_cast<double*>(w + lay.dots);
+  double* dev_n = reinterpret_cast<double*>(w + lay.scal);
+  const hodlr_desc& d = f->d;
+  const int64_t N = d.N;
+  std::vector<double> nb(k), nr(k);
+  hodlr_status st;
+  HODLR_CUDA(launch_copy_cols<double, double>(N, k, B, ldb, X, ldx, s));
+  if ((st = solve_any(*f, X, ldx, k, sw, 0, s)) != HODLR_OK) return st;
+  if ((st = col_norms2(N, k, B, ldb, dev_n, scratch, nb.data(), s)) != HODLR_OK) return st;
+  double prev = INFINITY;
+  int grew = 0, it = 0;
+  double worst = INFINITY;
+  for (;;) {
+    if ((st = matvec_core(d, D, U, V, X, ldx, R, N, k, mw, s)) != HODLR_OK) return st;
+    HODLR_CUDA(launch_axpby_cols(N, k, 1.0, B, ldb, -1.0, R, N, s));  // R = B - A X
+    if ((st = col_norms2(N, k, R, N, dev_n, scratch, nr.data(), s)) != HODLR_OK) return st;
+    worst = 0.0;
+    for (int j = 0; j < k; ++j) {
+      const double rr = nb[j] > 0.0 ? std::sqrt(nr[j] / nb[j]) : std::sqrt(nr[j]);
+      worst = std::isnan(rr) ? INFINITY : (rr > worst ? rr : worst);
+    }
+    if (worst <= tol || it >= max_iter) break;
+    grew = worst > prev ? grew + 1 : 0;
+    if (grew >= 2) break;
+    prev = worst;
+    if ((st = solve_any(*f, R, N, k, sw, 0, s)) != HODLR_OK) return st;
+    HODLR_CUDA(launch_axpby_cols(N, k, 1.0, R, N, 1.0, X, ldx, s));  // X += correction
+    ++it;
+  }
+  if (iters) *iters = it;
+  if (relres) *relres = worst;
+  DevStatus ds{};
+  HODLR_CUDA(cudaMemcpy(&ds, f->status, sizeof(ds), cudaMemcpyDeviceToHost));
+  if (ds.code != 0) return static_cast<hodlr_status>(ds.code);
+  return worst <= tol ? HODLR_OK : HODLR_ERR_NOT_CONVERGED;
+}
+
+hodlr_status hodlr_gmres(hodlr_factor_t f, const double* D, const double* U, const double* V, const double* B,
+                         int64_t ldb, double* X, int64_t ldx, int32_t k, double tol, int32_t restart,
+                         int32_t max_iter, void* workspace, size_t workspace_bytes, hodlr_stream_t stream,
+                         int32_t* iters, double* relres) {
+  if (!valid_factor(f) || !D || !U || !V || !B || !X || k < 1 || ldb < f->d.N || ldx < f->d.N || restart < 1 ||
+      restart > 200 || max_iter < 0 || !(tol > 0.0))
+    return HODLR_ERR_ARG;
+  const RefineLayout lay = refine_layout(*f, k, restart);
+  if (!workspace || !aligned(workspace, kAlign) || workspace_bytes < lay.total) return HODLR_ERR_WORKSPACE;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(workspace);
+  double* r = reinterpret_cast<double*>(w + lay.R);
+  void* sw = w + lay.solve;
+  void* mw = w + lay.mv;
+  double* scratch = reinterpret_cast<double*>(w + lay.dots);
+  double* dev_h = reinterpret_cast<double*>(w + lay.scal);
+  double* Vk = reinterpret_cast<double*>(w + lay.V);
+  double* Zk = reinterpret_cast<double*>(w + lay.Z);
+  double* wv = reinterpret_cast<double*>(w + lay.w);
+  const hodlr_desc& d = f->d;
+  const int64_t N = d.N;
+  const int m = restart;
+  std::vector<double> H((size_t)(m + 1) * m), g(m + 1), cs(m), sn(m), h(m + 1), h2(m + 1), y(m);
+  hodlr_status st;
+  int total_it = 0;
+  double worst = 0.0;
+  for (int j = 0; j < k; ++j) {
+    const double* b = B + (int64_t)j * ldb;
+    double* x = X + (int64_t)j * ldx;
+    double nb2 = 0.0;
+    if ((st = col_norms2(N, 1, b, N, dev_h, scratch, &nb2, s)) != HODLR_OK) return st;
+    const double nb = std::sqrt(nb2) > 0.0 ? std::sqrt(nb2) : 1.0;
+    HODLR_CUDA(launch_copy_cols<double, double>(N, 1, b, N, x, N, s));
+    if ((st = solve_any(*f, x, N, 1, sw, 0, s)) != HODLR_OK) return st;
+    int col_it = 0;
+    double rel = INFINITY;
+    for (;;) {
+      // true residual r = b - A x
+      if ((st = matvec_core(d, D, U, V, x, N, r, N, 1, mw, s)) != HODLR_OK) return st;
+      HODLR_CUDA(launch_axpby_cols(N, 1, 1.0, b, N, -1.0, r, N, s));
+      double beta2 = 0.0;
+      if ((st = col_norms2(N, 1, r, N, dev_h, scratch, &beta2, s)) != HODLR_OK) return st;
+      const double beta = std::sqrt(beta2);
+      rel = beta / nb;
+      if (!(rel > tol) || col_it >= max_iter) break;
+      HODLR_CUDA(launch_axpby_cols(N, 1, 1.0 / beta, r, N, 0.0, Vk, N, s));  // v_0 = r / beta
+      std::fill(g.begin(), g.end(), 0.0);
+      g[0] = beta;
+      int nsteps = 0;
+      for (int i = 0; i < m && col_it < max_iter; ++i) {
+        double* vi = Vk + (int64_t)i * N;
+        double* zi = Zk + (int64_t)i * N;
+        HODLR_CUDA(launch_copy_cols<double, double>(N, 1, vi, N, zi, N, s));
+        if ((st = solve_any(*f, zi, N, 1, sw, 0, s)) != HODLR_OK) return st;  // z_i = M^{-1} v_i
+        if ((st = matvec_core(d, D, U, V, zi, N, wv, N, 1, mw, s)) != HODLR_OK) return st;  // w = A z_i
+        // classical Gram-Schmidt, twice
+        for (int pass = 0; pass < 2; ++pass) {
+          HODLR_CUDA(launch_multidot(N, i + 1, Vk, N, wv, dev_h, scratch, s));
+          HODLR_CUDA(launch_gemv_sub(N, i + 1, Vk, N, dev_h, wv, s));
+          HODLR_CUDA(cudaMemcpyAsync(pass ? h2.data() : h.data(), dev_h, (size_t)(i + 1) * sizeof(double),
+                                     cudaMemcpyDeviceToHost, s));
+        }
+        double hn2 = 0.0;
+        if ((st = col_norms2(N, 1, wv, N, dev_h, scratch, &hn2, s)) != HODLR_OK) return st;  // syncs
+        double* Hi = H.data() + (size_t)i * (m + 1);
+        for (int q = 0; q <= i; ++q) Hi[q] = h[q] + h2[q];
+        Hi[i + 1] = std::sqrt(hn2);
+        if (Hi[i + 1] > 0.0)
+          HODLR_CUDA(launch_axpby_cols(N, 1, 1.0 / Hi[i + 1], wv, N, 0.0, Vk + (int64_t)(i + 1) * N, N, s));
+        // Givens rotations on column i
+        for (int q = 0; q < i; ++q) {
+          const double t = cs[q] * Hi[q] + sn[q] * Hi[q + 1];
+          Hi[q + 1] = -sn[q] * Hi[q] + cs[q] * Hi[q + 1];
+          Hi[q] = t;
+        }
+        const double den = std::hypot(Hi[i], Hi[i + 1]);
+        cs[i] = den > 0.0 ? Hi[i] / den : 1.0;
+        sn[i] = den > 0.0 ? Hi[i + 1] / den : 0.0;
+        Hi[i] = den;
+        Hi[i + 1] = 0.0;
+        g[i + 1] = -sn[i] * g[i];
+        g[i] = cs[i] * g[i];
+        ++nsteps;
+        ++col_it;
+        if (std::fabs(g[i + 1]) / nb <= 0.5 * tol) break;
+      }
+      // y = H(0:n, 0:n)^{-1} g(0:n), x += Z y
+      for (int q = nsteps - 1; q >= 0; --q) {
+        double acc = g[q];
+        for (int p = q + 1; p < nsteps; ++p) acc -= H[(size_t)p * (m + 1) + q] * y[p];
+        const double hq = H[(size_t)q * (m + 1) + q];
+        y[q] = hq != 0.0 ? acc / hq : 0.0;
+      }
+      for (int q = 0; q < nsteps; ++q) h[q] = -y[q];
+      HODLR_CUDA(cudaMemcpyAsync(dev_h, h.data(), (size_t)nsteps * sizeof(double), cudaMemcpyHostToDevice, s));
+      HODLR_CUDA(launch_gemv_sub(N, nsteps, Zk, N, dev_h, x, s));  // x -= Z(-y)
+      HODLR_CUDA(cudaStreamSynchronize(s));
+    }
+    total_it += col_it;
+    if (!(rel <= worst)) worst = rel;
+  }
+  if (iters) *iters = total_it;
+  if (relres) *relres = worst;
+  DevStatus ds{};
+  HODLR_CUDA(cudaMemcpy(&ds, f->status, sizeof(ds), cudaMemcpyDeviceToHost));
+  if (ds.code != 0) return static_cast<hodlr_status>(ds.code);
+  return worst <= tol ? HODLR_OK : HODLR_ERR_NOT_CONVERGED;
+}
+
+int64_t hodlr_launch_count(void) { return g_launches.load(); }
+
+void hodlr_profile_enable(int32_t on) { g_prof.store(on != 0); }
+
+void hodlr_profile_reset(void) {
+  std::lock_guard<std::mutex> g(g_mu);
+  for (int i = 0; i < KC_COUNT; ++i) {
+    g_ms[i] = 0.0;
+    g_n[i] = 0;
+  }
+}
+
+int32_t hodlr_profile_read(double* ms, int64_t* launches, int32_t n) {
+  cudaDeviceSynchronize();
+  std::lock_guard<std::mutex> g(g_mu);
+  for (const PendingBracket& p : g_pending) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+      g_ms[p.cls] += t;
+      g_n[p.cls] += p.n;
+    }
+    g_pool.push_back(p.a);
+    g_pool.push_back(p.b);
+  }
+  g_pending.clear();
+  for (int i = 0; i < n && i < KC_COUNT; ++i) {
+    if (ms) ms[i] = g_ms[i];
+    if (launches) launches[i] = g_n[i];
+  }
+  return KC_COUNT;
+}
+
+const char* hodlr_profile_name(int32_t cls) {
+  return (cls >= 0 && cls < KC_COUNT) ? kClassName[cls] : "";
+}
+
+}  // extern "C"

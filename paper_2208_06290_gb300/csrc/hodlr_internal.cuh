@@ -1,0 +1,163 @@
+// Internal declarations shared by the libhodlr translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "hodlr.h"
+
+namespace hodlr {
+
+// ---------------------------------------------------------------- status word
+// First device-side error wins (atomicCAS on code). Kernels never trap.
+struct DevStatus {
+  int code;
+  int pad;
+  long long where;
+  long long detail;
+};
+
+__device__ __forceinline__ void set_status(DevStatus* st, int code, long long where, long long detail) {
+  if (atomicCAS(&st->code, 0, code) == 0) {
+    st->where = where;
+    st->detail = detail;
+  }
+}
+
+// ---------------------------------------------------------------- conversions
+__device__ __forceinline__ void cvt(double& d, double s) { d = s; }
+__device__ __forceinline__ void cvt(float& d, double s) { d = (float)s; }
+__device__ __forceinline__ void cvt(float& d, float s) { d = s; }
+__device__ __forceinline__ void cvt(double& d, float s) { d = (double)s; }
+__device__ __forceinline__ void cvt(float& d, __nv_bfloat16 s) { d = __bfloat162float(s); }
+__device__ __forceinline__ void cvt(double& d, __nv_bfloat16 s) { d = (double)__bfloat162float(s); }
+__device__ __forceinline__ void cvt(__nv_bfloat16& d, float s) { d = __float2bfloat16_rn(s); }
+__device__ __forceinline__ void cvt(__nv_bfloat16& d, double s) { d = __float2bfloat16_rn((float)s); }
+
+template <typename TD, typename TS>
+__device__ __forceinline__ TD conv(TS s) {
+  TD d;
+  cvt(d, s);
+  return d;
+}
+
+// ---------------------------------------------------------------- tree geometry
+// Child level c (1..L): nodes of n_c = N >> c = m * 2^(L-c) rows. Projections
+// are split into row chunks of ch(c) rows, n_c halved until it is at most
+// kChunkMax (so ch divides n_c, whatever m is); chunk q covers rows
+// [q*ch, (q+1)*ch) and belongs to node q / (n_c / ch).
+constexpr int64_t kChunkMax = 4096;
+
+__host__ __device__ inline int64_t node_rows(int64_t N, int c) { return N >> c; }
+__host__ __device__ inline int64_t chunk_rows(int64_t N, int c) {
+  int64_t n = N >> c;
+  while (n > kChunkMax) n >>= 1;
+  return n;
+}
+__host__ __device__ inline int64_t num_chunks(int64_t N, int c) { return N / chunk_rows(N, c); }
+__host__ __device__ inline int64_t chunks_per_node(int64_t N, int c) {
+  return node_rows(N, c) / chunk_rows(N, c);
+}
+
+// ---------------------------------------------------------------- factor object
+enum class Prec { F64 = 0, F32 = 1, BF16 = 3 };
+
+struct Factor {
+  hodlr_desc d;
+  hodlr_prec prec;
+  cudaStream_t stream;
+  // leaf LUs (column-major m x m blocks) in FP64 or FP32, row permutations
+  void* lu;          // double* (FP64) or float*
+  int* perm;         // nleaf * m: row i of the factored block is row perm[i] of D_b
+  // Y_big (N x rL, ld N): double (FP64), float (FP32) or bf16 (BF16)
+  void* Y;
+  // V_big as used by the level kernels: the caller's V (FP64) or a copy
+  const void* Vp;
+  int64_t ldvp;
+  // coupling LUs: level c (1..L) parents j at Kc[c] + j*(2r)^2 (FP64), perms likewise
+  double* K;
+  int* Kperm;
+  int64_t Koff[26];  // offset (in parents) of child level c's first parent
+  // projection partials (FP64): max over levels of num_chunks * r * r*c
+  double* P;
+  size_t P_elems;
+  // log-determinant pieces: leaves (logabs, sign) then parents in Koff order
+  double* leaf_ld;
+  double* node_ld;
+  double* ld_out;    // 2 doubles
+  DevStatus* status;
+};
+
+size_t factor_workspace_bytes(const hodlr_desc& d, hodlr_prec prec);
+
+// ---------------------------------------------------------------- launch accounting
+enum KernelClass {
+  KC_LEAF_LU = 0, KC_LEAF_SOLVE, KC_PROJECT, KC_COUPLING, KC_COUPLING_APPLY, KC_UPDATE, KC_REDUCE,
+  KC_LEAF_MATVEC, KC_VECTOR, KC_LOGDET, KC_COUNT
+};
+// Called by every launcher right after its kernel launch(es): counts them and,
+// when profiling is on, records the closing event of the bracket that
+// prof_begin opened on the same stream.
+void note_launches(int n);
+struct ProfScope {
+  int cls;
+  cudaStream_t s;
+  void* a;
+  ProfScope(int c, cudaStream_t st);
+  ~ProfScope();
+};
+
+// ---------------------------------------------------------------- kernels (launchers)
+// Leaf stage
+cudaError_t launch_leaf_lu(const Factor& F, const double* D, cudaStream_t s);
+// X_b <- D_b^{-1} X_b (trans = 0) or D_b^{-T} X_b (trans = 1) for all leaves,
+// columns [0, ncols); in and out may alias.
+template <typename TIN, typename TOUT>
+cudaError_t launch_leaf_solve(const Factor& F, const TIN* in, int64_t ldin, TOUT* out, int64_t ldout,
+                              int ncols, int trans, cudaStream_t s);
+
+// Level stage. P[q] (r x ncols, ld r) = Bas(rows_q, block)^T R(rows_q, 0:ncols)
+// for every chunk q of child level c. Bas is N x (r*L) (ld ldb), block c-1.
+template <typename TB, typename TR>
+cudaError_t launch_project(int64_t N, int r, int c, const TB* Bas, int64_t ldb, int bas_block,
+                           const TR* R, int64_t ldr, int ncols, double* P, int acc_fp64, cudaStream_t s);
+
+// R(rows of node, 0:ncols) += alpha * Bas(rows, block) * W(node') with W(node')
+// = Wbase + node' * wstride (r x ncols, ld r), node' = node ^ swap_sibling.
+template <typename TB, typename TR>
+cudaError_t launch_update(int64_t N, int r, int c, const TB* Bas, int64_t ldb, int bas_block,
+                          TR* R, int64_t ldr, int ncols, const double* Wbase, int64_t wstride,
+                          int swap_sibling, double alpha, int acc_fp64, cudaStream_t s);
+
+// Coupling (FP64). Factor mode: reduce partials of both children, form K~,
+// LU, log|det|, solve for the ancestor columns; W' written to each child's
+// first chunk slot. Solve modes reuse the stored LU.
+cudaError_t launch_coupling_factor(const Factor& F, int c, cudaStream_t s);
+cudaError_t launch_coupling_solve(const Factor& F, int c, double* P, int k, int trans, cudaStream_t s);
+// Sum the chunk partials of every node into the node's first chunk slot.
+cudaError_t launch_reduce_chunks(int64_t N, int r, int c, double* P, int ncols, cudaStream_t s);
+
+// Leaf stage of the matvec: Y_b = D_b X_b (FP64).
+cudaError_t launch_leaf_matvec(const hodlr_desc& d, const double* D, const double* X, int64_t ldx,
+                               double* Y, int64_t ldy, int k, cudaStream_t s);
+
+// Vectors
+template <typename TD, typename TS>
+cudaError_t launch_copy_cols(int64_t N, int k, const TS* src, int64_t lds, TD* dst, int64_t ldd, cudaStream_t s);
+cudaError_t launch_axpby_cols(int64_t N, int k, double a, const double* x, int64_t ldx, double b, double* y,
+                              int64_t ldy, cudaStream_t s);  // y = a x + b y
+// out[j] = sum_i x(i,j)*y(i,j) for j < k (deterministic two-stage), scratch >= dot_scratch_elems(N,k)
+size_t dot_scratch_elems(int64_t N, int k);
+cudaError_t launch_dots(int64_t N, int k, const double* x, int64_t ldx, const double* y, int64_t ldy,
+                        double* out, double* scratch, cudaStream_t s);
+// out[j] = sum_i X(i, j) * w(i) for j < k (X N x k, ld ldx) -> multi-dot with one vector
+cudaError_t launch_multidot(int64_t N, int k, const double* X, int64_t ldx, const double* w, double* out,
+                            double* scratch, cudaStream_t s);
+// w -= X h  (X N x k, h k device vector)
+cudaError_t launch_gemv_sub(int64_t N, int k, const double* X, int64_t ldx, const double* h, double* w,
+                            cudaStream_t s);
+cudaError_t launch_logdet_reduce(const Factor& F, cudaStream_t s);
+
+}  // namespace hodlr

@@ -1,0 +1,492 @@
+// Level stage of the factorization and solves (Alg. 1 / Alg. 3 level loop,
+// Alg. 2 / Alg. 4 level loop): projections onto the level's bases, the 2r x 2r
+// coupling systems and the rank-r updates.
+#include "hodlr_internal.cuh"
+
+namespace hodlr {
+
+template <typename T> struct AccOf { using type = float; };
+template <> struct AccOf<double> { using type = double; };
+
+// ---------------------------------------------------------------------------
+// Projection partials. For child level c and chunk q (rows [q*ch, (q+1)*ch)),
+// P[q] (r x ncols, ld r, FP64) = Bas(rows, block)^T * R(rows, 0:ncols).
+// CTA = one chunk x 64 columns; the chunk is streamed 32 rows at a time
+// through shared memory and every thread keeps an (RT/16) x 4 register tile.
+template <typename TB, typename TR, typename TA, int RT>
+__global__ void __launch_bounds__(256) project_kernel(int64_t N, int r, int c, const TB* __restrict__ Bas,
+                                                      int64_t ldb, int bas_block, const TR* __restrict__ R,
+                                                      int64_t ldr, int ncols, double* __restrict__ P) {
+  constexpr int NV = RT / 16;
+  __shared__ TA sB[32][RT + 1];
+  __shared__ TA sR[32][64 + 1];
+  const int64_t ch = chunk_rows(N, c);
+  const int64_t q = blockIdx.x;
+  const int64_t row0 = q * ch;
+  const int j0 = blockIdx.y * 64;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const TB* B0 = Bas + (int64_t)bas_block * r * ldb + row0;
+  const TR* R0 = R + row0;
+  TA acc[NV][4];
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[v][u] = TA(0);
+  for (int64_t k0 = 0; k0 < ch; k0 += 32) {
+    const int kn = (ch - k0) < 32 ? (int)(ch - k0) : 32;
+    for (int e = tid; e < 32 * RT; e += 256) {
+      const int kk = e & 31, col = e >> 5;
+      sB[kk][col] = (col < r && kk < kn) ? conv<TA>(B0[(int64_t)col * ldb + k0 + kk]) : TA(0);
+    }
+    for (int e = tid; e < 32 * 64; e += 256) {
+      const int kk = e & 31, col = e >> 5;
+      sR[kk][col] = (j0 + col < ncols && kk < kn) ? conv<TA>(R0[(int64_t)(j0 + col) * ldr + k0 + kk]) : TA(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      TA bv[NV], rv[4];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) bv[v] = sB[kk][ty + 16 * v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) rv[u] = sR[kk][tx + 16 * u];
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[v][u] += bv[v] * rv[u];
+    }
+    __syncthreads();
+  }
+  double* Pq = P + (size_t)q * r * ncols;
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int row = ty + 16 * v, col = j0 + tx + 16 * u;
+      if (row < r && col < ncols) Pq[(size_t)col * r + row] = (double)acc[v][u];
+    }
+}
+
+template <typename TB, typename TR>
+cudaError_t launch_project(int64_t N, int r, int c, const TB* Bas, int64_t ldb, int bas_block, const TR* R,
+                           int64_t ldr, int ncols, double* P, int acc_fp64, cudaStream_t s) {
+  ProfScope prof_(KC_PROJECT, s);
+  if (ncols <= 0) return cudaSuccess;
+  dim3 grid((unsigned)num_chunks(N, c), (ncols + 63) / 64);
+  using TA = typename AccOf<TR>::type;
+  if (r <= 16)
+    { project_kernel<TB, TR, TA, 16><<<grid, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, ldr, ncols, P); note_launches(1); }
+  else if (r <= 32)
+    { project_kernel<TB, TR, TA, 32><<<grid, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, ldr, ncols, P); note_launches(1); }
+  else
+    { project_kernel<TB, TR, TA, 64><<<grid, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, ldr, ncols, P); note_launches(1); }
+  (void)acc_fp64;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Rank-r update: R(rows, 0:ncols) += alpha * Bas(rows, block) * W(node')
+// for a 64-row x 64-column tile (rows of one node). W is FP64 (r x ncols, ld r).
+template <typename TB, typename TR, typename TA, int RT>
+__global__ void __launch_bounds__(256) update_kernel(int64_t N, int r, int c, const TB* __restrict__ Bas,
+                                                     int64_t ldb, int bas_block, TR* __restrict__ R, int64_t ldr,
+                                                     int ncols, const double* __restrict__ Wbase, int64_t wstride,
+                                                     int swap_sibling, double alpha) {
+  constexpr int KT = RT < 32 ? RT : 32;  // inner-dimension tile
+  __shared__ TA sB[KT][64 + 1];  // [k][row]
+  __shared__ TA sW[KT][64 + 1];  // [k][col]
+  // tiles of 64 rows laid out node by node; the last tile of a node is ragged
+  const int64_t n = N >> c;
+  const int64_t tpn = (n + 63) / 64;
+  const int64_t node = blockIdx.x / tpn;
+  const int64_t t0 = (blockIdx.x % tpn) * 64;
+  const int rt = (n - t0) < 64 ? (int)(n - t0) : 64;
+  const int64_t row0 = node * n + t0;
+  const double* W = Wbase + (node ^ swap_sibling) * wstride;
+  const int j0 = blockIdx.y * 64;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const TB* B0 = Bas + (int64_t)bas_block * r * ldb + row0;
+  TA acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = TA(0);
+  for (int k0 = 0; k0 < r; k0 += KT) {
+    for (int e = tid; e < 64 * KT; e += 256) {
+      const int i = e & 63, kk = e >> 6;
+      sB[kk][i] = (k0 + kk < r && i < rt) ? conv<TA>(B0[(int64_t)(k0 + kk) * ldb + i]) : TA(0);
+    }
+    for (int e = tid; e < 64 * KT; e += 256) {
+      const int kk = e % KT, col = e / KT;
+      sW[kk][col] = (k0 + kk < r && j0 + col < ncols) ? conv<TA>(alpha * W[(size_t)(j0 + col) * r + k0 + kk])
+                                                      : TA(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < KT; ++kk) {
+      TA bv[4], wv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) bv[a] = sB[kk][tx + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) wv[b] = sW[kk][ty + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] += bv[a] * wv[b];
+    }
+    __syncthreads();
+  }
+  TR* R0 = R + row0;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int col = j0 + ty + 16 * b;
+    if (col >= ncols) continue;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int i = tx + 16 * a;
+      if (i < rt) {
+        TR* p = R0 + (int64_t)col * ldr + i;
+        *p = conv<TR>(conv<TA>(*p) + acc[a][b]);
+      }
+    }
+  }
+}
+
+template <typename TB, typename TR>
+cudaError_t launch_update(int64_t N, int r, int c, const TB* Bas, int64_t ldb, int bas_block, TR* R, int64_t ldr,
+                          int ncols, const double* Wbase, int64_t wstride, int swap_sibling, double alpha,
+                          int acc_fp64, cudaStream_t s) {
+  ProfScope prof_(KC_UPDATE, s);
+  if (ncols <= 0) return cudaSuccess;
+  const int64_t n = N >> c;
+  const int64_t tpn = (n + 63) / 64;
+  dim3 grid((unsigned)(((int64_t)1 << c) * tpn), (ncols + 63) / 64);
+  using TA = typename AccOf<TR>::type;
+  (void)acc_fp64;
+  if (r <= 16)
+    { update_kernel<TB, TR, TA, 16><<<grid, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, ldr, ncols, Wbase,
+                                                       wstride, swap_sibling, alpha); note_launches(1); }
+  else if (r <= 32)
+    { update_kernel<TB, TR, TA, 32><<<grid, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, ldr, ncols, Wbase,
+                                                       wstride, swap_sibling, alpha); note_launches(1); }
+  else
+    { update_kernel<TB, TR, TA, 64><<<grid, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, ldr, ncols, Wbase,
+                                                       wstride, swap_sibling, alpha); note_launches(1); }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// K4: coupling matrices of the parents of child level c, in FP64.
+// K~ = [[I, T_beta], [T_alpha, I]] with T_x = V_x^T Y_x summed over the chunk
+// partials of child x (own block = slot columns r(c-1) .. rc-1). The inverse
+// is computed in place by Gauss-Jordan elimination with partial pivoting; its
+// pivots and row swaps are those of LU with partial pivoting, which gives
+// log|det K~| and its sign.
+__global__ void __launch_bounds__(256) coupling_factor_kernel(int64_t N, int r, int c,
+                                                              const double* __restrict__ P,
+                                                              double* __restrict__ Kinv,
+                                                              double* __restrict__ node_ld, DevStatus* st,
+                                                              int64_t heap_first) {
+  extern __shared__ double sK[];
+  const int n = 2 * r;
+  int* spiv = reinterpret_cast<int*>(sK + (size_t)n * n);
+  double* scol = sK + (size_t)n * n + ((n + 1) / 2);
+  __shared__ int s_piv, s_swaps, s_sing;
+  __shared__ double s_pval, s_la;
+  __shared__ int s_neg;
+  const int64_t j = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int64_t cpn = chunks_per_node(N, c);
+  const size_t slot = (size_t)r * r * c;
+  const int anc = r * (c - 1);
+  const int64_t qa = 2 * j * cpn, qb = (2 * j + 1) * cpn;
+  if (tid == 0) { s_swaps = 0; s_sing = -1; s_la = 0.0; s_neg = 0; }
+  for (int e = tid; e < n * n; e += nt) {
+    const int row = e % n, col = e / n;
+    double v = (row == col) ? 1.0 : 0.0;
+    if (row < r && col >= r) {
+      double acc = 0.0;
+      for (int64_t q = 0; q < cpn; ++q) acc += P[(qb + q) * slot + (size_t)(anc + col - r) * r + row];
+      v = acc;
+    } else if (row >= r && col < r) {
+      double acc = 0.0;
+      for (int64_t q = 0; q < cpn; ++q) acc += P[(qa + q) * slot + (size_t)(anc + col) * r + (row - r)];
+      v = acc;
+    }
+    sK[e] = v;
+  }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (tid < 32) {
+      const int lane = tid;
+      double best = -1.0;
+      int bi = n;
+      for (int i = k + lane; i < n; i += 32) {
+        const double v = fabs(sK[(size_t)k * n + i]);
+        if (v > best) { best = v; bi = i; }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      if (lane == 0) s_piv = bi < n ? bi : k;
+    }
+    __syncthreads();
+    const int p = s_piv;
+    if (p != k) {
+      for (int jj = tid; jj < n; jj += nt) {
+        const double t = sK[(size_t)jj * n + k];
+        sK[(size_t)jj * n + k] = sK[(size_t)jj * n + p];
+        sK[(size_t)jj * n + p] = t;
+      }
+    }
+    if (tid == 0) {
+      spiv[k] = p;
+      if (p != k) s_swaps ^= 1;
+    }
+    __syncthreads();
+    const double piv = sK[(size_t)k * n + k];
+    if (tid == 0) {
+      s_la += log(fabs(piv));
+      s_neg ^= (piv < 0.0);
+      if (piv == 0.0 && s_sing < 0) s_sing = k;
+    }
+    const double rp = (piv != 0.0) ? 1.0 / piv : 0.0;
+    for (int i = tid; i < n; i += nt) scol[i] = sK[(size_t)k * n + i];
+    __syncthreads();
+    for (int jj = tid; jj < n; jj += nt) {
+      if (jj != k) sK[(size_t)jj * n + k] *= rp;
+    }
+    if (tid == 0) sK[(size_t)k * n + k] = rp;
+    __syncthreads();
+    for (int e = tid; e < n * n; e += nt) {
+      const int i = e % n, jj = e / n;
+      if (i == k) continue;
+      if (jj != k) sK[e] -= scol[i] * sK[(size_t)jj * n + k];
+      else sK[e] = -scol[i] * rp;
+    }
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = spiv[k];
+    if (p != k) {
+      for (int i = tid; i < n; i += nt) {
+        const double t = sK[(size_t)k * n + i];
+        sK[(size_t)k * n + i] = sK[(size_t)p * n + i];
+        sK[(size_t)p * n + i] = t;
+      }
+    }
+    __syncthreads();
+  }
+  double* out = Kinv + (size_t)j * n * n;
+  for (int e = tid; e < n * n; e += nt) out[e] = sK[e];
+  if (tid == 0) {
+    node_ld[2 * j] = s_la;
+    node_ld[2 * j + 1] = (s_sing >= 0) ? 0.0 : ((s_neg ^ s_swaps) ? -1.0 : 1.0);
+    if (s_sing >= 0) set_status(st, HODLR_ERR_SINGULAR_COUPLING, heap_first + j, s_sing);
+  }
+}
+
+cudaError_t launch_coupling_factor(const Factor& F, int c, cudaStream_t s) {
+  ProfScope prof_(KC_COUPLING, s);
+  const int r = F.d.r;
+  const int n = 2 * r;
+  const int64_t parents = (int64_t)1 << (c - 1);
+  const size_t sm = (size_t)n * n * sizeof(double) + (size_t)((n + 1) / 2) * sizeof(double) + n * sizeof(double);
+  cudaFuncSetAttribute(coupling_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  { coupling_factor_kernel<<<(unsigned)parents, 256, sm, s>>>(F.d.N, r, c, F.P, F.K + F.Koff[c] * n * n,
+                                                             F.node_ld + 2 * F.Koff[c], F.status,
+                                                             (int64_t)1 << (c - 1)); note_launches(1); }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Coupling application: for every parent and a 32-column tile of the
+// right-hand side, out = Kinv * rhs (or Kinv^T * rhs), with
+//   rhs = [from first; from second] summed over chunk partials,
+//   first = beta, second = alpha   (factor and solve: K~ [w_a; w_b] = [s_b; s_a])
+//   first = alpha, second = beta   (adjoint: K~^T t = [s_a; s_b]),
+// and out rows 0..r-1 written to alpha's first slot, rows r..2r-1 to beta's.
+// Slots are r x sw (ld r); the right-hand side is columns [0, nrhs).
+template <typename TA, int NR>
+__global__ void __launch_bounds__(256) coupling_apply_kernel(int64_t N, int r, int c, double* P, int64_t sw,
+                                                             int nrhs, const double* __restrict__ Kinv,
+                                                             int first_is_beta, int trans) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = 2 * r;
+  TA* sKc = reinterpret_cast<TA*>(smem_raw);  // [n][33]: Kinv(i, kb + kk) (or Kinv^T)
+  TA* sRhs = sKc + (size_t)n * 33;            // [n][33]: right-hand side, this CTA's columns
+  const int64_t j = blockIdx.x;
+  const int c0 = blockIdx.y * 32;
+  const int tid = threadIdx.x;
+  const int col = tid & 31, rg = tid >> 5;
+  const int64_t cpn = chunks_per_node(N, c);
+  const size_t slot = (size_t)r * sw;
+  const int64_t qa = 2 * j * cpn, qb = (2 * j + 1) * cpn;
+  const int64_t qfirst = first_is_beta ? qb : qa, qsecond = first_is_beta ? qa : qb;
+  const double* Kj = Kinv + (size_t)j * n * n;
+  // gather the right-hand side (FP64 sum of the chunk partials)
+  for (int e = tid; e < n * 32; e += 256) {
+    const int i = e % n, cc = e / n;
+    double acc = 0.0;
+    if (c0 + cc < nrhs) {
+      const int64_t q0 = i < r ? qfirst : qsecond;
+      const int row = i < r ? i : i - r;
+      for (int64_t q = 0; q < cpn; ++q) acc += P[(q0 + q) * slot + (size_t)(c0 + cc) * r + row];
+    }
+    sRhs[i * 33 + cc] = (TA)acc;
+  }
+  TA acc[NR];
+#pragma unroll
+  for (int a = 0; a < NR; ++a) acc[a] = TA(0);
+  for (int kb = 0; kb < n; kb += 32) {
+    __syncthreads();
+    for (int e = tid; e < n * 32; e += 256) {
+      const int i = e % n, kk = e / n;
+      const int kg = kb + kk;
+      double v = 0.0;
+      if (kg < n) v = trans ? Kj[(size_t)i * n + kg] : Kj[(size_t)kg * n + i];
+      sKc[i * 33 + kk] = (TA)v;
+    }
+    __syncthreads();
+    const int kn = min(32, n - kb);
+    for (int kk = 0; kk < kn; ++kk) {
+      const TA xv = sRhs[(kb + kk) * 33 + col];
+#pragma unroll
+      for (int a = 0; a < NR; ++a) {
+        const int i = rg + 8 * a;
+        if (i < n) acc[a] += sKc[i * 33 + kk] * xv;
+      }
+    }
+  }
+  __syncthreads();  // every CTA reads all its partials before any write below
+  if (c0 + col < nrhs) {
+#pragma unroll
+    for (int a = 0; a < NR; ++a) {
+      const int i = rg + 8 * a;
+      if (i < n) {
+        const int64_t q = i < r ? qa : qb;
+        const int row = i < r ? i : i - r;
+        P[q * slot + (size_t)(c0 + col) * r + row] = (double)acc[a];
+      }
+    }
+  }
+}
+
+template <typename TA>
+static cudaError_t coupling_apply(int64_t N, int r, int c, double* P, int64_t sw, int nrhs, const double* Kinv,
+                                  int first_is_beta, int trans, cudaStream_t s) {
+  if (nrhs <= 0) return cudaSuccess;
+  dim3 grid(1u << (c - 1), (nrhs + 31) / 32);
+  const int n = 2 * r;
+  const size_t sm = (size_t)2 * n * 33 * sizeof(TA);
+  if (n <= 32) {
+    { coupling_apply_kernel<TA, 4><<<grid, 256, sm, s>>>(N, r, c, P, sw, nrhs, Kinv, first_is_beta, trans); note_launches(1); }
+  } else if (n <= 64) {
+    { coupling_apply_kernel<TA, 8><<<grid, 256, sm, s>>>(N, r, c, P, sw, nrhs, Kinv, first_is_beta, trans); note_launches(1); }
+  } else {
+    cudaFuncSetAttribute(coupling_apply_kernel<TA, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    { coupling_apply_kernel<TA, 16><<<grid, 256, sm, s>>>(N, r, c, P, sw, nrhs, Kinv, first_is_beta, trans); note_launches(1); }
+  }
+  return cudaGetLastError();
+}
+
+// Factor: W' = Kinv [W_beta; W_alpha] for the ancestor columns of every parent.
+cudaError_t launch_coupling_factor_apply(const Factor& F, int c, cudaStream_t s) {
+  ProfScope prof_(KC_COUPLING_APPLY, s);
+  const int r = F.d.r;
+  const int anc = r * (c - 1);
+  const double* Kc = F.K + F.Koff[c] * 4 * r * r;
+  if (F.prec == HODLR_PREC_FP64) return coupling_apply<double>(F.d.N, r, c, F.P, (int64_t)r * c, anc, Kc, 1, 0, s);
+  return coupling_apply<float>(F.d.N, r, c, F.P, (int64_t)r * c, anc, Kc, 1, 0, s);
+}
+
+// Solve / adjoint: w = Kinv [s_beta; s_alpha] or t = Kinv^T [s_alpha; s_beta], FP64.
+cudaError_t launch_coupling_solve(const Factor& F, int c, double* P, int k, int trans, cudaStream_t s) {
+  ProfScope prof_(KC_COUPLING_APPLY, s);
+  const int r = F.d.r;
+  const double* Kc = F.K + F.Koff[c] * 4 * r * r;
+  return coupling_apply<double>(F.d.N, r, c, P, k, k, Kc, trans ? 0 : 1, trans, s);
+}
+
+// ---------------------------------------------------------------------------
+// Sum the chunk partials of each node into the node's first slot (FP64,
+// fixed order).
+__global__ void reduce_chunks_kernel(int64_t N, int r, int c, double* P, int ncols) {
+  const int64_t cpn = chunks_per_node(N, c);
+  const int64_t node = blockIdx.x;
+  const size_t slot = (size_t)r * ncols;
+  const int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)slot) return;
+  double acc = 0.0;
+  for (int64_t q = 0; q < cpn; ++q) acc += P[(node * cpn + q) * slot + e];
+  P[node * cpn * slot + e] = acc;
+}
+
+cudaError_t launch_reduce_chunks(int64_t N, int r, int c, double* P, int ncols, cudaStream_t s) {
+  ProfScope prof_(KC_REDUCE, s);
+  if (chunks_per_node(N, c) == 1) return cudaSuccess;
+  const size_t slot = (size_t)r * ncols;
+  dim3 grid(1u << c, (unsigned)((slot + 255) / 256));
+  { reduce_chunks_kernel<<<grid, 256, 0, s>>>(N, r, c, P, ncols); note_launches(1); }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic FP64 sum of the log-determinant pieces: leaves then parents.
+__global__ void logdet_reduce_kernel(const double* leaf_ld, int64_t nleaf, const double* node_ld, int64_t nnode,
+                                     double* out) {
+  __shared__ double sla[256];
+  __shared__ int sneg[256], szero[256];
+  const int tid = threadIdx.x;
+  double la = 0.0;
+  int neg = 0, zero = 0;
+  for (int64_t i = tid; i < nleaf + nnode; i += 256) {
+    const double* p = i < nleaf ? leaf_ld + 2 * i : node_ld + 2 * (i - nleaf);
+    la += p[0];
+    neg ^= (p[1] < 0.0);
+    zero |= (p[1] == 0.0);
+  }
+  sla[tid] = la;
+  sneg[tid] = neg;
+  szero[tid] = zero;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (tid < w) {
+      sla[tid] += sla[tid + w];
+      sneg[tid] ^= sneg[tid + w];
+      szero[tid] |= szero[tid + w];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    out[0] = szero[0] ? 0.0 : (sneg[0] ? -1.0 : 1.0);
+    out[1] = sla[0];
+  }
+}
+
+cudaError_t launch_logdet_reduce(const Factor& F, cudaStream_t s) {
+  ProfScope prof_(KC_LOGDET, s);
+  const int64_t nleaf = (int64_t)1 << F.d.L;
+  { logdet_reduce_kernel<<<1, 256, 0, s>>>(F.leaf_ld, nleaf, F.node_ld, nleaf - 1, F.ld_out); note_launches(1); }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Explicit instantiations
+#define HODLR_INST(TB, TR)                                                                                      \
+  template cudaError_t launch_project<TB, TR>(int64_t, int, int, const TB*, int64_t, int, const TR*, int64_t, \
+                                              int, double*, int, cudaStream_t);                                 \
+  template cudaError_t launch_update<TB, TR>(int64_t, int, int, const TB*, int64_t, int, TR*, int64_t, int,   \
+                                             const double*, int64_t, int, double, int, cudaStream_t);
+HODLR_INST(double, double)
+HODLR_INST(float, float)
+HODLR_INST(__nv_bfloat16, __nv_bfloat16)
+HODLR_INST(__nv_bfloat16, float)
+#undef HODLR_INST
+
+}  // namespace hodlr

@@ -1,0 +1,138 @@
+// Column-vector kernels for the solves and the refined solvers: copies with
+// precision change, axpby, and deterministic FP64 dot products (fixed-order
+// two-stage reductions, so results do not depend on scheduling).
+#include "hodlr_internal.cuh"
+
+namespace hodlr {
+
+template <typename TD, typename TS>
+__global__ void copy_cols_kernel(int64_t N, int k, const TS* __restrict__ src, int64_t lds, TD* __restrict__ dst,
+                                 int64_t ldd) {
+  const int j = blockIdx.y;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    dst[(int64_t)j * ldd + i] = conv<TD>(src[(int64_t)j * lds + i]);
+}
+
+static unsigned grid_for(int64_t N) {
+  int64_t b = (N + 255) / 256;
+  return (unsigned)(b < 4096 ? b : 4096);
+}
+
+template <typename TD, typename TS>
+cudaError_t launch_copy_cols(int64_t N, int k, const TS* src, int64_t lds, TD* dst, int64_t ldd, cudaStream_t s) {
+  ProfScope prof_(KC_VECTOR, s);
+  if (k <= 0) return cudaSuccess;
+  { copy_cols_kernel<TD, TS><<<dim3(grid_for(N), k), 256, 0, s>>>(N, k, src, lds, dst, ldd); note_launches(1); }
+  return cudaGetLastError();
+}
+template cudaError_t launch_copy_cols<float, double>(int64_t, int, const double*, int64_t, float*, int64_t,
+                                                     cudaStream_t);
+template cudaError_t launch_copy_cols<double, float>(int64_t, int, const float*, int64_t, double*, int64_t,
+                                                     cudaStream_t);
+template cudaError_t launch_copy_cols<double, double>(int64_t, int, const double*, int64_t, double*, int64_t,
+                                                      cudaStream_t);
+template cudaError_t launch_copy_cols<float, float>(int64_t, int, const float*, int64_t, float*, int64_t,
+                                                    cudaStream_t);
+template cudaError_t launch_copy_cols<__nv_bfloat16, double>(int64_t, int, const double*, int64_t, __nv_bfloat16*,
+                                                             int64_t, cudaStream_t);
+
+__global__ void axpby_kernel(int64_t N, double a, const double* __restrict__ x, int64_t ldx, double b,
+                             double* __restrict__ y, int64_t ldy) {
+  const int j = blockIdx.y;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    y[(int64_t)j * ldy + i] = a * x[(int64_t)j * ldx + i] + b * y[(int64_t)j * ldy + i];
+}
+
+cudaError_t launch_axpby_cols(int64_t N, int k, double a, const double* x, int64_t ldx, double b, double* y,
+                              int64_t ldy, cudaStream_t s) {
+  ProfScope prof_(KC_VECTOR, s);
+  if (k <= 0) return cudaSuccess;
+  { axpby_kernel<<<dim3(grid_for(N), k), 256, 0, s>>>(N, a, x, ldx, b, y, ldy); note_launches(1); }
+  return cudaGetLastError();
+}
+
+// Stage 1: block b of column j sums x(i,j)*y(i,j) over its grid-stride rows,
+// tree-reduced in shared memory -> scratch[j * nb + b]. Stage 2: one block per
+// column sums the nb partials in index order.
+constexpr int kDotBlocks = 512;
+
+size_t dot_scratch_elems(int64_t N, int k) {
+  (void)N;
+  return (size_t)k * kDotBlocks;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  const int tid = threadIdx.x;
+  sh[tid] = v;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (tid < w) sh[tid] += sh[tid + w];
+    __syncthreads();
+  }
+  return sh[0];
+}
+
+// mode 0: x(:,j) . y(:,j); mode 1: X(:,j) . w (y is one vector)
+__global__ void dot_stage1(int64_t N, const double* __restrict__ x, int64_t ldx, const double* __restrict__ y,
+                           int64_t ldy, int mode, double* __restrict__ scratch) {
+  __shared__ double sh[256];
+  const int j = blockIdx.y;
+  const double* xj = x + (int64_t)j * ldx;
+  const double* yj = mode == 0 ? y + (int64_t)j * ldy : y;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    acc += xj[i] * yj[i];
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) scratch[(size_t)j * gridDim.x + blockIdx.x] = t;
+}
+
+__global__ void dot_stage2(const double* __restrict__ scratch, int nb, double* __restrict__ out) {
+  __shared__ double sh[256];
+  const int j = blockIdx.x;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += scratch[(size_t)j * nb + b];
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) out[j] = t;
+}
+
+static cudaError_t dots_impl(int64_t N, int k, const double* x, int64_t ldx, const double* y, int64_t ldy, int mode,
+                             double* out, double* scratch, cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  int64_t nb = (N + 255) / 256;
+  if (nb > kDotBlocks) nb = kDotBlocks;
+  { dot_stage1<<<dim3((unsigned)nb, k), 256, 0, s>>>(N, x, ldx, y, ldy, mode, scratch); note_launches(1); }
+  { dot_stage2<<<k, 256, 0, s>>>(scratch, (int)nb, out); note_launches(1); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dots(int64_t N, int k, const double* x, int64_t ldx, const double* y, int64_t ldy, double* out,
+                        double* scratch, cudaStream_t s) {
+  ProfScope prof_(KC_VECTOR, s);
+  return dots_impl(N, k, x, ldx, y, ldy, 0, out, scratch, s);
+}
+
+cudaError_t launch_multidot(int64_t N, int k, const double* X, int64_t ldx, const double* w, double* out,
+                            double* scratch, cudaStream_t s) {
+  ProfScope prof_(KC_VECTOR, s);
+  return dots_impl(N, k, X, ldx, w, 0, 1, out, scratch, s);
+}
+
+// w -= X h, X N x k (ld ldx), h a device vector of length k.
+__global__ void gemv_sub_kernel(int64_t N, int k, const double* __restrict__ X, int64_t ldx,
+                                const double* __restrict__ h, double* __restrict__ w) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < k; ++j) acc += X[(int64_t)j * ldx + i] * h[j];
+    w[i] -= acc;
+  }
+}
+
+cudaError_t launch_gemv_sub(int64_t N, int k, const double* X, int64_t ldx, const double* h, double* w,
+                            cudaStream_t s) {
+  ProfScope prof_(KC_VECTOR, s);
+  if (k <= 0) return cudaSuccess;
+  { gemv_sub_kernel<<<grid_for(N), 256, 0, s>>>(N, k, X, ldx, h, w); note_launches(1); }
+  return cudaGetLastError();
+}
+
+}  // namespace hodlr

@@ -1,0 +1,173 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances. The FP64 path and the oracle are both backward-stable
+eliminations of the same operator (LU with partial pivoting at the leaves;
+the GPU inverts each 2r x 2r coupling matrix by Gauss-Jordan where the oracle
+calls getrf/getrs), so their solutions differ by about cond(A) * u with
+u = 2^-53; the synthetic operators here have cond(A) < 1e2, hence the bound
+1e-11 on the relative solution difference (1e3 margin) and on the log-det
+difference relative to max(1, |log det|). Refined mixed-precision solves must
+reach the spec residual 1e-10, measured with the oracle's own matvec.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle.hodlr import RecursiveHODLR, assemble_dense, matvec as o_matvec
+from synth import HodlrShape, gaussian_rhs, synthetic_hodlr, to_math
+
+pytestmark = pytest.mark.gpu
+
+SOL_TOL = 1e-11
+LD_TOL = 1e-11
+
+
+def make_case(N, L, r, seed, shift=4.0, k=3):
+    D, U, V, g = synthetic_hodlr(HodlrShape(N, L, r), shift, seed)
+    B = gaussian_rhs(N, k, g)
+    host = to_math(D, U, V, B)
+    dev = tuple(t.to("cuda") for t in (D, U, V, B))
+    return host, dev
+
+
+def relerr(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def relres_oracle(Dm, Um, Vm, L, B, X):
+    R = B - o_matvec(Dm, Um, Vm, L, X)
+    return max(np.linalg.norm(R[:, j]) / np.linalg.norm(B[:, j]) for j in range(B.shape[1]))
+
+
+# (N, L, r): m = N >> L
+SHAPES = [
+    (256, 2, 4),        # m 64
+    (384, 3, 5),        # m 48, odd rank: partial warps and tiles
+    (200, 3, 1),        # m 25, rank 1
+    (128, 1, 3),        # one level
+    (4096, 6, 16),      # the N = 4096 synthetic configuration
+    (2048, 3, 32),      # m 256: leaf LU outside shared memory
+    (1024, 4, 64),      # maximum rank
+    (1 << 14, 6, 8),    # top levels split into several row chunks per node
+]
+
+
+@pytest.mark.parametrize("N,L,r", SHAPES)
+def test_fp64_factor_solve_logdet_adjoint(cuda_lib, N, L, r):
+    hb = cuda_lib
+    (Dm, Um, Vm, Bm), (D, U, V, B) = make_case(N, L, r, seed=N + 7 * L + r)
+    rec = RecursiveHODLR(Dm, Um, Vm, L)
+    F = hb.hodlr_factor(D, U, V, L, r, "fp64")
+    assert hb.hodlr_factor_status(F)[0] == 0
+    X = hb.hodlr_solve(F, B.clone())
+    x_or = rec.solve(Bm)
+    assert relerr(X.cpu().numpy(), x_or) < SOL_TOL
+    Xt = hb.hodlr_solve_adjoint(F, B.clone())
+    assert relerr(Xt.cpu().numpy(), rec.solve_adjoint(Bm)) < SOL_TOL
+    s, la = hb.hodlr_logdet(F)
+    so, lao = rec.slogdet()
+    assert s == so
+    assert abs(la - lao) <= LD_TOL * max(1.0, abs(lao))
+
+
+@pytest.mark.parametrize("N,L,r", SHAPES[:6])
+def test_matvec_fp64(cuda_lib, N, L, r):
+    hb = cuda_lib
+    (Dm, Um, Vm, Bm), (D, U, V, B) = make_case(N, L, r, seed=3 * N + r)
+    Y = hb.hodlr_matvec(D, U, V, L, r, B)
+    ref = o_matvec(Dm, Um, Vm, L, Bm)
+    assert relerr(Y.cpu().numpy(), ref) < 1e-13
+
+
+def test_dense_c0_configuration(cuda_lib):
+    """N = 4096, leaf 64, rank 16, shift 4, seed 0: factor, solve and slogdet
+    against dense FP64 LU of the assembled matrix."""
+    hb = cuda_lib
+    (Dm, Um, Vm, Bm), (D, U, V, B) = make_case(4096, 6, 16, seed=0, k=1)
+    A = assemble_dense(Dm, Um, Vm, 6)
+    F = hb.hodlr_factor(D, U, V, 6, 16, "fp64")
+    X = hb.hodlr_solve(F, B.clone()).cpu().numpy()
+    assert relerr(X, np.linalg.solve(A, Bm)) < SOL_TOL
+    assert np.linalg.norm(Bm - A @ X) / np.linalg.norm(Bm) < 1e-13
+    s, la = hb.hodlr_logdet(F)
+    sd, lad = np.linalg.slogdet(A)
+    assert s == sd and abs(la - lad) <= LD_TOL * abs(lad)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("N,L,r", [(256, 2, 4), (4096, 6, 16), (2048, 3, 32), (1 << 14, 6, 8)])
+def test_mixed_refined_reaches_1e10(cuda_lib, prec, N, L, r):
+    hb = cuda_lib
+    (Dm, Um, Vm, Bm), (D, U, V, B) = make_case(N, L, r, seed=11 * N + r, k=2)
+    F = hb.hodlr_factor(D, U, V, L, r, prec)
+    X, it, rr, code = hb.hodlr_solve_refined(F, D, U, V, B, tol=1e-10, max_iter=60)
+    Xh = X.cpu().numpy()
+    assert rr <= 1e-10
+    assert relres_oracle(Dm, Um, Vm, L, Bm, Xh) <= 2e-10
+    assert relerr(Xh, RecursiveHODLR(Dm, Um, Vm, L).solve(Bm)) < 1e-8
+    # the low-precision factor's log-determinant, FP64-accumulated
+    s, la = hb.hodlr_logdet(F)
+    so, lao = RecursiveHODLR(Dm, Um, Vm, L).slogdet()
+    assert s == so
+    assert abs(la - lao) <= (1e-4 if prec == "fp32" else 5e-2) * max(1.0, abs(lao))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_gmres_reaches_1e10(cuda_lib, prec):
+    hb = cuda_lib
+    N, L, r = 4096, 5, 16
+    (Dm, Um, Vm, Bm), (D, U, V, B) = make_case(N, L, r, seed=99, k=1)
+    F = hb.hodlr_factor(D, U, V, L, r, prec)
+    X, it, rr, code = hb.hodlr_gmres(F, D, U, V, B, tol=1e-10, restart=30, max_iter=300)
+    assert rr <= 1e-10
+    assert relres_oracle(Dm, Um, Vm, L, Bm, X.cpu().numpy()) <= 2e-10
+
+
+def test_mixed_solve_adjoint_close_to_oracle(cuda_lib):
+    hb = cuda_lib
+    N, L, r = 2048, 4, 8
+    (Dm, Um, Vm, Bm), (D, U, V, B) = make_case(N, L, r, seed=5)
+    rec = RecursiveHODLR(Dm, Um, Vm, L)
+    for prec, tol in (("fp32", 1e-4), ("bf16", 5e-2)):
+        F = hb.hodlr_factor(D, U, V, L, r, prec)
+        assert relerr(hb.hodlr_solve(F, B.clone()).cpu().numpy(), rec.solve(Bm)) < tol
+        assert relerr(hb.hodlr_solve_adjoint(F, B.clone()).cpu().numpy(), rec.solve_adjoint(Bm)) < tol
+
+
+# ------------------------------------------------------------- device status
+def test_singular_leaf_reported(cuda_lib):
+    hb = cuda_lib
+    (_, _, _, _), (D, U, V, B) = make_case(512, 3, 4, seed=1)
+    D[5].zero_()
+    F = hb.hodlr_factor(D, U, V, 3, 4, "fp64")
+    code, where, detail = hb.hodlr_factor_status(F)
+    assert code == hb.HODLR_ERR_SINGULAR_LEAF and where == 5 and detail == 0
+
+
+def test_nonfinite_reported(cuda_lib):
+    hb = cuda_lib
+    (_, _, _, _), (D, U, V, B) = make_case(512, 3, 4, seed=1)
+    D[2, 3, 4] = float("nan")
+    F = hb.hodlr_factor(D, U, V, 3, 4, "fp32")
+    code, where, _ = hb.hodlr_factor_status(F)
+    assert code == hb.HODLR_ERR_NONFINITE and where == 2
+
+
+def test_singular_coupling_reported(cuda_lib):
+    """D = I, only the level-1 bases nonzero with U_a = V_a = e_1 (alpha) and
+    U_b = V_b = e_1 (beta): rows 1 and N/2+1 of A coincide and the root's
+    K~ = [[1, 1], [1, 1]] has an exact zero second pivot."""
+    hb = cuda_lib
+    N, L, r = 256, 2, 1
+    m = N >> L
+    D = torch.eye(m, dtype=torch.float64).repeat(1 << L, 1, 1).transpose(1, 2).contiguous().transpose(1, 2)
+    U = torch.zeros(r * L, N, dtype=torch.float64).T
+    U[0, 0] = 1.0
+    U[N // 2, 0] = 1.0
+    V = U.clone().T.contiguous().T
+    D, U, V = (t.to("cuda") for t in (D, U, V))
+    F = hb.hodlr_factor(D, U, V, L, r, "fp64")
+    code, where, detail = hb.hodlr_factor_status(F)
+    assert code == hb.HODLR_ERR_SINGULAR_COUPLING and where == 1 and detail == 1
+    with pytest.raises(hb.HodlrError):
+        hb.hodlr_logdet(F)
