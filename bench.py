@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""HODLR factor + solve benchmark on GB300 (one JSON line on stdout).
+
+Step = one pass of the whole hot path on one batch of synthetic input:
+low-precision factorization (leaf LU, leaf solves, per-level projections,
+FP64 coupling matrices, ancestor updates), the solve recovered to an FP64
+relative residual <= 1e-10 (FGMRES or iterative refinement, FP64 residual
+matvec), and the log-determinant. The plain FP64 factor + solve is timed
+beside it on the same inputs.
+
+value = algorithmic factor + solve flops (the exact loop count of the FP64
+algorithm, counted by paper_2208_06290_gb300.costs) / seconds per step,
+whole job (N replicas under torchrun: one independent problem per GPU).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                       [--impl native|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "HODLR factor+solve seconds & TFLOP/s at N=2^20, mixed vs FP64, resid ≤1e-10"
+
+# Workloads (shapes of the benchmark configurations). data: how the operator
+# is generated (untimed).
+WORKLOADS = {
+    "bie-2^20": dict(N=1 << 20, L=13, r=32, k=1, prec="bf16", solver="gmres", shift=4.0, seed=2,
+                     data="bie", desc="2D Laplace second-kind BIE on the star curve, N=2^20, leaf 128, rank 32, "
+                                      "1 RHS; BF16-panel factor as FGMRES preconditioner to relres 1e-10"),
+    "synthetic-4096": dict(N=4096, L=6, r=16, k=1, prec="fp64", solver="direct", shift=4.0, seed=0,
+                           data="synthetic", desc="synthetic HODLR N=4096, leaf 64, rank 16, FP64"),
+    "synthetic-2^23": dict(N=1 << 23, L=15, r=32, k=64, prec="bf16", solver="refine", shift=8.0, seed=4,
+                           data="synthetic", desc="synthetic HODLR N=2^23, leaf 256, rank 32, 64 RHS; BF16 "
+                                                  "factor + refinement to 1e-10"),
+}
+DEFAULT_WORKLOAD = "bie-2^20"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "bf16_tflops": d.get("bf16_tflops", 1900.0),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+# FP64 FMA-pipe peak used for ALU-bound kernels: derived in the design notes
+# from the sampled SM clock (see fp64_peak_tflops).
+FP64_FLOP_PER_CLK_PER_SM = 4.0
+
+
+def fp64_peak_tflops(sm_mhz):
+    return 152 * FP64_FLOP_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
+
+
+# ----------------------------------------------------------------- inputs
+def make_inputs(w, device, rank=0):
+    import torch
+    from synth import HodlrShape, gaussian_rhs, synthetic_hodlr
+    shape = HodlrShape(w["N"], w["L"], w["r"])
+    if w["data"] == "bie":
+        from synth.kernels import bie_hodlr
+        D, U, V = bie_hodlr(shape, device=device)
+        g = torch.Generator(device=device)
+        g.manual_seed(w["seed"] + 1000 * rank)
+    else:
+        D, U, V, g = synthetic_hodlr(shape, w["shift"], w["seed"] + 1000 * rank, device=device)
+    B = gaussian_rhs(w["N"], w["k"], g, device=device)
+    return D, U, V, B
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- native arm
+def run_native(args, w, rank, world):
+    import torch
+    import torch.distributed as dist
+    from paper_2208_06290_gb300 import binding as hb
+    from paper_2208_06290_gb300 import costs
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    N, L, r, k = w["N"], w["L"], w["r"], w["k"]
+    m = N >> L
+    D, U, V, B = make_inputs(w, dev, rank)
+    X = torch.empty(k, N, dtype=torch.float64, device=dev).T
+    flops = costs.factor_flops(N, m, r, L) + costs.solve_flops(N, m, r, L, k)
+    prec = w["prec"]
+    stream = torch.cuda.current_stream()
+
+    def step():
+        F = hb.hodlr_factor(D, U, V, L, r, prec)
+        if w["solver"] == "gmres":
+            _, it, rr, code = hb.hodlr_gmres(F, D, U, V, B, tol=1e-10, restart=30, max_iter=300, X=X,
+                                             raise_on_fail=False)
+        elif w["solver"] == "refine":
+            _, it, rr, code = hb.hodlr_solve_refined(F, D, U, V, B, tol=1e-10, max_iter=50, X=X,
+                                                     raise_on_fail=False)
+        else:
+            X.copy_(B)
+            hb.hodlr_solve(F, X)
+            it, rr, code = 0, None, 0
+        sign, ld = hb.hodlr_logdet(F)
+        return it, rr, code, ld
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    hb.hodlr_profile_reset()
+    hb.hodlr_profile_enable(True)
+    launches0 = hb.hodlr_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    info = [step() for _ in range(args.steps)]
+    e1.record(stream)
+    barrier()
+    hb.hodlr_profile_enable(False)
+    launches = hb.hodlr_launch_count() - launches0
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    prof = hb.hodlr_profile_read()
+    work = hb.hodlr_profile_work()
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    sec_step = ms_max / 1e3 / args.steps
+    iters = [i[0] for i in info]
+    relres = [i[1] for i in info]
+    # relres measured independently of the solver's own report
+    res = hb.hodlr_matvec(D, U, V, L, r, X)
+    res.sub_(B).neg_()
+    rel_true = float((res.norm(dim=0) / B.norm(dim=0)).max().item())
+
+    # plain FP64 factor + solve on the same inputs
+    fp64 = None
+    if not args.no_fp64:
+        Xf = torch.empty_like(X)
+
+        def step64():
+            F64 = hb.hodlr_factor(D, U, V, L, r, "fp64")
+            Xf.copy_(B)
+            hb.hodlr_solve(F64, Xf)
+            hb.hodlr_logdet(F64)
+
+        step64()
+        barrier()
+        n64 = max(1, min(args.steps, 2))
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(n64):
+            step64()
+        a1.record(stream)
+        barrier()
+        s64 = a0.elapsed_time(a1) / 1e3 / n64
+        r64 = hb.hodlr_matvec(D, U, V, L, r, Xf)
+        r64.sub_(B).neg_()
+        fp64 = {"seconds": s64, "tflops": flops / s64 / 1e12,
+                "relres": float((r64.norm(dim=0) / B.norm(dim=0)).max().item()),
+                "speedup_of_mixed": s64 / sec_step}
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        Dh, Uh, Vh, Bh = (tt.cpu().pin_memory() for tt in (D, U, V, B))
+        Xh = torch.empty(k, N, dtype=torch.float64).pin_memory().T
+        h2d = sum(tt.numel() * 8 for tt in (Dh, Uh, Vh, Bh))
+        d2h = Xh.numel() * 8
+        n_e2e = max(1, min(args.steps, 3))
+        barrier()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(n_e2e):
+            D.copy_(Dh, non_blocking=True)
+            U.copy_(Uh, non_blocking=True)
+            V.copy_(Vh, non_blocking=True)
+            B.copy_(Bh, non_blocking=True)
+            step()
+            Xh.copy_(X, non_blocking=True)
+        c1.record(stream)
+        barrier()
+        s_e2e = c0.elapsed_time(c1) / 1e3 / n_e2e
+        te = torch.tensor([s_e2e], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * flops / float(te.item()) / 1e12, "unit": "TFLOP/s", "seconds": float(te.item()),
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # roofline of the dominant kernel class, from the live CUDA-event brackets
+    pk = peaks()
+    dom = max(prof, key=lambda c: prof[c][0])
+    dms, dn = prof[dom]
+    dbytes, dflops = work[dom]
+    sm_mhz = clocks.get("sm_mhz") or 1462.0
+    if dom in ("coupling",) or prec == "fp64":
+        achieved = dflops / (dms / 1e3) / 1e12
+        peak = fp64_peak_tflops(sm_mhz)
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"FP64 FMA pipe, {FP64_FLOP_PER_CLK_PER_SM:g} flop/clk/SM x 152 SMs x median "
+                               f"{sm_mhz:.0f} MHz"}
+    else:
+        achieved = dbytes / (dms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": pk["source"]}
+    roof["launches_in_region"] = dn
+    roof["avg_launch_us"] = dms * 1e3 / max(dn, 1)
+    roof["bytes_per_launch"] = dbytes / max(dn, 1)
+    share = {c: round(prof[c][0] / max(sum(v[0] for v in prof.values()), 1e-9), 4) for c in prof if prof[c][1]}
+
+    line = {
+        "metric": METRIC, "value": world * flops / sec_step / 1e12, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_step * 1e3, "seconds_per_step": sec_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if prec == "bf16" else ("f32" if prec == "fp32" else "f64"),
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": w["desc"], "N": N, "leaf": m, "levels": L, "rank": r,
+                   "rhs": k, "factor_precision": prec, "coupling_precision": "fp64",
+                   "residual_precision": "fp64", "solver": w["solver"], "tol": 1e-10,
+                   "flops_per_step": flops, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (D, U, V = %.1f GB FP64)" % (8.0 * (m * N + 2 * r * N * L) / 1e9)},
+        "mixed": {"iterations": iters, "relres_reported": relres, "relres_fp64_matvec": rel_true},
+        "fp64": fp64,
+        "e2e": e2e,
+        "roofline": roof,
+        "kernel_time_share": share,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, steps=1)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- oracle (CPU) arm
+def cpu_sample(w):
+    """Bounded sample of the workload for the CPU oracle: the same leaf size and
+    rank at N = 2^16 (or the full N if smaller)."""
+    N = min(w["N"], 1 << 16)
+    m = w["N"] >> w["L"]
+    L = max(1, int(round(math.log2(N // m))))
+    return N, L, w["r"], w["k"]
+
+
+def cpu_baseline(w, steps=1):
+    import numpy as np
+    from oracle import costs as oc
+    from oracle.hodlr import RecursiveHODLR
+    from synth import HodlrShape, gaussian_rhs, synthetic_hodlr, to_math
+    N, L, r, k = cpu_sample(w)
+    m = N >> L
+    D, U, V, g = synthetic_hodlr(HodlrShape(N, L, r), w["shift"], w["seed"])
+    B = gaussian_rhs(N, k, g)
+    Dm, Um, Vm, Bm = to_math(D, U, V, B)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        rec = RecursiveHODLR(Dm, Um, Vm, L)
+        rec.solve(Bm)
+        rec.slogdet()
+        times.append(time.perf_counter() - t0)
+    sec = statistics.mean(times)
+    flops = oc.loop_factor_flops(N, m, r, L) + oc.loop_solve_flops(N, m, r, L, k)
+    return {"value": flops / sec / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+            "seconds": sec,
+            "sample": f"FP64 recursive oracle (numpy/LAPACK) factor+solve+slogdet at N={N}, leaf {m}, rank {r}, "
+                      f"{k} RHS (same leaf and rank as the workload, N reduced to bound CPU time)"}
+
+
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return
+    times = []
+    for i in range(args.warmup + args.steps):
+        b = cpu_baseline(w, steps=1)
+        if i >= args.warmup:
+            times.append(b["seconds"])
+    sec = statistics.mean(times)
+    N, L, r, k = cpu_sample(w)
+    m = N >> L
+    from oracle import costs as oc
+    flops = oc.loop_factor_flops(N, m, r, L) + oc.loop_solve_flops(N, m, r, L, k)
+    val = flops / sec / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": w["desc"], "cpu_sample_N": N},
+            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": b["sample"]},
+            "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "native":
+        ap.error("--warmup must be >= 3")
+    w = WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, w, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    try:
+        run_native(args, w, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -61,7 +61,8 @@ typedef enum {
   HODLR_ERR_SINGULAR_LEAF = 4,     /* exact zero pivot in a leaf LU (where = leaf, detail = column) */
   HODLR_ERR_SINGULAR_COUPLING = 5, /* exact zero pivot in a 2r x 2r coupling LU (where = heap node, detail = column) */
   HODLR_ERR_NONFINITE = 6,         /* NaN or Inf in D (where = leaf) */
-  HODLR_ERR_NOT_CONVERGED = 7      /* refinement / GMRES hit its iteration limit */
+  HODLR_ERR_NOT_CONVERGED = 7,     /* refinement / GMRES hit its iteration limit */
+  HODLR_ERR_TIMEOUT = 8            /* a device-side wait gave up after its spin limit (where = child level) */
 } hodlr_status;
 
 /* Arithmetic of the factorization (not of the input, which is always FP64).
@@ -200,11 +201,20 @@ HODLR_API hodlr_status hodlr_gmres(hodlr_factor_t f, const double* D, const doub
  * per-kernel-class totals, copies up to n of them (milliseconds and launch
  * counts, in class order) and returns the number of classes;
  * hodlr_profile_name gives a class's name, hodlr_profile_reset clears the
- * totals. Profiling is process-wide and not thread-safe; it is off by default. */
+ * totals. hodlr_profile_work gives, per class, the algorithmic bytes and
+ * flops of the profiled launches (the operation's definition: every operand
+ * read once and every result written once, not the traffic the kernels
+ * actually cause). Profiling is process-wide and not thread-safe; it is off
+ * by default. */
 HODLR_API int64_t hodlr_launch_count(void);
+/* Tensor-core kernels (tcgen05/TMA) for the BF16 factor's panel products:
+ * on by default; off selects the CUDA-core kernels (same results up to FP32
+ * summation order). Process-wide; for tests and benchmarks. */
+HODLR_API void hodlr_tc_enable(int32_t on);
 HODLR_API void hodlr_profile_enable(int32_t on);
 HODLR_API void hodlr_profile_reset(void);
 HODLR_API int32_t hodlr_profile_read(double* ms, int64_t* launches, int32_t n);
+HODLR_API int32_t hodlr_profile_work(double* bytes, double* flops, int32_t n);
 HODLR_API const char* hodlr_profile_name(int32_t cls);
 
 #ifdef __cplusplus

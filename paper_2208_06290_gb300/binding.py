@@ -29,6 +29,7 @@ HODLR_ERR_SINGULAR_LEAF = 4
 HODLR_ERR_SINGULAR_COUPLING = 5
 HODLR_ERR_NONFINITE = 6
 HODLR_ERR_NOT_CONVERGED = 7
+HODLR_ERR_TIMEOUT = 8
 
 PREC = {"fp64": 0, "fp32": 1, "bf16": 3}
 
@@ -37,7 +38,7 @@ EXPORTED = (
     "hodlr_solve_workspace_size", "hodlr_solve", "hodlr_solve_adjoint", "hodlr_logdet",
     "hodlr_matvec_workspace_size", "hodlr_matvec", "hodlr_refine_workspace_size", "hodlr_solve_refined",
     "hodlr_gmres", "hodlr_launch_count", "hodlr_profile_enable", "hodlr_profile_reset", "hodlr_profile_read",
-    "hodlr_profile_name",
+    "hodlr_profile_name", "hodlr_profile_work", "hodlr_tc_enable",
 )
 
 
@@ -76,6 +77,8 @@ _SIGS = {
     "hodlr_profile_reset": ([], None),
     "hodlr_profile_read": ([_c.POINTER(_dbl), _c.POINTER(_i64), _i32], _i32),
     "hodlr_profile_name": ([_i32], _c.c_char_p),
+    "hodlr_profile_work": ([_c.POINTER(_dbl), _c.POINTER(_dbl), _i32], _i32),
+    "hodlr_tc_enable": ([_i32], None),
 }
 
 
@@ -302,5 +305,19 @@ def hodlr_profile_read() -> dict:
     return {hodlr_profile_name(i): (ms[i], cnt[i]) for i in range(min(k, n))}
 
 
+def hodlr_profile_work() -> dict:
+    """{kernel class: (algorithmic bytes, algorithmic flops)} of the profiled launches."""
+    n = 16
+    by = (ctypes.c_double * n)()
+    fl = (ctypes.c_double * n)()
+    k = _LIB.hodlr_profile_work(by, fl, n)
+    return {hodlr_profile_name(i): (by[i], fl[i]) for i in range(min(k, n))}
+
+
 def hodlr_profile_name(i: int) -> str:
     return _LIB.hodlr_profile_name(i).decode()
+
+
+def hodlr_tc_enable(on: bool = True) -> None:
+    """Select tensor-core (on, default) or CUDA-core kernels for the BF16 factor."""
+    _LIB.hodlr_tc_enable(1 if on else 0)

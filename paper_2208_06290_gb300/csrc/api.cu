@@ -6,6 +6,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "hodlr_internal.cuh"
@@ -14,23 +15,29 @@ namespace hodlr {
 
 cudaError_t launch_coupling_factor_apply(const Factor& F, int c, cudaStream_t s);
 
+bool g_use_tc = true;
+
 // ---------------------------------------------------------------- launch accounting
 namespace {
 std::atomic<long long> g_launches{0};
 std::atomic<bool> g_prof{false};
 thread_local int t_bracket = 0;
+thread_local double t_bytes = 0.0, t_flops = 0.0;
 struct PendingBracket {
   int cls;
   cudaEvent_t a, b;
   int n;
+  double bytes, flops;
 };
 std::mutex g_mu;
 std::vector<PendingBracket> g_pending;
 std::vector<cudaEvent_t> g_pool;
 double g_ms[KC_COUNT];
 long long g_n[KC_COUNT];
+double g_bytes[KC_COUNT], g_flops[KC_COUNT];
 const char* kClassName[KC_COUNT] = {"leaf_lu", "leaf_solve", "project", "coupling", "coupling_apply",
-                                    "update", "reduce_chunks", "leaf_matvec", "vector", "logdet"};
+                                    "update", "reduce_chunks", "leaf_matvec", "vector", "logdet",
+                                    "project_tc", "update_tc"};
 
 cudaEvent_t pool_get() {
   std::lock_guard<std::mutex> g(g_mu);
@@ -50,9 +57,16 @@ void note_launches(int n) {
   t_bracket += n;
 }
 
+void note_work(double bytes, double flops) {
+  t_bytes += bytes;
+  t_flops += flops;
+}
+
 ProfScope::ProfScope(int c, cudaStream_t st) : cls(c), s(st), a(nullptr) {
   if (!g_prof.load(std::memory_order_relaxed)) return;
   t_bracket = 0;
+  t_bytes = 0.0;
+  t_flops = 0.0;
   cudaEvent_t e = pool_get();
   if (e && cudaEventRecord(e, s) == cudaSuccess) a = e;
 }
@@ -68,7 +82,7 @@ ProfScope::~ProfScope() {
   cudaEvent_t e1 = pool_get();
   if (!e1 || cudaEventRecord(e1, s) != cudaSuccess) return;
   std::lock_guard<std::mutex> g(g_mu);
-  g_pending.push_back({cls, e0, e1, t_bracket});
+  g_pending.push_back({cls, e0, e1, t_bracket, t_bytes, t_flops});
 }
 
 namespace {
@@ -151,7 +165,14 @@ hodlr_status factor_levels(Factor& F, cudaStream_t s) {
   for (int c = d.L; c >= 1; --c) {
     const int rc = d.r * c;
     const int anc = d.r * (c - 1);
-    HODLR_CUDA(launch_project<TP, TP>(d.N, d.r, c, Vp, F.ldvp, c - 1, Y, d.N, rc, F.P, 0, s));
+    if constexpr (std::is_same<TP, __nv_bfloat16>::value) {
+      if (g_use_tc && project_tc_supported(d.N, d.r, c))
+        HODLR_CUDA(launch_project_tc(d.N, d.r, d.L, c, Vp, F.ldvp, Y, F.P, F.status, s));
+      else
+        HODLR_CUDA(launch_project<TP, TP>(d.N, d.r, c, Vp, F.ldvp, c - 1, Y, d.N, rc, F.P, 0, s));
+    } else {
+      HODLR_CUDA(launch_project<TP, TP>(d.N, d.r, c, Vp, F.ldvp, c - 1, Y, d.N, rc, F.P, 0, s));
+    }
     HODLR_CUDA(launch_coupling_factor(F, c, s));
     if (anc > 0) {
       HODLR_CUDA(launch_coupling_factor_apply(F, c, s));
@@ -251,6 +272,7 @@ const char* hodlr_strerror(hodlr_status s) {
     case HODLR_ERR_SINGULAR_COUPLING: return "singular coupling matrix";
     case HODLR_ERR_NONFINITE: return "non-finite input";
     case HODLR_ERR_NOT_CONVERGED: return "iteration did not converge";
+    case HODLR_ERR_TIMEOUT: return "device-side wait timed out";
   }
   return "unknown status";
 }
@@ -604,6 +626,8 @@ hodlr_status hodlr_gmres(hodlr_factor_t f, const double* D, const double* U, con
 
 int64_t hodlr_launch_count(void) { return g_launches.load(); }
 
+void hodlr_tc_enable(int32_t on) { g_use_tc = on != 0; }
+
 void hodlr_profile_enable(int32_t on) { g_prof.store(on != 0); }
 
 void hodlr_profile_reset(void) {
@@ -611,7 +635,19 @@ void hodlr_profile_reset(void) {
   for (int i = 0; i < KC_COUNT; ++i) {
     g_ms[i] = 0.0;
     g_n[i] = 0;
+    g_bytes[i] = 0.0;
+    g_flops[i] = 0.0;
   }
+}
+
+int32_t hodlr_profile_work(double* bytes, double* flops, int32_t n) {
+  hodlr_profile_read(nullptr, nullptr, 0);
+  std::lock_guard<std::mutex> g(g_mu);
+  for (int i = 0; i < n && i < KC_COUNT; ++i) {
+    if (bytes) bytes[i] = g_bytes[i];
+    if (flops) flops[i] = g_flops[i];
+  }
+  return KC_COUNT;
 }
 
 int32_t hodlr_profile_read(double* ms, int64_t* launches, int32_t n) {
@@ -622,6 +658,8 @@ int32_t hodlr_profile_read(double* ms, int64_t* launches, int32_t n) {
     if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
       g_ms[p.cls] += t;
       g_n[p.cls] += p.n;
+      g_bytes[p.cls] += p.bytes;
+      g_flops[p.cls] += p.flops;
     }
     g_pool.push_back(p.a);
     g_pool.push_back(p.b);

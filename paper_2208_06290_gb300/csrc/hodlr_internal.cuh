@@ -48,7 +48,7 @@ __device__ __forceinline__ TD conv(TS s) {
 // are split into row chunks of ch(c) rows, n_c halved until it is at most
 // kChunkMax (so ch divides n_c, whatever m is); chunk q covers rows
 // [q*ch, (q+1)*ch) and belongs to node q / (n_c / ch).
-constexpr int64_t kChunkMax = 4096;
+constexpr int64_t kChunkMax = 1024;
 
 __host__ __device__ inline int64_t node_rows(int64_t N, int c) { return N >> c; }
 __host__ __device__ inline int64_t chunk_rows(int64_t N, int c) {
@@ -95,12 +95,16 @@ size_t factor_workspace_bytes(const hodlr_desc& d, hodlr_prec prec);
 // ---------------------------------------------------------------- launch accounting
 enum KernelClass {
   KC_LEAF_LU = 0, KC_LEAF_SOLVE, KC_PROJECT, KC_COUPLING, KC_COUPLING_APPLY, KC_UPDATE, KC_REDUCE,
-  KC_LEAF_MATVEC, KC_VECTOR, KC_LOGDET, KC_COUNT
+  KC_LEAF_MATVEC, KC_VECTOR, KC_LOGDET, KC_PROJECT_TC, KC_UPDATE_TC, KC_COUNT
 };
 // Called by every launcher right after its kernel launch(es): counts them and,
 // when profiling is on, records the closing event of the bracket that
 // prof_begin opened on the same stream.
 void note_launches(int n);
+// Algorithmic bytes moved and flops done by the launch(es) of the current
+// bracket (the kernel's definition, not its actual traffic); summed per class
+// while profiling is on.
+void note_work(double bytes, double flops);
 struct ProfScope {
   int cls;
   cudaStream_t s;
@@ -159,5 +163,13 @@ cudaError_t launch_multidot(int64_t N, int k, const double* X, int64_t ldx, cons
 cudaError_t launch_gemv_sub(int64_t N, int k, const double* X, int64_t ldx, const double* h, double* w,
                             cudaStream_t s);
 cudaError_t launch_logdet_reduce(const Factor& F, cudaStream_t s);
+
+// Tensor-core (tcgen05 + TMA) projection of the BF16 factor; supported when
+// r is 32 or 64 and the level's row chunks are multiples of 64 rows.
+bool project_tc_supported(int64_t N, int r, int c);
+cudaError_t launch_project_tc(int64_t N, int r, int L, int c, const __nv_bfloat16* Vp, int64_t ldv,
+                              const __nv_bfloat16* Y, double* P, DevStatus* st, cudaStream_t s);
+// Set by hodlr_tc_enable (process-wide; default on).
+extern bool g_use_tc;
 
 }  // namespace hodlr

@@ -129,6 +129,7 @@ static cudaError_t leaf_lu_dispatch(const Factor& F, const double* D, cudaStream
   const size_t aux = (size_t)((m + 3) & ~3) * sizeof(int) + (size_t)m * sizeof(TL) + 16;
   const size_t full = (size_t)m * m * sizeof(TL) + aux;
   TL* lu = static_cast<TL*>(F.lu);
+  note_work((8.0 + sizeof(TL)) * nleaf * m * m + 4.0 * nleaf * m, 2.0 / 3.0 * m * m * (double)m * nleaf);
   if (full <= 160 * 1024) {
     cudaFuncSetAttribute(leaf_lu_kernel<TL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)full);
     { leaf_lu_kernel<TL, true><<<nleaf, 256, full, s>>>(m, D, lu, F.perm, F.leaf_ld, F.status); note_launches(1); }
@@ -287,16 +288,30 @@ __global__ void __launch_bounds__(256) leaf_solve_kernel(int m, const TL* __rest
   }
 }
 
-template <typename TL, typename TIN, typename TOUT, int RPL>
-static cudaError_t leaf_solve_rpl(const Factor& F, const TIN* in, int64_t ldin, TOUT* out, int64_t ldout,
+template <typename TL, typename TIN, typename TOUT, int RPL, int CPW>
+static cudaError_t leaf_solve_cpw(const Factor& F, const TIN* in, int64_t ldin, TOUT* out, int64_t ldout,
                                   int ncols, int trans, cudaStream_t s) {
-  constexpr int CPW = sizeof(TL) == 8 ? 4 : 8;
   const int nleaf = 1 << F.d.L;
   const int cols_per_cta = 8 * CPW;
+  const double Nd = (double)nleaf * F.d.m;
+  note_work((sizeof(TIN) + sizeof(TOUT)) * Nd * ncols + sizeof(TL) * Nd * F.d.m + 4.0 * Nd,
+            2.0 * F.d.m * Nd * ncols);
   dim3 grid(nleaf, (ncols + cols_per_cta - 1) / cols_per_cta);
   { leaf_solve_kernel<TL, TIN, TOUT, RPL, CPW><<<grid, 256, 0, s>>>(
       F.d.m, static_cast<const TL*>(F.lu), F.perm, in, ldin, out, ldout, ncols, trans); note_launches(1); }
   return cudaGetLastError();
+}
+
+// Columns per warp: 4 (FP64) or 8 (FP32) registers' worth, fewer when the
+// right-hand side is narrower, so no FLOPs go to padding columns.
+template <typename TL, typename TIN, typename TOUT, int RPL>
+static cudaError_t leaf_solve_rpl(const Factor& F, const TIN* in, int64_t ldin, TOUT* out, int64_t ldout,
+                                  int ncols, int trans, cudaStream_t s) {
+  constexpr int CPWMAX = sizeof(TL) == 8 ? 4 : 8;
+  if (ncols == 1) return leaf_solve_cpw<TL, TIN, TOUT, RPL, 1>(F, in, ldin, out, ldout, ncols, trans, s);
+  if (ncols == 2 || CPWMAX == 2) return leaf_solve_cpw<TL, TIN, TOUT, RPL, 2>(F, in, ldin, out, ldout, ncols, trans, s);
+  if (ncols <= 4 || CPWMAX == 4) return leaf_solve_cpw<TL, TIN, TOUT, RPL, 4>(F, in, ldin, out, ldout, ncols, trans, s);
+  return leaf_solve_cpw<TL, TIN, TOUT, RPL, CPWMAX>(F, in, ldin, out, ldout, ncols, trans, s);
 }
 
 template <typename TL, typename TIN, typename TOUT>
@@ -329,34 +344,47 @@ template cudaError_t launch_leaf_solve<float, float>(const Factor&, const float*
 
 // ---------------------------------------------------------------------------
 // Leaf part of the FP64 matvec: Y_b = D_b X_b. Thread i of the CTA owns row i
-// of the leaf; X_b columns are staged in shared memory 32 at a time.
+// of the leaf; KC columns of X_b are staged in shared memory per CTA.
+template <int KC>
 __global__ void __launch_bounds__(256) leaf_matvec_kernel(int m, const double* __restrict__ D,
                                                           const double* __restrict__ X, int64_t ldx,
                                                           double* __restrict__ Y, int64_t ldy, int k) {
-  extern __shared__ double sx[];  // m x 32, [j][c]
+  extern __shared__ double sx[];  // m x KC, [j][c]
   const int b = blockIdx.x;
-  const int c0 = blockIdx.y * 32;
-  const int kc = min(32, k - c0);
+  const int c0 = blockIdx.y * KC;
+  const int kc = min(KC, k - c0);
   const double* Db = D + (size_t)b * m * m;
   const int64_t row0 = (int64_t)b * m;
-  for (int e = threadIdx.x; e < m * 32; e += blockDim.x) {
+  for (int e = threadIdx.x; e < m * KC; e += blockDim.x) {
     const int j = e % m, c = e / m;
-    sx[j * 32 + c] = (c < kc) ? X[(int64_t)(c0 + c) * ldx + row0 + j] : 0.0;
+    sx[j * KC + c] = (c < kc) ? X[(int64_t)(c0 + c) * ldx + row0 + j] : 0.0;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    double acc[32];
+    double acc[KC];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) acc[c] = 0.0;
+    for (int c = 0; c < KC; ++c) acc[c] = 0.0;
     for (int j = 0; j < m; ++j) {
       const double d = Db[(size_t)j * m + i];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) acc[c] += d * sx[j * 32 + c];
+      for (int c = 0; c < KC; ++c) acc[c] += d * sx[j * KC + c];
     }
 #pragma unroll
-    for (int c = 0; c < 32; ++c)
+    for (int c = 0; c < KC; ++c)
       if (c < kc) Y[(int64_t)(c0 + c) * ldy + row0 + i] = acc[c];
   }
+}
+
+template <int KC>
+static void leaf_matvec_go(const hodlr_desc& d, const double* D, const double* X, int64_t ldx, double* Y,
+                           int64_t ldy, int k, cudaStream_t s) {
+  const int m = d.m;
+  const int nleaf = 1 << d.L;
+  const int threads = m >= 256 ? 256 : ((m + 31) / 32) * 32;
+  dim3 grid(nleaf, (k + KC - 1) / KC);
+  const size_t sm = (size_t)m * KC * sizeof(double);
+  if (sm > 48 * 1024) cudaFuncSetAttribute(leaf_matvec_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  { leaf_matvec_kernel<KC><<<grid, threads, sm, s>>>(m, D, X, ldx, Y, ldy, k); note_launches(1); }
 }
 
 cudaError_t launch_leaf_matvec(const hodlr_desc& d, const double* D, const double* X, int64_t ldx, double* Y,
@@ -364,11 +392,12 @@ cudaError_t launch_leaf_matvec(const hodlr_desc& d, const double* D, const doubl
   ProfScope prof_(KC_LEAF_MATVEC, s);
   const int m = d.m;
   const int nleaf = 1 << d.L;
-  const int threads = m >= 256 ? 256 : ((m + 31) / 32) * 32;
-  dim3 grid(nleaf, (k + 31) / 32);
-  const size_t sm = (size_t)m * 32 * sizeof(double);
-  cudaFuncSetAttribute(leaf_matvec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  { leaf_matvec_kernel<<<grid, threads, sm, s>>>(m, D, X, ldx, Y, ldy, k); note_launches(1); }
+  note_work(8.0 * ((double)m * m * nleaf + 2.0 * (double)d.N * k), 2.0 * m * (double)d.N * k);
+  if (k == 1) leaf_matvec_go<1>(d, D, X, ldx, Y, ldy, k, s);
+  else if (k <= 2) leaf_matvec_go<2>(d, D, X, ldx, Y, ldy, k, s);
+  else if (k <= 4) leaf_matvec_go<4>(d, D, X, ldx, Y, ldy, k, s);
+  else if (k <= 8) leaf_matvec_go<8>(d, D, X, ldx, Y, ldy, k, s);
+  else leaf_matvec_go<32>(d, D, X, ldx, Y, ldy, k, s);
   return cudaGetLastError();
 }
 

@@ -68,6 +68,60 @@ __global__ void __launch_bounds__(256) project_kernel(int64_t N, int r, int c, c
     }
 }
 
+// Skinny variant for ncols <= 8 (solves and residuals with few right-hand
+// sides): thread t streams rows row0+t, row0+t+256, ... of the chunk and keeps
+// a 16 x KC register tile for basis columns j0..j0+15; the 256 partial tiles
+// are reduced by warp shuffles and then across warps in a fixed order.
+template <typename TB, typename TR, typename TA, int KC>
+__global__ void __launch_bounds__(256) project_skinny_kernel(int64_t N, int r, int c, const TB* __restrict__ Bas,
+                                                             int64_t ldb, int bas_block, const TR* __restrict__ R,
+                                                             int64_t ldr, int ncols, double* __restrict__ P) {
+  __shared__ TA sred[8][16 * KC];
+  const int64_t ch = chunk_rows(N, c);
+  const int64_t q = blockIdx.x;
+  const int64_t row0 = q * ch;
+  const int j0 = blockIdx.y * 16;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int jn = (r - j0) < 16 ? (r - j0) : 16;
+  const TB* B0 = Bas + ((int64_t)bas_block * r + j0) * ldb + row0;
+  const TR* R0 = R + row0;
+  TA acc[16][KC];
+#pragma unroll
+  for (int jj = 0; jj < 16; ++jj)
+#pragma unroll
+    for (int cc = 0; cc < KC; ++cc) acc[jj][cc] = TA(0);
+  for (int64_t i = tid; i < ch; i += 256) {
+    TA xv[KC];
+#pragma unroll
+    for (int cc = 0; cc < KC; ++cc) xv[cc] = cc < ncols ? conv<TA>(R0[(int64_t)cc * ldr + i]) : TA(0);
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) {
+      if (jj < jn) {
+        const TA b = conv<TA>(B0[(int64_t)jj * ldb + i]);
+#pragma unroll
+        for (int cc = 0; cc < KC; ++cc) acc[jj][cc] += b * xv[cc];
+      }
+    }
+  }
+#pragma unroll
+  for (int jj = 0; jj < 16; ++jj)
+#pragma unroll
+    for (int cc = 0; cc < KC; ++cc) {
+      TA v = acc[jj][cc];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (lane == 0) sred[warp][jj * KC + cc] = v;
+    }
+  __syncthreads();
+  if (tid < 16 * KC) {
+    const int jj = tid / KC, cc = tid % KC;
+    TA v = TA(0);
+#pragma unroll
+    for (int w = 0; w < 8; ++w) v += sred[w][tid];
+    if (jj < jn && cc < ncols) P[(size_t)q * r * ncols + (size_t)cc * r + j0 + jj] = (double)v;
+  }
+}
+
 template <typename TB, typename TR>
 cudaError_t launch_project(int64_t N, int r, int c, const TB* Bas, int64_t ldb, int bas_block, const TR* R,
                            int64_t ldr, int ncols, double* P, int acc_fp64, cudaStream_t s) {
@@ -75,6 +129,20 @@ cudaError_t launch_project(int64_t N, int r, int c, const TB* Bas, int64_t ldb, 
   if (ncols <= 0) return cudaSuccess;
   dim3 grid((unsigned)num_chunks(N, c), (ncols + 63) / 64);
   using TA = typename AccOf<TR>::type;
+  note_work(sizeof(TB) * (double)N * r + sizeof(TR) * (double)N * ncols + 8.0 * num_chunks(N, c) * r * ncols,
+            2.0 * N * r * (double)ncols);
+  if (ncols <= 8) {
+    dim3 g2((unsigned)num_chunks(N, c), (r + 15) / 16);
+    if (ncols == 1)
+      { project_skinny_kernel<TB, TR, TA, 1><<<g2, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, ldr, ncols, P); note_launches(1); }
+    else if (ncols <= 2)
+      { project_skinny_kernel<TB, TR, TA, 2><<<g2, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, ldr, ncols, P); note_launches(1); }
+    else if (ncols <= 4)
+      { project_skinny_kernel<TB, TR, TA, 4><<<g2, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, ldr, ncols, P); note_launches(1); }
+    else
+      { project_skinny_kernel<TB, TR, TA, 8><<<g2, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, ldr, ncols, P); note_launches(1); }
+    return cudaGetLastError();
+  }
   if (r <= 16)
     { project_kernel<TB, TR, TA, 16><<<grid, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, ldr, ncols, P); note_launches(1); }
   else if (r <= 32)
@@ -154,6 +222,45 @@ __global__ void __launch_bounds__(256) update_kernel(int64_t N, int r, int c, co
   }
 }
 
+// Skinny variant for ncols <= 8: one thread per row, W(node') (times alpha)
+// staged in shared memory and read by broadcast; tiles of 256 rows laid out
+// node by node.
+template <typename TB, typename TR, typename TA, int KC>
+__global__ void __launch_bounds__(256) update_skinny_kernel(int64_t N, int r, int c, const TB* __restrict__ Bas,
+                                                            int64_t ldb, int bas_block, TR* __restrict__ R,
+                                                            int64_t ldr, int ncols, const double* __restrict__ Wbase,
+                                                            int64_t wstride, int swap_sibling, double alpha) {
+  __shared__ TA sW[64][KC];
+  const int64_t n = N >> c;
+  const int64_t tpn = (n + 255) / 256;
+  const int64_t node = blockIdx.x / tpn;
+  const int64_t t0 = (blockIdx.x % tpn) * 256;
+  const double* W = Wbase + (node ^ swap_sibling) * wstride;
+  for (int e = threadIdx.x; e < r * KC; e += 256) {
+    const int j = e / KC, cc = e % KC;
+    sW[j][cc] = cc < ncols ? conv<TA>(alpha * W[(size_t)cc * r + j]) : TA(0);
+  }
+  __syncthreads();
+  const int64_t i = t0 + threadIdx.x;
+  if (i >= n) return;
+  const int64_t row = node * n + i;
+  const TB* B0 = Bas + (int64_t)bas_block * r * ldb + row;
+  TA acc[KC];
+#pragma unroll
+  for (int cc = 0; cc < KC; ++cc) acc[cc] = TA(0);
+  for (int j = 0; j < r; ++j) {
+    const TA b = conv<TA>(B0[(int64_t)j * ldb]);
+#pragma unroll
+    for (int cc = 0; cc < KC; ++cc) acc[cc] += b * sW[j][cc];
+  }
+#pragma unroll
+  for (int cc = 0; cc < KC; ++cc)
+    if (cc < ncols) {
+      TR* p = R + (int64_t)cc * ldr + row;
+      *p = conv<TR>(conv<TA>(*p) + acc[cc]);
+    }
+}
+
 template <typename TB, typename TR>
 cudaError_t launch_update(int64_t N, int r, int c, const TB* Bas, int64_t ldb, int bas_block, TR* R, int64_t ldr,
                           int ncols, const double* Wbase, int64_t wstride, int swap_sibling, double alpha,
@@ -163,6 +270,22 @@ cudaError_t launch_update(int64_t N, int r, int c, const TB* Bas, int64_t ldb, i
   const int64_t n = N >> c;
   const int64_t tpn = (n + 63) / 64;
   dim3 grid((unsigned)(((int64_t)1 << c) * tpn), (ncols + 63) / 64);
+  note_work(sizeof(TB) * (double)N * r + 2.0 * sizeof(TR) * (double)N * ncols + 8.0 * (double)(1ll << c) * r * ncols,
+            2.0 * N * r * (double)ncols);
+  if (ncols <= 8) {
+    using TA2 = typename AccOf<TR>::type;
+    const int64_t tpn2 = (n + 255) / 256;
+    const unsigned g2 = (unsigned)(((int64_t)1 << c) * tpn2);
+    if (ncols == 1)
+      { update_skinny_kernel<TB, TR, TA2, 1><<<g2, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, ldr, ncols, Wbase, wstride, swap_sibling, alpha); note_launches(1); }
+    else if (ncols <= 2)
+      { update_skinny_kernel<TB, TR, TA2, 2><<<g2, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, ldr, ncols, Wbase, wstride, swap_sibling, alpha); note_launches(1); }
+    else if (ncols <= 4)
+      { update_skinny_kernel<TB, TR, TA2, 4><<<g2, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, ldr, ncols, Wbase, wstride, swap_sibling, alpha); note_launches(1); }
+    else
+      { update_skinny_kernel<TB, TR, TA2, 8><<<g2, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, ldr, ncols, Wbase, wstride, swap_sibling, alpha); note_launches(1); }
+    return cudaGetLastError();
+  }
   using TA = typename AccOf<TR>::type;
   (void)acc_fp64;
   if (r <= 16)
@@ -298,6 +421,7 @@ cudaError_t launch_coupling_factor(const Factor& F, int c, cudaStream_t s) {
   const int64_t parents = (int64_t)1 << (c - 1);
   const size_t sm = (size_t)n * n * sizeof(double) + (size_t)((n + 1) / 2) * sizeof(double) + n * sizeof(double);
   cudaFuncSetAttribute(coupling_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  note_work(8.0 * num_chunks(F.d.N, c) * r * r + 8.0 * parents * n * n, parents * 2.0 / 3.0 * n * n * (double)n);
   { coupling_factor_kernel<<<(unsigned)parents, 256, sm, s>>>(F.d.N, r, c, F.P, F.K + F.Koff[c] * n * n,
                                                              F.node_ld + 2 * F.Koff[c], F.status,
                                                              (int64_t)1 << (c - 1)); note_launches(1); }
@@ -383,6 +507,9 @@ static cudaError_t coupling_apply(int64_t N, int r, int c, double* P, int64_t sw
   if (nrhs <= 0) return cudaSuccess;
   dim3 grid(1u << (c - 1), (nrhs + 31) / 32);
   const int n = 2 * r;
+  const double parents = (double)(1ll << (c - 1));
+  note_work(8.0 * ((double)num_chunks(N, c) * r * nrhs + parents * n * n + 2.0 * parents * r * nrhs),
+            parents * 2.0 * n * n * (double)nrhs);
   const size_t sm = (size_t)2 * n * 33 * sizeof(TA);
   if (n <= 32) {
     { coupling_apply_kernel<TA, 4><<<grid, 256, sm, s>>>(N, r, c, P, sw, nrhs, Kinv, first_is_beta, trans); note_launches(1); }
@@ -405,12 +532,82 @@ cudaError_t launch_coupling_factor_apply(const Factor& F, int c, cudaStream_t s)
   return coupling_apply<float>(F.d.N, r, c, F.P, (int64_t)r * c, anc, Kc, 1, 0, s);
 }
 
+// Skinny coupling solve (k <= 8 right-hand sides), FP64: n = 2r threads per
+// parent, thread i gathers row i of the right-hand side (sum of chunk
+// partials) and then forms row i of Kinv * rhs (Kinv read column by column,
+// coalesced) or of Kinv^T * rhs.
+template <int KC>
+__global__ void __launch_bounds__(256) coupling_solve_skinny_kernel(int64_t N, int r, int c, double* P, int k,
+                                                                    const double* __restrict__ Kinv,
+                                                                    int first_is_beta, int trans) {
+  __shared__ double sRhs[256 * KC];
+  const int n = 2 * r;
+  const int ppc = 256 / n;  // parents per CTA
+  const int slot_in_cta = threadIdx.x / n;
+  const int i = threadIdx.x % n;
+  const int64_t parents = (int64_t)1 << (c - 1);
+  const int64_t j = (int64_t)blockIdx.x * ppc + slot_in_cta;
+  const bool active = slot_in_cta < ppc && j < parents;
+  const int64_t cpn = chunks_per_node(N, c);
+  const size_t slot = (size_t)r * k;
+  const int64_t qa = 2 * j * cpn, qb = (2 * j + 1) * cpn;
+  double* rhs = sRhs + slot_in_cta * n * KC;
+  if (active) {
+    const int64_t q0 = (i < r) == (first_is_beta != 0) ? qb : qa;
+    const int row = i < r ? i : i - r;
+#pragma unroll
+    for (int cc = 0; cc < KC; ++cc) {
+      double acc = 0.0;
+      if (cc < k)
+        for (int64_t q = 0; q < cpn; ++q) acc += P[(q0 + q) * slot + (size_t)cc * r + row];
+      rhs[i * KC + cc] = acc;
+    }
+  }
+  __syncthreads();
+  double acc[KC];
+#pragma unroll
+  for (int cc = 0; cc < KC; ++cc) acc[cc] = 0.0;
+  if (active) {
+    const double* Kj = Kinv + (size_t)j * n * n;
+    for (int jj = 0; jj < n; ++jj) {
+      const double kv = trans ? Kj[(size_t)i * n + jj] : Kj[(size_t)jj * n + i];
+#pragma unroll
+      for (int cc = 0; cc < KC; ++cc) acc[cc] += kv * rhs[jj * KC + cc];
+    }
+  }
+  __syncthreads();  // all reads of this CTA's partials done before the writes
+  if (!active) return;
+  const int64_t q = i < r ? qa : qb;
+  const int row = i < r ? i : i - r;
+#pragma unroll
+  for (int cc = 0; cc < KC; ++cc)
+    if (cc < k) P[q * slot + (size_t)cc * r + row] = acc[cc];
+}
+
+template <int KC>
+static cudaError_t coupling_solve_skinny(int64_t N, int r, int c, double* P, int k, const double* Kinv,
+                                         int first_is_beta, int trans, cudaStream_t s) {
+  const int n = 2 * r;
+  const int ppc = 256 / n;
+  const int64_t parents = (int64_t)1 << (c - 1);
+  const unsigned grid = (unsigned)((parents + ppc - 1) / ppc);
+  note_work(8.0 * ((double)num_chunks(N, c) * r * k + parents * n * n + 2.0 * parents * r * k),
+            parents * 2.0 * n * n * (double)k);
+  { coupling_solve_skinny_kernel<KC><<<grid, 256, 0, s>>>(N, r, c, P, k, Kinv, first_is_beta, trans); note_launches(1); }
+  return cudaGetLastError();
+}
+
 // Solve / adjoint: w = Kinv [s_beta; s_alpha] or t = Kinv^T [s_alpha; s_beta], FP64.
 cudaError_t launch_coupling_solve(const Factor& F, int c, double* P, int k, int trans, cudaStream_t s) {
   ProfScope prof_(KC_COUPLING_APPLY, s);
   const int r = F.d.r;
   const double* Kc = F.K + F.Koff[c] * 4 * r * r;
-  return coupling_apply<double>(F.d.N, r, c, P, k, k, Kc, trans ? 0 : 1, trans, s);
+  const int fib = trans ? 0 : 1;
+  if (k == 1) return coupling_solve_skinny<1>(F.d.N, r, c, P, k, Kc, fib, trans, s);
+  if (k <= 2) return coupling_solve_skinny<2>(F.d.N, r, c, P, k, Kc, fib, trans, s);
+  if (k <= 4) return coupling_solve_skinny<4>(F.d.N, r, c, P, k, Kc, fib, trans, s);
+  if (k <= 8) return coupling_solve_skinny<8>(F.d.N, r, c, P, k, Kc, fib, trans, s);
+  return coupling_apply<double>(F.d.N, r, c, P, k, k, Kc, fib, trans, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -432,6 +629,7 @@ cudaError_t launch_reduce_chunks(int64_t N, int r, int c, double* P, int ncols, 
   if (chunks_per_node(N, c) == 1) return cudaSuccess;
   const size_t slot = (size_t)r * ncols;
   dim3 grid(1u << c, (unsigned)((slot + 255) / 256));
+  note_work(8.0 * ((double)num_chunks(N, c) + (double)(1ll << c)) * slot, (double)num_chunks(N, c) * slot);
   { reduce_chunks_kernel<<<grid, 256, 0, s>>>(N, r, c, P, ncols); note_launches(1); }
   return cudaGetLastError();
 }
@@ -472,6 +670,7 @@ __global__ void logdet_reduce_kernel(const double* leaf_ld, int64_t nleaf, const
 cudaError_t launch_logdet_reduce(const Factor& F, cudaStream_t s) {
   ProfScope prof_(KC_LOGDET, s);
   const int64_t nleaf = (int64_t)1 << F.d.L;
+  note_work(32.0 * nleaf, 2.0 * nleaf);
   { logdet_reduce_kernel<<<1, 256, 0, s>>>(F.leaf_ld, nleaf, F.node_ld, nleaf - 1, F.ld_out); note_launches(1); }
   return cudaGetLastError();
 }

@@ -22,6 +22,7 @@ template <typename TD, typename TS>
 cudaError_t launch_copy_cols(int64_t N, int k, const TS* src, int64_t lds, TD* dst, int64_t ldd, cudaStream_t s) {
   ProfScope prof_(KC_VECTOR, s);
   if (k <= 0) return cudaSuccess;
+  note_work((sizeof(TS) + sizeof(TD)) * (double)N * k, 0.0);
   { copy_cols_kernel<TD, TS><<<dim3(grid_for(N), k), 256, 0, s>>>(N, k, src, lds, dst, ldd); note_launches(1); }
   return cudaGetLastError();
 }
@@ -47,6 +48,7 @@ cudaError_t launch_axpby_cols(int64_t N, int k, double a, const double* x, int64
                               int64_t ldy, cudaStream_t s) {
   ProfScope prof_(KC_VECTOR, s);
   if (k <= 0) return cudaSuccess;
+  note_work(24.0 * N * k, 3.0 * N * k);
   { axpby_kernel<<<dim3(grid_for(N), k), 256, 0, s>>>(N, a, x, ldx, b, y, ldy); note_launches(1); }
   return cudaGetLastError();
 }
@@ -100,6 +102,7 @@ static cudaError_t dots_impl(int64_t N, int k, const double* x, int64_t ldx, con
   if (k <= 0) return cudaSuccess;
   int64_t nb = (N + 255) / 256;
   if (nb > kDotBlocks) nb = kDotBlocks;
+  note_work(mode == 0 ? 16.0 * N * k : 8.0 * N * (k + 1.0), 2.0 * N * k);
   { dot_stage1<<<dim3((unsigned)nb, k), 256, 0, s>>>(N, x, ldx, y, ldy, mode, scratch); note_launches(1); }
   { dot_stage2<<<k, 256, 0, s>>>(scratch, (int)nb, out); note_launches(1); }
   return cudaGetLastError();
@@ -131,6 +134,7 @@ cudaError_t launch_gemv_sub(int64_t N, int k, const double* X, int64_t ldx, cons
                             cudaStream_t s) {
   ProfScope prof_(KC_VECTOR, s);
   if (k <= 0) return cudaSuccess;
+  note_work(8.0 * N * (k + 2.0), 2.0 * N * k);
   { gemv_sub_kernel<<<grid_for(N), 256, 0, s>>>(N, k, X, ldx, h, w); note_launches(1); }
   return cudaGetLastError();
 }

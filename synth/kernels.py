@@ -1,0 +1,269 @@
+"""Seeded kernel-matrix and boundary-integral HODLR inputs (untimed construction).
+
+The solver's input is the HODLR operator (D, U_big, V_big). These generators
+build it from a dense matrix that is never formed: leaf blocks are evaluated
+exactly, and every off-diagonal sibling block A(I_alpha, I_beta) is compressed
+to the fixed rank r: blocks up to 2048 rows by a randomized range finder with
+one power iteration (Gaussian test matrix, oversampling 10) evaluated tile by
+tile, larger blocks by a skeleton (CUR) approximation from 8r sampled rows
+and columns. The compression error is not part of the solver's problem: the
+oracle and the GPU path both take the generated (D, U, V) as the matrix.
+
+Workloads (structure of the paper's Sec. 4 experiments; real field):
+* ``bie_hodlr``: 2D Laplace double-layer second-kind BIE on the star curve
+  rho(t) = 1 + 0.3 cos 5t, trapezoid rule on N equispaced parameters, natural
+  curve order, A = -1/2 I + D with D(x_i, y_j) w_j off the diagonal,
+  d(x, y) = n(y).(x - y) / (2 pi |x - y|^2), n the outward normal, and the
+  smooth-quadrature diagonal -1/2 - w_i kappa_i / (4 pi) (the limit of the
+  kernel at x = y, kappa the curvature). Gauss's identity gives A 1 = -1 up to
+  quadrature error.
+* ``kernel_hodlr``: symmetric kernel matrices on points uniform in [0,1]^d
+  ordered by a kd-tree of median splits (axes cycling with depth, leaves of
+  m points), K(x, y) = k(|x - y|) + nugget * delta; the symmetric split of
+  each block's SVD gives U = V.
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+from .generators import HodlrShape
+
+
+# ------------------------------------------------------------------ geometry
+def star_curve(N: int, device="cpu", dtype=torch.float64):
+    """Points, outward unit normals, trapezoid weights and curvature on the
+    star curve rho(t) = 1 + 0.3 cos(5t), t_i = 2 pi i / N."""
+    t = torch.arange(N, device=device, dtype=dtype) * (2 * math.pi / N)
+    rho = 1 + 0.3 * torch.cos(5 * t)
+    drho = -1.5 * torch.sin(5 * t)
+    ddrho = -7.5 * torch.cos(5 * t)
+    c, s = torch.cos(t), torch.sin(t)
+    x = torch.stack([rho * c, rho * s], dim=1)
+    tx = drho * c - rho * s
+    ty = drho * s + rho * c
+    speed = torch.sqrt(tx * tx + ty * ty)
+    normal = torch.stack([ty / speed, -tx / speed], dim=1)  # outward for a counter-clockwise curve
+    w = speed * (2 * math.pi / N)
+    kappa = (rho * rho + 2 * drho * drho - rho * ddrho) / (rho * rho + drho * drho) ** 1.5
+    return x, normal, w, kappa
+
+
+def bie_block(x, normal, w, rows, cols):
+    """Off-diagonal entries A(rows, cols) = d(x_i, y_j) w_j (no i == j)."""
+    xi = x[rows]  # (..., a, 2)
+    yj = x[cols]  # (..., b, 2)
+    d = xi.unsqueeze(-2) - yj.unsqueeze(-3)
+    r2 = (d * d).sum(-1)
+    nd = (d * normal[cols].unsqueeze(-3)).sum(-1)
+    return nd / (2 * math.pi * r2) * w[cols].unsqueeze(-2)
+
+
+def bie_dense(N: int, dtype=torch.float64):
+    """The full N x N BIE matrix (small N only, for checks)."""
+    x, n, w, kappa = star_curve(N, dtype=dtype)
+    idx = torch.arange(N)
+    A = torch.zeros(N, N, dtype=dtype)
+    off = idx[:, None] != idx[None, :]
+    blk = bie_block(x, n, w, idx, idx)
+    A[off] = blk[off]
+    A[idx, idx] = -0.5 - w * kappa / (4 * math.pi)
+    return A
+
+
+def kd_order(pts: torch.Tensor, m: int) -> torch.Tensor:
+    """Permutation ordering the points by a kd-tree of median splits, axes
+    cycling with depth, until nodes hold m points (N = m 2^L); stable sorts."""
+    N, dim = pts.shape
+    perm = torch.arange(N, device=pts.device)
+    size = N
+    depth = 0
+    while size > m:
+        axis = depth % dim
+        groups = perm.view(-1, size)
+        keys = pts[groups, axis]
+        order = torch.argsort(keys, dim=1, stable=True)
+        perm = torch.gather(groups, 1, order).reshape(-1)
+        size //= 2
+        depth += 1
+    return perm
+
+
+# ------------------------------------------------------------------ compression
+def _qr(Y):
+    return torch.linalg.qr(Y, mode="reduced")[0]
+
+
+def _rsvd_blocks(entries, row_start, col_start, n, r, g, device, oversample=10, budget=1 << 27):
+    """Randomized range finder with one power iteration on blocks
+    K_b = A(row_start[b] + [0, n), col_start[b] + [0, n)), evaluated tile by
+    tile. Returns (Ub, Vb) with K_b ~= Ub[b] Vb[b]^T, rank r."""
+    nblk = row_start.numel()
+    p = r + oversample
+    if n * n <= budget:
+        bs, tr = max(1, budget // (n * n)), n
+    else:
+        bs, tr = 1, max(1, budget // n)
+    Uo = torch.empty(nblk, n, r, device=device)
+    Vo = torch.empty(nblk, n, r, device=device)
+    ar = torch.arange(n, device=device)
+    for b0 in range(0, nblk, bs):
+        b1 = min(nblk, b0 + bs)
+        nb = b1 - b0
+        cols = col_start[b0:b1, None] + ar[None, :]
+
+        def tile(r0, r1):
+            return entries(row_start[b0:b1, None] + ar[None, r0:r1], cols)
+
+        def times(M):      # block @ M
+            out = torch.empty(nb, n, M.shape[-1], device=device)
+            for r0 in range(0, n, tr):
+                r1 = min(n, r0 + tr)
+                out[:, r0:r1] = tile(r0, r1) @ M
+            return out
+
+        def ttimes(M):     # block^T @ M
+            out = torch.zeros(nb, n, M.shape[-1], device=device)
+            for r0 in range(0, n, tr):
+                r1 = min(n, r0 + tr)
+                out += tile(r0, r1).transpose(1, 2) @ M[:, r0:r1]
+            return out
+
+        Om = torch.randn(nb, n, p, generator=g, device=device)
+        Q = _qr(times(Om))
+        Q = _qr(times(_qr(ttimes(Q))))
+        Bt = ttimes(Q)                                  # block^T Q
+        Ub_, S, Vh = torch.linalg.svd(Bt.transpose(1, 2), full_matrices=False)
+        sq = torch.sqrt(S[:, :r])
+        Uo[b0:b1] = (Q @ Ub_[:, :, :r]) * sq[:, None, :]
+        Vo[b0:b1] = Vh[:, :r, :].transpose(1, 2) * sq[:, None, :]
+    return Uo, Vo
+
+
+def _cur_blocks(entries, row_start, col_start, n, r, s, g, device, budget=1 << 27):
+    """Skeleton (CUR) approximation of large blocks from s sampled columns J
+    and rows I: K ~= K(:, J) K(I, J)^+ K(I, :), truncated to rank r through
+    the SVD of the s x s core. Costs O(n s) entries per block instead of n^2;
+    accurate for the smooth kernels used here."""
+    nblk = row_start.numel()
+    Uo = torch.empty(nblk, n, r, device=device)
+    Vo = torch.empty(nblk, n, r, device=device)
+    ar = torch.arange(n, device=device)
+    bs = max(1, budget // (n * s))
+    for b0 in range(0, nblk, bs):
+        b1 = min(nblk, b0 + bs)
+        nb = b1 - b0
+        J = torch.rand(nb, n, generator=g, device=device).argsort(dim=1)[:, :s].sort(dim=1).values
+        I = torch.rand(nb, n, generator=g, device=device).argsort(dim=1)[:, :s].sort(dim=1).values
+        rows = row_start[b0:b1, None] + ar[None, :]
+        cols = col_start[b0:b1, None] + ar[None, :]
+        C = entries(rows, col_start[b0:b1, None] + J).double()                 # (nb, n, s)
+        R = entries(row_start[b0:b1, None] + I, cols).double()                 # (nb, s, n)
+        W = entries(row_start[b0:b1, None] + I, col_start[b0:b1, None] + J).double()
+        Qc, Rc = torch.linalg.qr(C, mode="reduced")
+        Qr, Rr = torch.linalg.qr(R.transpose(1, 2), mode="reduced")
+        M = Rc @ torch.linalg.pinv(W, rtol=1e-12) @ Rr.transpose(1, 2)
+        Um, Sm, Vmh = torch.linalg.svd(M)
+        sq = torch.sqrt(Sm[:, :r])
+        Uo[b0:b1] = ((Qc @ Um[:, :, :r]) * sq[:, None, :]).float()
+        Vo[b0:b1] = ((Qr @ Vmh.transpose(1, 2)[:, :, :r]) * sq[:, None, :]).float()
+    return Uo, Vo
+
+
+def compress_blocks(entries, row_start, col_start, n, r, g, device):
+    """Rank-r factors of the n x n blocks at (row_start[b], col_start[b]):
+    randomized SVD up to n = 2048, CUR with 8r samples above."""
+    s = 8 * r
+    if n > 2048 and n > 2 * s:
+        return _cur_blocks(entries, row_start, col_start, n, r, s, g, device)
+    return _rsvd_blocks(entries, row_start, col_start, n, r, g, device)
+
+
+def _assemble(shape: HodlrShape, leaf_fn, entries, seed, device, symmetric):
+    """D (column-major blocks), U, V (column-major N x rL) in FP64."""
+    N, L, r, m = shape.N, shape.L, shape.r, shape.m
+    g = torch.Generator(device=device)
+    g.manual_seed(seed + 1000)
+    Dt = torch.empty(shape.nleaf, m, m, device=device, dtype=torch.float64)
+    step = max(1, (1 << 26) // (m * m))
+    for b0 in range(0, shape.nleaf, step):
+        b1 = min(shape.nleaf, b0 + step)
+        Dt[b0:b1] = leaf_fn(b0, b1).transpose(1, 2).double()
+    D = Dt.transpose(1, 2)
+    Ut = torch.empty(shape.rL, N, device=device, dtype=torch.float64)
+    Vt = torch.empty(shape.rL, N, device=device, dtype=torch.float64)
+    for c in range(1, L + 1):
+        n = N >> c
+        cols = slice((c - 1) * r, c * r)
+        if symmetric:
+            # blocks A(I_left, I_right) of the 2^(c-1) pairs; U = V by the symmetric split
+            j = torch.arange(1 << (c - 1), device=device)
+            Ub, Vb = compress_blocks(entries, 2 * j * n, (2 * j + 1) * n, n, r, g, device)
+            for jj in range(1 << (c - 1)):
+                Ut[cols, (2 * jj) * n:(2 * jj + 1) * n] = Ub[jj].T.double()
+                Ut[cols, (2 * jj + 1) * n:(2 * jj + 2) * n] = Vb[jj].T.double()
+            Vt[cols] = Ut[cols]
+        else:
+            # block b < 2^c: rows of node b, columns of its sibling b ^ 1
+            b = torch.arange(1 << c, device=device)
+            Ub, Vb = compress_blocks(entries, b * n, (b ^ 1) * n, n, r, g, device)
+            Ut[cols] = Ub.transpose(1, 2).permute(1, 0, 2).reshape(r, N).double()
+            Vt[cols] = Vb[b ^ 1].transpose(1, 2).permute(1, 0, 2).reshape(r, N).double()
+    return D, Ut.T, Vt.T
+
+
+def bie_hodlr(shape: HodlrShape, device="cpu", seed=2):
+    """HODLR operator of the star-curve Laplace BIE (see module doc)."""
+    shape.validate()
+    N, m = shape.N, shape.m
+    x, nrm, w, kappa = star_curve(N, device=device, dtype=torch.float64)
+    x32, n32, w32 = x.float(), nrm.float(), w.float()
+    diag = (-0.5 - w * kappa / (4 * math.pi))
+
+    def leaf_fn(b0, b1):
+        idx = torch.arange(b0 * m, b1 * m, device=device).view(b1 - b0, m)
+        blk = bie_block(x, nrm, w, idx, idx)
+        ii = torch.arange(m, device=device)
+        blk[:, ii, ii] = diag[idx]
+        return blk
+
+    def entries(rows, cols):
+        return bie_block(x32, n32, w32, rows, cols)
+
+    return _assemble(shape, leaf_fn, entries, seed, device, symmetric=False)
+
+
+def kernel_hodlr(shape: HodlrShape, dim: int, kind: str, scale: float, nugget: float, device="cpu", seed=1):
+    """HODLR operator of a symmetric kernel matrix on kd-ordered uniform points.
+    kind 'gaussian': exp(-d^2 / (2 scale^2)); kind 'matern32':
+    (1 + sqrt(3) d / scale) exp(-sqrt(3) d / scale). Returns (D, U, V, points)."""
+    shape.validate()
+    N, m = shape.N, shape.m
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    pts = torch.rand(N, dim, generator=g, device=device, dtype=torch.float64)
+    pts = pts[kd_order(pts, m)].contiguous()
+    p32 = pts.float()
+
+    def kfun(d2):
+        if kind == "gaussian":
+            return torch.exp(-d2 / (2 * scale * scale))
+        d = torch.sqrt(torch.clamp(d2, min=0))
+        a = math.sqrt(3) * d / scale
+        return (1 + a) * torch.exp(-a)
+
+    def leaf_fn(b0, b1):
+        P = pts[b0 * m:b1 * m].view(b1 - b0, m, dim)
+        d2 = ((P[:, :, None, :] - P[:, None, :, :]) ** 2).sum(-1)
+        K = kfun(d2)
+        ii = torch.arange(m, device=device)
+        K[:, ii, ii] += nugget
+        return K
+
+    def entries(rows, cols):
+        d2 = ((p32[rows][:, :, None, :] - p32[cols][:, None, :, :]) ** 2).sum(-1)
+        return kfun(d2)
+
+    D, U, V = _assemble(shape, leaf_fn, entries, seed, device, symmetric=True)
+    return D, U, V, pts

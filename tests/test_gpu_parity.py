@@ -171,3 +171,31 @@ def test_singular_coupling_reported(cuda_lib):
     assert code == hb.HODLR_ERR_SINGULAR_COUPLING and where == 1 and detail == 1
     with pytest.raises(hb.HodlrError):
         hb.hodlr_logdet(F)
+
+
+@pytest.mark.parametrize("N,L,r", [(1 << 14, 7, 32), (1 << 15, 7, 64), (1 << 13, 5, 32)])
+def test_bf16_tensor_core_factor_matches_cuda_core(cuda_lib, N, L, r):
+    """The tcgen05/TMA panel kernels and the CUDA-core kernels compute the same
+    BF16-input, FP32-accumulated products (only the summation order differs),
+    so the two BF16 factors' solves agree far below BF16 rounding."""
+    hb = cuda_lib
+    (Dm, Um, Vm, Bm), (D, U, V, B) = make_case(N, L, r, seed=77 + r, k=2)
+    try:
+        hb.hodlr_tc_enable(False)
+        Fc = hb.hodlr_factor(D, U, V, L, r, "bf16")
+        Xc = hb.hodlr_solve(Fc, B.clone()).cpu().numpy()
+        lc = hb.hodlr_logdet(Fc)
+    finally:
+        hb.hodlr_tc_enable(True)
+    hb.hodlr_profile_reset()
+    hb.hodlr_profile_enable(True)
+    Ft = hb.hodlr_factor(D, U, V, L, r, "bf16")
+    hb.hodlr_profile_enable(False)
+    assert hb.hodlr_profile_read()["project_tc"][1] == L   # every level ran on the tensor cores
+    assert hb.hodlr_factor_status(Ft)[0] == 0
+    Xt = hb.hodlr_solve(Ft, B.clone()).cpu().numpy()
+    lt = hb.hodlr_logdet(Ft)
+    assert relerr(Xt, Xc) < 1e-4
+    assert lt[0] == lc[0] and abs(lt[1] - lc[1]) < 1e-6 * max(1.0, abs(lc[1]))
+    # and the BF16 factor is a BF16-accurate inverse of the FP64 operator
+    assert relerr(Xt, RecursiveHODLR(Dm, Um, Vm, L).solve(Bm)) < 5e-2
