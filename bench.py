@@ -41,6 +41,12 @@ WORKLOADS = {
                                       "1 RHS; BF16-panel factor as FGMRES preconditioner to relres 1e-10"),
     "synthetic-4096": dict(N=4096, L=6, r=16, k=1, prec="fp64", solver="direct", shift=4.0, seed=0,
                            data="synthetic", desc="synthetic HODLR N=4096, leaf 64, rank 16, FP64"),
+    "gaussian-2^18": dict(N=1 << 18, L=10, r=64, k=16, prec="fp32", solver="refine", shift=0.0, seed=1,
+                          data="gaussian", desc="Gaussian kernel (sigma 0.1, nugget 1e-2) on 2^18 kd-ordered points "
+                                                "in [0,1]^2, leaf 256, rank 64, 16 RHS; FP32 factor + refinement"),
+    "matern-2^20": dict(N=1 << 20, L=12, r=64, k=32, prec="fp32", solver="refine", shift=0.0, seed=3,
+                        data="matern", desc="Matern-3/2 kernel (lengthscale 0.2, nugget 1e-3) on 2^20 kd-ordered "
+                                            "points in [0,1]^3, leaf 256, rank 64, 32 RHS; FP32 factor + refinement"),
     "synthetic-2^23": dict(N=1 << 23, L=15, r=32, k=64, prec="bf16", solver="refine", shift=8.0, seed=4,
                            data="synthetic", desc="synthetic HODLR N=2^23, leaf 256, rank 32, 64 RHS; BF16 "
                                                   "factor + refinement to 1e-10"),
@@ -72,9 +78,14 @@ def make_inputs(w, device, rank=0):
     import torch
     from synth import HodlrShape, gaussian_rhs, synthetic_hodlr
     shape = HodlrShape(w["N"], w["L"], w["r"])
-    if w["data"] == "bie":
-        from synth.kernels import bie_hodlr
-        D, U, V = bie_hodlr(shape, device=device)
+    if w["data"] in ("bie", "gaussian", "matern"):
+        from synth.kernels import bie_hodlr, kernel_hodlr
+        if w["data"] == "bie":
+            D, U, V = bie_hodlr(shape, device=device, seed=w["seed"])
+        elif w["data"] == "gaussian":
+            D, U, V, _ = kernel_hodlr(shape, 2, "gaussian", 0.1, 1e-2, device=device, seed=w["seed"])
+        else:
+            D, U, V, _ = kernel_hodlr(shape, 3, "matern32", 0.2, 1e-3, device=device, seed=w["seed"])
         g = torch.Generator(device=device)
         g.manual_seed(w["seed"] + 1000 * rank)
     else:

@@ -192,6 +192,30 @@ HODLR_API hodlr_status hodlr_gmres(hodlr_factor_t f, const double* D, const doub
                          void* workspace, size_t workspace_bytes, hodlr_stream_t stream,
                          int32_t* iters, double* relres);
 
+/* -------------------------------------------------------------- gradient --
+ * Gradient of  loss = sum_j b_j^T A^{-1} b_j + log|det A|  (k columns b_j of
+ * B) with respect to B, the leaf blocks D_b and the bases U_big, V_big, for an
+ * FP64 factor f of (D, U, V). With X = A^{-1} B, Lam = A^{-T} B and
+ * G = dloss/dA = -Lam X^T + A^{-T}:
+ *   dB = X + Lam;  dD_b = G(I_b, I_b);  for siblings (alpha, beta):
+ *   dU_alpha = G(I_alpha, I_beta) V_beta,  dV_beta = G(I_alpha, I_beta)^T U_alpha.
+ * The -Lam X^T part is rank k and is applied block by block. The A^{-T} part
+ * is taken through the factorization A = F_0 F_L ... F_1 (Sec. 3.5):
+ * log|det A| = sum log|det D_b| + sum log|det K~_gamma|; with
+ * Z_alpha = A_alpha^{-T} V_alpha (a top-down sweep of the adjoint levels over
+ * V_big) and H_alpha the off-diagonal block of K~_gamma^{-T} facing alpha,
+ * dV_alpha += Y_alpha H_alpha^T, dU_alpha += Z_alpha H_alpha, and the rank-r
+ * term -Z_alpha H_alpha Y_alpha^T of dloss/dA_alpha is pushed to every pair
+ * and leaf below alpha; dD_b also gets D_b^{-T}.
+ * dD has D's layout, dU and dV are N x rL with leading dimension N, dB is
+ * N x k (lddb). Results overwrite the outputs. If loss is not NULL the call
+ * synchronizes and stores the loss value. Only FP64 factors
+ * (HODLR_ERR_ARG otherwise). */
+HODLR_API hodlr_status hodlr_grad_workspace_size(hodlr_factor_t f, int32_t k, size_t* bytes);
+HODLR_API hodlr_status hodlr_grad(hodlr_factor_t f, const double* U, const double* V, const double* B, int64_t ldb,
+                                  int32_t k, double* dD, double* dU, double* dV, double* dB, int64_t lddb,
+                                  void* workspace, size_t workspace_bytes, hodlr_stream_t stream, double* loss);
+
 /* ------------------------------------------------------------ diagnostics --
  * Accounting of the library's own kernel launches, for benchmarks; not part
  * of the method. hodlr_launch_count: kernels enqueued by this library since

@@ -38,7 +38,7 @@ EXPORTED = (
     "hodlr_solve_workspace_size", "hodlr_solve", "hodlr_solve_adjoint", "hodlr_logdet",
     "hodlr_matvec_workspace_size", "hodlr_matvec", "hodlr_refine_workspace_size", "hodlr_solve_refined",
     "hodlr_gmres", "hodlr_launch_count", "hodlr_profile_enable", "hodlr_profile_reset", "hodlr_profile_read",
-    "hodlr_profile_name", "hodlr_profile_work", "hodlr_tc_enable",
+    "hodlr_profile_name", "hodlr_profile_work", "hodlr_tc_enable", "hodlr_grad_workspace_size", "hodlr_grad",
 )
 
 
@@ -79,6 +79,9 @@ _SIGS = {
     "hodlr_profile_name": ([_i32], _c.c_char_p),
     "hodlr_profile_work": ([_c.POINTER(_dbl), _c.POINTER(_dbl), _i32], _i32),
     "hodlr_tc_enable": ([_i32], None),
+    "hodlr_grad_workspace_size": ([_vp, _i32, _c.POINTER(_sz)], _c.c_int),
+    "hodlr_grad": ([_vp, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp, _i64, _vp, _sz, _vp, _c.POINTER(_dbl)],
+                   _c.c_int),
 }
 
 
@@ -321,3 +324,31 @@ def hodlr_profile_name(i: int) -> str:
 def hodlr_tc_enable(on: bool = True) -> None:
     """Select tensor-core (on, default) or CUDA-core kernels for the BF16 factor."""
     _LIB.hodlr_tc_enable(1 if on else 0)
+
+
+# ------------------------------------------------------------------- gradient
+def hodlr_grad_workspace_size(F: FactorHandle, k: int) -> int:
+    out = ctypes.c_size_t()
+    _check(_LIB.hodlr_grad_workspace_size(F.handle, k, ctypes.byref(out)))
+    return out.value
+
+
+def hodlr_grad(F: FactorHandle, U, V, B, want_loss: bool = True):
+    """(loss, dD, dU, dV, dB) of loss = sum_j b_j^T A^{-1} b_j + log|det A| for
+    the FP64 factor F of (D, U, V); dD in D's layout, dU / dV / dB column-major."""
+    N = F.N
+    ldb = _ld(B, N)
+    k = B.shape[1]
+    m, L = F.desc.m, F.desc.L
+    rL = F.desc.r * L
+    dev = B.device
+    dD = torch.empty(1 << L, m, m, dtype=torch.float64, device=dev).transpose(1, 2)
+    dU = torch.empty(rL, N, dtype=torch.float64, device=dev).T
+    dV = torch.empty(rL, N, dtype=torch.float64, device=dev).T
+    dB = torch.empty(k, N, dtype=torch.float64, device=dev).T
+    ws = _workspace(hodlr_grad_workspace_size(F, k), dev)
+    loss = ctypes.c_double()
+    _check(_LIB.hodlr_grad(F.handle, _ptr(U), _ptr(V), _ptr(B), ldb, k, _ptr(dD), _ptr(dU), _ptr(dV), _ptr(dB), N,
+                           _ptr(ws), ws.numel(), _stream(), ctypes.byref(loss) if want_loss else None),
+           "hodlr_grad: ")
+    return (loss.value if want_loss else None), dD, dU, dV, dB

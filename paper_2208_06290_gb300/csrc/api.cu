@@ -1,6 +1,7 @@
 // C ABI of libhodlr: argument checks, workspace layout and the host-side
 // sequencing of the level-by-level factorization (Alg. 1 / Alg. 3) and solves
 // (Alg. 2 / Alg. 4), the FP64 matvec and the refined solvers.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -173,12 +174,23 @@ hodlr_status factor_levels(Factor& F, cudaStream_t s) {
     } else {
       HODLR_CUDA(launch_project<TP, TP>(d.N, d.r, c, Vp, F.ldvp, c - 1, Y, d.N, rc, F.P, 0, s));
     }
+    F.P_reduced = chunks_per_node(d.N, c) > 1;
+    if (F.P_reduced) HODLR_CUDA(launch_reduce_chunks(d.N, d.r, c, F.P, rc, s));
     HODLR_CUDA(launch_coupling_factor(F, c, s));
     if (anc > 0) {
       HODLR_CUDA(launch_coupling_factor_apply(F, c, s));
       const int64_t wstride = chunks_per_node(d.N, c) * (int64_t)d.r * rc;
-      HODLR_CUDA(launch_update<TP, TP>(d.N, d.r, c, Y, d.N, c - 1, Y, d.N, anc, F.P, wstride, 0, -1.0, 0, s));
+      bool done = false;
+      if constexpr (std::is_same<TP, __nv_bfloat16>::value) {
+        if (g_use_tc && update_tc_supported(d.N, d.r, c)) {
+          HODLR_CUDA(launch_update_tc(d.N, d.r, c, Y, F.P, wstride, F.status, s));
+          done = true;
+        }
+      }
+      if (!done)
+        HODLR_CUDA(launch_update<TP, TP>(d.N, d.r, c, Y, d.N, c - 1, Y, d.N, anc, F.P, wstride, 0, -1.0, 0, s));
     }
+    F.P_reduced = false;
   }
   return HODLR_OK;
 }
@@ -622,6 +634,167 @@ hodlr_status hodlr_gmres(hodlr_factor_t f, const double* D, const double* U, con
   HODLR_CUDA(cudaMemcpy(&ds, f->status, sizeof(ds), cudaMemcpyDeviceToHost));
   if (ds.code != 0) return static_cast<hodlr_status>(ds.code);
   return worst <= tol ? HODLR_OK : HODLR_ERR_NOT_CONVERGED;
+}
+
+// ------------------------------------------------------------------ gradient
+}  // extern "C"
+
+namespace {
+
+struct GradLayout {
+  size_t X, Lam, Z, Pb, E, H, HT, Ps, solve, dots, total;
+};
+
+GradLayout grad_layout(const Factor& F, int k) {
+  const hodlr_desc& d = F.d;
+  GradLayout l{};
+  const size_t N = (size_t)d.N, rL = (size_t)d.r * d.L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes); return o; };
+  l.X = take(N * k * 8);
+  l.Lam = take(N * k * 8);
+  l.Z = take(N * rL * 8);
+  l.Pb = take(N * rL * 8);
+  l.E = take(N * (size_t)d.m * 8);
+  l.H = take(((size_t)1 << d.L) * d.r * d.r * 8);
+  l.HT = take(((size_t)1 << d.L) * d.r * d.r * 8);
+  size_t ps = 0;
+  for (int c = 1; c <= d.L; ++c) {
+    const size_t w = (size_t)num_chunks(d.N, c) *
+                     std::max<size_t>((size_t)k * d.r, std::max<size_t>((size_t)d.r * d.r, (size_t)d.r * d.r * (c - 1)));
+    ps = std::max(ps, w);
+  }
+  l.Ps = take(ps * 8);
+  l.solve = take(solve_ws_bytes(F, k));
+  l.dots = take((dot_scratch_elems(d.N, k) + (size_t)k) * 8);
+  l.total = off;
+  return l;
+}
+
+hodlr_status grad_core(const Factor& F, const double* U, const double* V, const double* B, int64_t ldb, int k,
+                       double* dD, double* dU, double* dV, double* dB, int64_t lddb, char* w, const GradLayout& lay,
+                       cudaStream_t s, double* loss) {
+  const hodlr_desc& d = F.d;
+  const int64_t N = d.N;
+  const int r = d.r, L = d.L, m = d.m, rL = r * L;
+  double* X = reinterpret_cast<double*>(w + lay.X);
+  double* Lam = reinterpret_cast<double*>(w + lay.Lam);
+  double* Z = reinterpret_cast<double*>(w + lay.Z);
+  double* Pb = reinterpret_cast<double*>(w + lay.Pb);
+  double* E = reinterpret_cast<double*>(w + lay.E);
+  double* H = reinterpret_cast<double*>(w + lay.H);
+  double* HT = reinterpret_cast<double*>(w + lay.HT);
+  double* Ps = reinterpret_cast<double*>(w + lay.Ps);
+  void* sw = w + lay.solve;
+  double* dots = reinterpret_cast<double*>(w + lay.dots);
+  const double* Y = static_cast<const double*>(F.Y);
+  const int64_t ldu = d.ldu, ldv = d.ldv;
+  hodlr_status st;
+  // X = A^{-1} B, Lam = A^{-T} B, dB = X + Lam
+  HODLR_CUDA(launch_copy_cols<double, double>(N, k, B, ldb, X, N, s));
+  if ((st = solve_any(F, X, N, k, sw, 0, s)) != HODLR_OK) return st;
+  HODLR_CUDA(launch_copy_cols<double, double>(N, k, B, ldb, Lam, N, s));
+  if ((st = solve_any(F, Lam, N, k, sw, 1, s)) != HODLR_OK) return st;
+  HODLR_CUDA(launch_copy_cols<double, double>(N, k, X, N, dB, lddb, s));
+  HODLR_CUDA(launch_axpby_cols(N, k, 1.0, Lam, N, 1.0, dB, lddb, s));
+  // quadratic term: dD_b = -Lam_b X_b^T; dU_a = -Lam_a (X_b^T V_b); dV_b = -X_b (Lam_a^T U_a)
+  HODLR_CUDA(launch_leaf_outer(N, m, k, Lam, N, X, N, -1.0, 0.0, nullptr, dD, s));
+  HODLR_CUDA(cudaMemsetAsync(dU, 0, (size_t)N * rL * 8, s));
+  HODLR_CUDA(cudaMemsetAsync(dV, 0, (size_t)N * rL * 8, s));
+  HODLR_CUDA(cudaMemsetAsync(Pb, 0, (size_t)N * rL * 8, s));
+  for (int c = 1; c <= L; ++c) {
+    const int64_t ws = chunks_per_node(N, c) * (int64_t)k * r;
+    HODLR_CUDA((launch_project<double, double>(N, k, c, X, N, 0, V + (int64_t)(c - 1) * r * ldv, ldv, r, Ps, 1, s)));
+    HODLR_CUDA(launch_reduce_chunks(N, k, c, Ps, r, s));
+    HODLR_CUDA((launch_update<double, double>(N, k, c, Lam, N, 0, dU + (int64_t)(c - 1) * r * N, N, r, Ps, ws, 1,
+                                              -1.0, 1, s)));
+    HODLR_CUDA((launch_project<double, double>(N, k, c, Lam, N, 0, U + (int64_t)(c - 1) * r * ldu, ldu, r, Ps, 1, s)));
+    HODLR_CUDA(launch_reduce_chunks(N, k, c, Ps, r, s));
+    HODLR_CUDA((launch_update<double, double>(N, k, c, X, N, 0, dV + (int64_t)(c - 1) * r * N, N, r, Ps, ws, 1,
+                                              -1.0, 1, s)));
+  }
+  // Z_alpha = A_alpha^{-T} V_alpha for every node: adjoint levels top-down on V_big's
+  // ancestor columns, then D_b^{-T}
+  HODLR_CUDA(launch_copy_cols<double, double>(N, rL, V, ldv, Z, N, s));
+  for (int c = 2; c <= L; ++c) {
+    const int anc = r * (c - 1);
+    HODLR_CUDA((launch_project<double, double>(N, r, c, Y, N, c - 1, Z, N, anc, Ps, 1, s)));
+    HODLR_CUDA(launch_coupling_apply_any(F, c, Ps, anc, anc, 0, 1, s));
+    const int64_t ws = chunks_per_node(N, c) * (int64_t)r * anc;
+    HODLR_CUDA((launch_update<double, double>(N, r, c, V, ldv, c - 1, Z, N, anc, Ps, ws, 1, -1.0, 1, s)));
+  }
+  HODLR_CUDA((launch_leaf_solve<double, double>(F, Z, N, Z, N, rL, 1, s)));
+  // log-det term at each coupling: dV_a += Y_a H_a^T, dU_a += Z_a H_a, Pb_a = -Z_a H_a
+  for (int c = 1; c <= L; ++c) {
+    HODLR_CUDA(launch_coupling_h(F, c, H, HT, s));
+    const int64_t ws = (int64_t)r * r;
+    HODLR_CUDA((launch_update<double, double>(N, r, c, Y, N, c - 1, dV + (int64_t)(c - 1) * r * N, N, r, HT, ws, 0,
+                                              1.0, 1, s)));
+    HODLR_CUDA((launch_update<double, double>(N, r, c, Z, N, c - 1, dU + (int64_t)(c - 1) * r * N, N, r, H, ws, 0,
+                                              1.0, 1, s)));
+    HODLR_CUDA((launch_update<double, double>(N, r, c, Z, N, c - 1, Pb + (int64_t)(c - 1) * r * N, N, r, H, ws, 0,
+                                              -1.0, 1, s)));
+  }
+  // push the rank-r terms Pb_a Y_a^T down to every pair (mu, nu) below a
+  for (int c = 2; c <= L; ++c) {
+    const int64_t ws = chunks_per_node(N, c) * (int64_t)r * r;
+    for (int j = 0; j <= c - 2; ++j) {
+      HODLR_CUDA((launch_project<double, double>(N, r, c, Y, N, j, V + (int64_t)(c - 1) * r * ldv, ldv, r, Ps, 1, s)));
+      HODLR_CUDA(launch_reduce_chunks(N, r, c, Ps, r, s));
+      HODLR_CUDA((launch_update<double, double>(N, r, c, Pb, N, j, dU + (int64_t)(c - 1) * r * N, N, r, Ps, ws, 1,
+                                                1.0, 1, s)));
+      HODLR_CUDA((launch_project<double, double>(N, r, c, Pb, N, j, U + (int64_t)(c - 1) * r * ldu, ldu, r, Ps, 1, s)));
+      HODLR_CUDA(launch_reduce_chunks(N, r, c, Ps, r, s));
+      HODLR_CUDA((launch_update<double, double>(N, r, c, Y, N, j, dV + (int64_t)(c - 1) * r * N, N, r, Ps, ws, 1, 1.0,
+                                                1, s)));
+    }
+  }
+  // leaves: dD_b += D_b^{-T} + Pb(I_b, :) Y(I_b, :)^T
+  HODLR_CUDA(launch_leaf_identity(N, m, E, s));
+  HODLR_CUDA((launch_leaf_solve<double, double>(F, E, N, E, N, m, 0, s)));
+  HODLR_CUDA(launch_leaf_outer(N, m, rL, Pb, N, Y, N, 1.0, 1.0, E, dD, s));
+  if (loss) {
+    HODLR_CUDA(launch_dots(N, k, B, ldb, X, N, dots + dot_scratch_elems(N, k), dots, s));
+    std::vector<double> q(k);
+    HODLR_CUDA(cudaMemcpyAsync(q.data(), dots + dot_scratch_elems(N, k), (size_t)k * 8, cudaMemcpyDeviceToHost, s));
+    HODLR_CUDA(launch_logdet_reduce(F, s));
+    double ld[2];
+    HODLR_CUDA(cudaMemcpyAsync(ld, F.ld_out, sizeof(ld), cudaMemcpyDeviceToHost, s));
+    HODLR_CUDA(cudaStreamSynchronize(s));
+    double acc = ld[1];
+    for (int j = 0; j < k; ++j) acc += q[j];
+    *loss = acc;
+  }
+  return HODLR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hodlr_status hodlr_grad_workspace_size(hodlr_factor_t f, int32_t k, size_t* bytes) {
+  if (!valid_factor(f) || k < 1 || k > 64 || !bytes) return HODLR_ERR_ARG;
+  *bytes = grad_layout(*f, k).total;
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_grad(hodlr_factor_t f, const double* U, const double* V, const double* B, int64_t ldb, int32_t k,
+                        double* dD, double* dU, double* dV, double* dB, int64_t lddb, void* workspace,
+                        size_t workspace_bytes, hodlr_stream_t stream, double* loss) {
+  if (!valid_factor(f) || f->prec != HODLR_PREC_FP64 || !U || !V || !B || !dD || !dU || !dV || !dB || k < 1 ||
+      k > 64 || ldb < f->d.N || lddb < f->d.N)
+    return HODLR_ERR_ARG;
+  const GradLayout lay = grad_layout(*f, k);
+  if (!workspace || !aligned(workspace, kAlign) || workspace_bytes < lay.total) return HODLR_ERR_WORKSPACE;
+  hodlr_status st = grad_core(*f, U, V, B, ldb, k, dD, dU, dV, dB, lddb, static_cast<char*>(workspace), lay,
+                              reinterpret_cast<cudaStream_t>(stream), loss);
+  if (st != HODLR_OK) return st;
+  if (loss) {
+    DevStatus ds{};
+    HODLR_CUDA(cudaMemcpy(&ds, f->status, sizeof(ds), cudaMemcpyDeviceToHost));
+    if (ds.code != 0) return static_cast<hodlr_status>(ds.code);
+  }
+  return HODLR_OK;
 }
 
 int64_t hodlr_launch_count(void) { return g_launches.load(); }

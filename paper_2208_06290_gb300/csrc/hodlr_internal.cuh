@@ -83,6 +83,10 @@ struct Factor {
   // projection partials (FP64): max over levels of num_chunks * r * r*c
   double* P;
   size_t P_elems;
+  // set while the factor's level loop has already summed each node's chunk
+  // partials into its first slot (top levels), so the coupling kernels read
+  // one slot per node
+  bool P_reduced = false;
   // log-determinant pieces: leaves (logabs, sign) then parents in Koff order
   double* leaf_ld;
   double* node_ld;
@@ -143,6 +147,23 @@ cudaError_t launch_coupling_solve(const Factor& F, int c, double* P, int k, int 
 // Sum the chunk partials of every node into the node's first chunk slot.
 cudaError_t launch_reduce_chunks(int64_t N, int r, int c, double* P, int ncols, cudaStream_t s);
 
+// Low-precision factors with m <= 128 keep D_b^{-1} (FP32) instead of the LU
+// factors; their leaf solves are GEMMs with it.
+bool leaf_uses_inverse(const Factor& F);
+cudaError_t launch_leaf_inv(const Factor& F, const double* D, cudaStream_t s);
+template <typename TIN, typename TOUT>
+cudaError_t launch_leaf_apply_inv(const Factor& F, const TIN* in, int64_t ldin, TOUT* out, int64_t ldout, int ncols,
+                                  int trans, cudaStream_t s);
+
+// Coupling application with any slot width (gradient sweeps).
+cudaError_t launch_coupling_apply_any(const Factor& F, int c, double* P, int64_t sw, int nrhs, int first_is_beta,
+                                      int trans, cudaStream_t s);
+// Gradient helpers (grad.cu)
+cudaError_t launch_leaf_identity(int64_t N, int m, double* E, cudaStream_t s);
+cudaError_t launch_leaf_outer(int64_t N, int m, int K, const double* A, int64_t lda, const double* B, int64_t ldb,
+                              double alpha, double beta, const double* Tadd, double* out, cudaStream_t s);
+cudaError_t launch_coupling_h(const Factor& F, int c, double* H, double* HT, cudaStream_t s);
+
 // Leaf stage of the matvec: Y_b = D_b X_b (FP64).
 cudaError_t launch_leaf_matvec(const hodlr_desc& d, const double* D, const double* X, int64_t ldx,
                                double* Y, int64_t ldy, int k, cudaStream_t s);
@@ -169,6 +190,9 @@ cudaError_t launch_logdet_reduce(const Factor& F, cudaStream_t s);
 bool project_tc_supported(int64_t N, int r, int c);
 cudaError_t launch_project_tc(int64_t N, int r, int L, int c, const __nv_bfloat16* Vp, int64_t ldv,
                               const __nv_bfloat16* Y, double* P, DevStatus* st, cudaStream_t s);
+bool update_tc_supported(int64_t N, int r, int c);
+cudaError_t launch_update_tc(int64_t N, int r, int c, __nv_bfloat16* Y, const double* Wbase, int64_t wstride,
+                             DevStatus* st, cudaStream_t s);
 // Set by hodlr_tc_enable (process-wide; default on).
 extern bool g_use_tc;
 

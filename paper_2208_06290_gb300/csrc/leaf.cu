@@ -1,6 +1,8 @@
 // Leaf stage: batched LU with partial pivoting of the 2^L leaf blocks and the
 // batched triangular solves with them (Alg. 1 leaf loop; Alg. 3 first two steps;
 // Alg. 2 / Alg. 4 leaf step).
+#include <type_traits>
+
 #include "hodlr_internal.cuh"
 
 namespace hodlr {
@@ -141,6 +143,7 @@ static cudaError_t leaf_lu_dispatch(const Factor& F, const double* D, cudaStream
 
 cudaError_t launch_leaf_lu(const Factor& F, const double* D, cudaStream_t s) {
   ProfScope prof_(KC_LEAF_LU, s);
+  if (leaf_uses_inverse(F)) return launch_leaf_inv(F, D, s);
   if (F.prec == HODLR_PREC_FP64) return leaf_lu_dispatch<double>(F, D, s);
   return leaf_lu_dispatch<float>(F, D, s);
 }
@@ -151,18 +154,33 @@ cudaError_t launch_leaf_lu(const Factor& F, const double* D, cudaStream_t s) {
 // l, l+32, ... in registers, so the substitutions need no block barrier: the
 // pivot row value moves by warp shuffle and each L / U column is read once
 // per warp (coalesced, through L1/L2) for CPW columns at a time.
-template <typename TL, typename TIN, typename TOUT, int RPL, int CPW>
+// SMEM: the CTA first copies the leaf's LU factor and permutation to shared
+// memory and its warps then sweep all column groups of the leaf (one LU load
+// per leaf instead of one per column group).
+template <typename TL, typename TIN, typename TOUT, int RPL, int CPW, bool SMEM>
 __global__ void __launch_bounds__(256) leaf_solve_kernel(int m, const TL* __restrict__ LU,
                                                          const int* __restrict__ perm, const TIN* in,
                                                          int64_t ldin, TOUT* out, int64_t ldout, int ncols,
                                                          int trans) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int col0 = (blockIdx.y * (blockDim.x >> 5) + warp) * CPW;
-  if (col0 >= ncols) return;
+  const int nwarps = blockDim.x >> 5;
   const TL* A = LU + (size_t)b * m * m;
   const int* pb = perm + (size_t)b * m;
+  if (SMEM) {
+    TL* sA = reinterpret_cast<TL*>(smem_raw);
+    int* sp = reinterpret_cast<int*>(sA + (size_t)m * m);
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) sA[e] = A[e];
+    for (int e = threadIdx.x; e < m; e += blockDim.x) sp[e] = pb[e];
+    __syncthreads();
+    A = sA;
+    pb = sp;
+  }
   const int64_t row0 = (int64_t)b * m;
+  const int cstride = SMEM ? nwarps * CPW : 0;
+  for (int col0 = SMEM ? warp * CPW : (blockIdx.y * nwarps + warp) * CPW; col0 < ncols;
+       col0 += SMEM ? cstride : ncols) {
   TL x[CPW][RPL];
 #pragma unroll
   for (int s = 0; s < RPL; ++s) {
@@ -286,19 +304,28 @@ __global__ void __launch_bounds__(256) leaf_solve_kernel(int m, const TL* __rest
       }
     }
   }
+  }
 }
 
 template <typename TL, typename TIN, typename TOUT, int RPL, int CPW>
 static cudaError_t leaf_solve_cpw(const Factor& F, const TIN* in, int64_t ldin, TOUT* out, int64_t ldout,
                                   int ncols, int trans, cudaStream_t s) {
   const int nleaf = 1 << F.d.L;
+  const int m = F.d.m;
   const int cols_per_cta = 8 * CPW;
-  const double Nd = (double)nleaf * F.d.m;
-  note_work((sizeof(TIN) + sizeof(TOUT)) * Nd * ncols + sizeof(TL) * Nd * F.d.m + 4.0 * Nd,
-            2.0 * F.d.m * Nd * ncols);
-  dim3 grid(nleaf, (ncols + cols_per_cta - 1) / cols_per_cta);
-  { leaf_solve_kernel<TL, TIN, TOUT, RPL, CPW><<<grid, 256, 0, s>>>(
-      F.d.m, static_cast<const TL*>(F.lu), F.perm, in, ldin, out, ldout, ncols, trans); note_launches(1); }
+  const double Nd = (double)nleaf * m;
+  note_work((sizeof(TIN) + sizeof(TOUT)) * Nd * ncols + sizeof(TL) * Nd * m + 4.0 * Nd, 2.0 * m * Nd * ncols);
+  const size_t sm = (size_t)m * m * sizeof(TL) + (size_t)m * sizeof(int);
+  if (ncols >= 2 * cols_per_cta && sm <= 160 * 1024) {
+    cudaFuncSetAttribute(leaf_solve_kernel<TL, TIN, TOUT, RPL, CPW, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    { leaf_solve_kernel<TL, TIN, TOUT, RPL, CPW, true><<<nleaf, 256, sm, s>>>(
+        m, static_cast<const TL*>(F.lu), F.perm, in, ldin, out, ldout, ncols, trans); note_launches(1); }
+  } else {
+    dim3 grid(nleaf, (ncols + cols_per_cta - 1) / cols_per_cta);
+    { leaf_solve_kernel<TL, TIN, TOUT, RPL, CPW, false><<<grid, 256, 0, s>>>(
+        m, static_cast<const TL*>(F.lu), F.perm, in, ldin, out, ldout, ncols, trans); note_launches(1); }
+  }
   return cudaGetLastError();
 }
 
@@ -329,6 +356,9 @@ cudaError_t launch_leaf_solve(const Factor& F, const TIN* in, int64_t ldin, TOUT
                               int ncols, int trans, cudaStream_t s) {
   ProfScope prof_(KC_LEAF_SOLVE, s);
   if (ncols <= 0) return cudaSuccess;
+  if constexpr (!std::is_same<TIN, double>::value || !std::is_same<TOUT, double>::value) {
+    if (leaf_uses_inverse(F)) return launch_leaf_apply_inv<TIN, TOUT>(F, in, ldin, out, ldout, ncols, trans, s);
+  }
   if (F.prec == HODLR_PREC_FP64) return leaf_solve_tl<double>(F, in, ldin, out, ldout, ncols, trans, s);
   return leaf_solve_tl<float>(F, in, ldin, out, ldout, ncols, trans, s);
 }

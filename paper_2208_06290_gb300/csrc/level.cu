@@ -1,7 +1,7 @@
 // Level stage of the factorization and solves (Alg. 1 / Alg. 3 level loop,
 // Alg. 2 / Alg. 4 level loop): projections onto the level's bases, the 2r x 2r
 // coupling systems and the rank-r updates.
-#include "hodlr_internal.cuh"
+#include "gj.cuh"
 
 namespace hodlr {
 
@@ -122,6 +122,59 @@ __global__ void __launch_bounds__(256) project_skinny_kernel(int64_t N, int r, i
   }
 }
 
+// One right-hand side (k = 1): one warp per chunk. Lane l streams rows l,
+// l+32, ... of the chunk and accumulates all RT <= 64 basis-column products;
+// a butterfly transpose-reduce (31 shuffles per 32 columns) then leaves the
+// chunk total of column j in lane j % 32, which writes it. No shared memory,
+// no block barrier; fixed summation order.
+template <typename TA>
+__device__ __forceinline__ TA warp_transpose_reduce32(TA (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool upper = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const TA send = upper ? v[i] : v[i + s];
+      const TA keep = upper ? v[i + s] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  return v[0];
+}
+
+template <typename TB, typename TR, typename TA, int RT>
+__global__ void __launch_bounds__(256) project_k1_kernel(int64_t N, int r, int c, const TB* __restrict__ Bas,
+                                                         int64_t ldb, int bas_block, const TR* __restrict__ R,
+                                                         double* __restrict__ P) {
+  const int lane = threadIdx.x & 31;
+  const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (q >= num_chunks(N, c)) return;
+  const int64_t ch = chunk_rows(N, c);
+  const int64_t row0 = q * ch;
+  const TB* B0 = Bas + (int64_t)bas_block * r * ldb + row0;
+  const TR* R0 = R + row0;
+  TA acc[RT];
+#pragma unroll
+  for (int j = 0; j < RT; ++j) acc[j] = TA(0);
+  for (int64_t i = lane; i < ch; i += 32) {
+    const TA x = conv<TA>(R0[i]);
+#pragma unroll
+    for (int j = 0; j < RT; ++j)
+      if (j < r) acc[j] += conv<TA>(B0[(int64_t)j * ldb + i]) * x;
+  }
+  double* Pq = P + (size_t)q * r;
+#pragma unroll
+  for (int g = 0; g < RT / 32; ++g) {
+    TA v[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = acc[g * 32 + j];
+    const TA t = warp_transpose_reduce32(v);
+    const int j = g * 32 + lane;
+    if (j < r) Pq[j] = (double)t;
+  }
+}
+
 template <typename TB, typename TR>
 cudaError_t launch_project(int64_t N, int r, int c, const TB* Bas, int64_t ldb, int bas_block, const TR* R,
                            int64_t ldr, int ncols, double* P, int acc_fp64, cudaStream_t s) {
@@ -131,6 +184,14 @@ cudaError_t launch_project(int64_t N, int r, int c, const TB* Bas, int64_t ldb, 
   using TA = typename AccOf<TR>::type;
   note_work(sizeof(TB) * (double)N * r + sizeof(TR) * (double)N * ncols + 8.0 * num_chunks(N, c) * r * ncols,
             2.0 * N * r * (double)ncols);
+  if (ncols == 1 && r > 16) {
+    const unsigned g1 = (unsigned)((num_chunks(N, c) + 7) / 8);
+    if (r <= 32)
+      { project_k1_kernel<TB, TR, TA, 32><<<g1, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, P); note_launches(1); }
+    else
+      { project_k1_kernel<TB, TR, TA, 64><<<g1, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, P); note_launches(1); }
+    return cudaGetLastError();
+  }
   if (ncols <= 8) {
     dim3 g2((unsigned)num_chunks(N, c), (r + 15) / 16);
     if (ncols == 1)
@@ -308,108 +369,50 @@ cudaError_t launch_update(int64_t N, int r, int c, const TB* Bas, int64_t ldb, i
 // pivots and row swaps are those of LU with partial pivoting, which gives
 // log|det K~| and its sign.
 __global__ void __launch_bounds__(256) coupling_factor_kernel(int64_t N, int r, int c,
-                                                              const double* __restrict__ P,
+                                                              const double* __restrict__ P, int64_t cpn_read,
                                                               double* __restrict__ Kinv,
                                                               double* __restrict__ node_ld, DevStatus* st,
                                                               int64_t heap_first) {
   extern __shared__ double sK[];
   const int n = 2 * r;
-  int* spiv = reinterpret_cast<int*>(sK + (size_t)n * n);
-  double* scol = sK + (size_t)n * n + ((n + 1) / 2);
-  __shared__ int s_piv, s_swaps, s_sing;
-  __shared__ double s_pval, s_la;
-  __shared__ int s_neg;
+  const int lda = n + 1;
+  double* scol = sK + (size_t)n * lda;
+  double* srow = scol + n;
+  double* spv = srow + n;
+  int* spiv = reinterpret_cast<int*>(spv + n);
+  int* spos = spiv + n;
+  __shared__ double s_la;
+  __shared__ int s_neg, s_sing;
   const int64_t j = blockIdx.x;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int64_t cpn = chunks_per_node(N, c);
   const size_t slot = (size_t)r * r * c;
   const int anc = r * (c - 1);
   const int64_t qa = 2 * j * cpn, qb = (2 * j + 1) * cpn;
-  if (tid == 0) { s_swaps = 0; s_sing = -1; s_la = 0.0; s_neg = 0; }
   for (int e = tid; e < n * n; e += nt) {
     const int row = e % n, col = e / n;
     double v = (row == col) ? 1.0 : 0.0;
     if (row < r && col >= r) {
       double acc = 0.0;
-      for (int64_t q = 0; q < cpn; ++q) acc += P[(qb + q) * slot + (size_t)(anc + col - r) * r + row];
+      for (int64_t q = 0; q < cpn_read; ++q) acc += P[(qb + q) * slot + (size_t)(anc + col - r) * r + row];
       v = acc;
     } else if (row >= r && col < r) {
       double acc = 0.0;
-      for (int64_t q = 0; q < cpn; ++q) acc += P[(qa + q) * slot + (size_t)(anc + col) * r + (row - r)];
+      for (int64_t q = 0; q < cpn_read; ++q) acc += P[(qa + q) * slot + (size_t)(anc + col) * r + (row - r)];
       v = acc;
     }
-    sK[e] = v;
+    sK[(size_t)col * lda + row] = v;
   }
   __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    if (tid < 32) {
-      const int lane = tid;
-      double best = -1.0;
-      int bi = n;
-      for (int i = k + lane; i < n; i += 32) {
-        const double v = fabs(sK[(size_t)k * n + i]);
-        if (v > best) { best = v; bi = i; }
-      }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const double ov = __shfl_down_sync(0xffffffffu, best, off);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-      }
-      if (lane == 0) s_piv = bi < n ? bi : k;
-    }
-    __syncthreads();
-    const int p = s_piv;
-    if (p != k) {
-      for (int jj = tid; jj < n; jj += nt) {
-        const double t = sK[(size_t)jj * n + k];
-        sK[(size_t)jj * n + k] = sK[(size_t)jj * n + p];
-        sK[(size_t)jj * n + p] = t;
-      }
-    }
-    if (tid == 0) {
-      spiv[k] = p;
-      if (p != k) s_swaps ^= 1;
-    }
-    __syncthreads();
-    const double piv = sK[(size_t)k * n + k];
-    if (tid == 0) {
-      s_la += log(fabs(piv));
-      s_neg ^= (piv < 0.0);
-      if (piv == 0.0 && s_sing < 0) s_sing = k;
-    }
-    const double rp = (piv != 0.0) ? 1.0 / piv : 0.0;
-    for (int i = tid; i < n; i += nt) scol[i] = sK[(size_t)k * n + i];
-    __syncthreads();
-    for (int jj = tid; jj < n; jj += nt) {
-      if (jj != k) sK[(size_t)jj * n + k] *= rp;
-    }
-    if (tid == 0) sK[(size_t)k * n + k] = rp;
-    __syncthreads();
-    for (int e = tid; e < n * n; e += nt) {
-      const int i = e % n, jj = e / n;
-      if (i == k) continue;
-      if (jj != k) sK[e] -= scol[i] * sK[(size_t)jj * n + k];
-      else sK[e] = -scol[i] * rp;
-    }
-    __syncthreads();
-  }
-  for (int k = n - 1; k >= 0; --k) {
-    const int p = spiv[k];
-    if (p != k) {
-      for (int i = tid; i < n; i += nt) {
-        const double t = sK[(size_t)k * n + i];
-        sK[(size_t)k * n + i] = sK[(size_t)p * n + i];
-        sK[(size_t)p * n + i] = t;
-      }
-    }
-    __syncthreads();
-  }
+  gj_invert_smem<double>(sK, n, lda, spiv, spv, scol, srow, spos, &s_la, &s_neg, &s_sing);
   double* out = Kinv + (size_t)j * n * n;
-  for (int e = tid; e < n * n; e += nt) out[e] = sK[e];
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e % n, jj = e / n;
+    out[e] = sK[(size_t)spos[jj] * lda + i];
+  }
   if (tid == 0) {
     node_ld[2 * j] = s_la;
-    node_ld[2 * j + 1] = (s_sing >= 0) ? 0.0 : ((s_neg ^ s_swaps) ? -1.0 : 1.0);
+    node_ld[2 * j + 1] = (s_sing >= 0) ? 0.0 : (s_neg ? -1.0 : 1.0);
     if (s_sing >= 0) set_status(st, HODLR_ERR_SINGULAR_COUPLING, heap_first + j, s_sing);
   }
 }
@@ -419,10 +422,10 @@ cudaError_t launch_coupling_factor(const Factor& F, int c, cudaStream_t s) {
   const int r = F.d.r;
   const int n = 2 * r;
   const int64_t parents = (int64_t)1 << (c - 1);
-  const size_t sm = (size_t)n * n * sizeof(double) + (size_t)((n + 1) / 2) * sizeof(double) + n * sizeof(double);
+  const size_t sm = (size_t)n * (n + 1) * sizeof(double) + 3 * (size_t)n * sizeof(double) + 2 * (size_t)n * sizeof(int);
   cudaFuncSetAttribute(coupling_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   note_work(8.0 * num_chunks(F.d.N, c) * r * r + 8.0 * parents * n * n, parents * 2.0 / 3.0 * n * n * (double)n);
-  { coupling_factor_kernel<<<(unsigned)parents, 256, sm, s>>>(F.d.N, r, c, F.P, F.K + F.Koff[c] * n * n,
+  { coupling_factor_kernel<<<(unsigned)parents, 256, sm, s>>>(F.d.N, r, c, F.P, F.P_reduced ? 1 : chunks_per_node(F.d.N, c), F.K + F.Koff[c] * n * n,
                                                              F.node_ld + 2 * F.Koff[c], F.status,
                                                              (int64_t)1 << (c - 1)); note_launches(1); }
   return cudaGetLastError();
@@ -439,7 +442,7 @@ cudaError_t launch_coupling_factor(const Factor& F, int c, cudaStream_t s) {
 template <typename TA, int NR>
 __global__ void __launch_bounds__(256) coupling_apply_kernel(int64_t N, int r, int c, double* P, int64_t sw,
                                                              int nrhs, const double* __restrict__ Kinv,
-                                                             int first_is_beta, int trans) {
+                                                             int first_is_beta, int trans, int64_t cpn_read) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = 2 * r;
   TA* sKc = reinterpret_cast<TA*>(smem_raw);  // [n][33]: Kinv(i, kb + kk) (or Kinv^T)
@@ -460,7 +463,7 @@ __global__ void __launch_bounds__(256) coupling_apply_kernel(int64_t N, int r, i
     if (c0 + cc < nrhs) {
       const int64_t q0 = i < r ? qfirst : qsecond;
       const int row = i < r ? i : i - r;
-      for (int64_t q = 0; q < cpn; ++q) acc += P[(q0 + q) * slot + (size_t)(c0 + cc) * r + row];
+      for (int64_t q = 0; q < cpn_read; ++q) acc += P[(q0 + q) * slot + (size_t)(c0 + cc) * r + row];
     }
     sRhs[i * 33 + cc] = (TA)acc;
   }
@@ -503,7 +506,8 @@ __global__ void __launch_bounds__(256) coupling_apply_kernel(int64_t N, int r, i
 
 template <typename TA>
 static cudaError_t coupling_apply(int64_t N, int r, int c, double* P, int64_t sw, int nrhs, const double* Kinv,
-                                  int first_is_beta, int trans, cudaStream_t s) {
+                                  int first_is_beta, int trans, cudaStream_t s, int64_t cpn_read = -1) {
+  if (cpn_read < 0) cpn_read = chunks_per_node(N, c);
   if (nrhs <= 0) return cudaSuccess;
   dim3 grid(1u << (c - 1), (nrhs + 31) / 32);
   const int n = 2 * r;
@@ -512,14 +516,22 @@ static cudaError_t coupling_apply(int64_t N, int r, int c, double* P, int64_t sw
             parents * 2.0 * n * n * (double)nrhs);
   const size_t sm = (size_t)2 * n * 33 * sizeof(TA);
   if (n <= 32) {
-    { coupling_apply_kernel<TA, 4><<<grid, 256, sm, s>>>(N, r, c, P, sw, nrhs, Kinv, first_is_beta, trans); note_launches(1); }
+    { coupling_apply_kernel<TA, 4><<<grid, 256, sm, s>>>(N, r, c, P, sw, nrhs, Kinv, first_is_beta, trans, cpn_read); note_launches(1); }
   } else if (n <= 64) {
-    { coupling_apply_kernel<TA, 8><<<grid, 256, sm, s>>>(N, r, c, P, sw, nrhs, Kinv, first_is_beta, trans); note_launches(1); }
+    { coupling_apply_kernel<TA, 8><<<grid, 256, sm, s>>>(N, r, c, P, sw, nrhs, Kinv, first_is_beta, trans, cpn_read); note_launches(1); }
   } else {
     cudaFuncSetAttribute(coupling_apply_kernel<TA, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    { coupling_apply_kernel<TA, 16><<<grid, 256, sm, s>>>(N, r, c, P, sw, nrhs, Kinv, first_is_beta, trans); note_launches(1); }
+    { coupling_apply_kernel<TA, 16><<<grid, 256, sm, s>>>(N, r, c, P, sw, nrhs, Kinv, first_is_beta, trans, cpn_read); note_launches(1); }
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_coupling_apply_any(const Factor& F, int c, double* P, int64_t sw, int nrhs, int first_is_beta,
+                                      int trans, cudaStream_t s) {
+  ProfScope prof_(KC_COUPLING_APPLY, s);
+  const int r = F.d.r;
+  const double* Kc = F.K + F.Koff[c] * 4 * r * r;
+  return coupling_apply<double>(F.d.N, r, c, P, sw, nrhs, Kc, first_is_beta, trans, s);
 }
 
 // Factor: W' = Kinv [W_beta; W_alpha] for the ancestor columns of every parent.
@@ -528,8 +540,9 @@ cudaError_t launch_coupling_factor_apply(const Factor& F, int c, cudaStream_t s)
   const int r = F.d.r;
   const int anc = r * (c - 1);
   const double* Kc = F.K + F.Koff[c] * 4 * r * r;
-  if (F.prec == HODLR_PREC_FP64) return coupling_apply<double>(F.d.N, r, c, F.P, (int64_t)r * c, anc, Kc, 1, 0, s);
-  return coupling_apply<float>(F.d.N, r, c, F.P, (int64_t)r * c, anc, Kc, 1, 0, s);
+  const int64_t cr = F.P_reduced ? 1 : chunks_per_node(F.d.N, c);
+  if (F.prec == HODLR_PREC_FP64) return coupling_apply<double>(F.d.N, r, c, F.P, (int64_t)r * c, anc, Kc, 1, 0, s, cr);
+  return coupling_apply<float>(F.d.N, r, c, F.P, (int64_t)r * c, anc, Kc, 1, 0, s, cr);
 }
 
 // Skinny coupling solve (k <= 8 right-hand sides), FP64: n = 2r threads per
@@ -613,22 +626,27 @@ cudaError_t launch_coupling_solve(const Factor& F, int c, double* P, int k, int 
 // ---------------------------------------------------------------------------
 // Sum the chunk partials of each node into the node's first slot (FP64,
 // fixed order).
+// One warp per slot element: lanes sum strided chunks, then a fixed-order
+// butterfly; the result goes to the node's first slot.
 __global__ void reduce_chunks_kernel(int64_t N, int r, int c, double* P, int ncols) {
   const int64_t cpn = chunks_per_node(N, c);
   const int64_t node = blockIdx.x;
   const size_t slot = (size_t)r * ncols;
-  const int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t e = (int64_t)blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (e >= (int64_t)slot) return;
   double acc = 0.0;
-  for (int64_t q = 0; q < cpn; ++q) acc += P[(node * cpn + q) * slot + e];
-  P[node * cpn * slot + e] = acc;
+  for (int64_t q = lane; q < cpn; q += 32) acc += P[(node * cpn + q) * slot + e];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane == 0) P[node * cpn * slot + e] = acc;
 }
 
 cudaError_t launch_reduce_chunks(int64_t N, int r, int c, double* P, int ncols, cudaStream_t s) {
   ProfScope prof_(KC_REDUCE, s);
   if (chunks_per_node(N, c) == 1) return cudaSuccess;
   const size_t slot = (size_t)r * ncols;
-  dim3 grid(1u << c, (unsigned)((slot + 255) / 256));
+  dim3 grid(1u << c, (unsigned)((slot + 7) / 8));
   note_work(8.0 * ((double)num_chunks(N, c) + (double)(1ll << c)) * slot, (double)num_chunks(N, c) * slot);
   { reduce_chunks_kernel<<<grid, 256, 0, s>>>(N, r, c, P, ncols); note_launches(1); }
   return cudaGetLastError();

@@ -104,8 +104,10 @@ __global__ void __launch_bounds__(128) project_tc_kernel(const __grid_constant__
       tc::mma_commit(done);
     }
     kt_global += nk;
-    // epilogue: wait for the accumulator, drain TMEM, write the FP64 partial
+    // epilogue: wait for the accumulator, drain TMEM, write the FP64 partial.
+    // ok is made block-uniform first: tcgen05.ld is warp-collective.
     if (!tc::mbar_wait(done, item_count & 1)) ok = false;
+    ok = __syncthreads_and(ok) != 0;
     tc::tc_fence_after();
     if (ok) {
       const int m = col0 + warp * 32 + lane;
@@ -212,6 +214,158 @@ cudaError_t launch_project_tc(int64_t N, int r, int L, int c, const __nv_bfloat1
   note_work(2.0 * (double)N * r + 2.0 * (double)N * rc + 8.0 * num_chunks(N, c) * r * rc, 2.0 * N * r * (double)rc);
   if (r == 32) return project_tc_go<32>(Vp, ldv, Y, N, r * L, c, rc, P, st, s);
   return project_tc_go<64>(Vp, ldv, Y, N, r * L, c, rc, P, st, s);
+}
+
+
+// ===========================================================================
+// Tensor-core ancestor update of the BF16 factor (Eq. e:node2):
+//   Y(rows, 0:anc) -= Y(rows, own block) * W'(node),  W' FP64 r x anc (ld r).
+// Tile = 128 rows of one node (M = 128), N = up to 256 ancestor columns per
+// MMA, K = r. Y's own block is column-major, i.e. M-contiguous for this
+// product, so the CTA's threads transpose it into the K-major canonical
+// layout without swizzle (8-row x 16-byte core matrices, LBO = 128 B between
+// cores along K, SBO = r/8 * 128 B between 8-row groups); W' is converted to
+// BF16 into the same layout (N rows). The FP32 accumulator in TMEM is then
+// subtracted from the old BF16 values, 32 columns per tcgen05.ld.
+namespace {
+
+constexpr int kUpdNC = 256;  // ancestor columns per MMA chunk
+
+template <int RK>
+struct UpdSmem {
+  static constexpr uint32_t kABytes = 128 * RK * 2;
+  static constexpr uint32_t kBBytes = kUpdNC * RK * 2;
+  // padded so that at most two CTAs (2 x 256 TMEM columns) share an SM
+  static constexpr uint32_t kBytes = (kABytes + kBBytes + 192) > 100 * 1024 ? (kABytes + kBBytes + 192) : 100 * 1024;
+};
+
+}  // namespace
+
+template <int RK>
+__global__ void __launch_bounds__(256) update_tc_kernel(int64_t N, int c, __nv_bfloat16* __restrict__ Y,
+                                                        const double* __restrict__ Wbase, int64_t wstride, int anc,
+                                                        DevStatus* st) {
+  using S = UpdSmem<RK>;
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  uint8_t* sA = smem_raw;
+  uint8_t* sB = smem_raw + S::kABytes;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sB + S::kBBytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr uint32_t kSBO = (RK / 8) * 128;
+  constexpr uint32_t kTmemCols = kUpdNC;
+
+  if (tid == 0) {
+    tc::mbar_init(bar, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(tmem_slot, kTmemCols);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const int64_t n = N >> c;
+  const int64_t tiles = N / 128;
+  const int rk = RK;
+  bool ok = true;
+  uint32_t phase = 0;
+  for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+    const int64_t row0 = t * 128;
+    const int64_t node = row0 / n;
+    const double* W = Wbase + node * wstride;
+    const __nv_bfloat16* Yown = Y + (int64_t)(c - 1) * rk * N + row0;
+    // A: 128 rows x RK of the own block, K-major cores
+    for (int e = tid; e < 128 * (RK / 8); e += blockDim.x) {
+      const int m = e & 127, kg = e >> 7;
+      uint32_t pk[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const __nv_bfloat16 lo = Yown[(int64_t)(kg * 8 + 2 * q) * N + m];
+        const __nv_bfloat16 hi = Yown[(int64_t)(kg * 8 + 2 * q + 1) * N + m];
+        pk[q] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+      }
+      *reinterpret_cast<uint4*>(sA + kg * 128 + (m >> 3) * kSBO + (m & 7) * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+    for (int col0 = 0; col0 < anc && ok; col0 += kUpdNC) {
+      const int nc = (anc - col0) < kUpdNC ? (anc - col0) : kUpdNC;  // multiple of 16 (anc = r (c-1))
+      // B: nc rows (ancestor columns) x RK, K-major cores, from FP64 W'
+      for (int e = tid; e < nc * (RK / 8); e += blockDim.x) {
+        const int nn = e % nc, kg = e / nc;
+        const double* w = W + (int64_t)(col0 + nn) * rk + kg * 8;
+        uint32_t pk[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const __nv_bfloat16 lo = __float2bfloat16_rn((float)w[2 * q]);
+          const __nv_bfloat16 hi = __float2bfloat16_rn((float)w[2 * q + 1]);
+          pk[q] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+        }
+        *reinterpret_cast<uint4*>(sB + kg * 128 + (nn >> 3) * kSBO + (nn & 7) * 16) =
+            make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc::tc_fence_before();
+      __syncthreads();
+      tc::tc_fence_after();
+      if (tid == 0) {
+        const uint32_t idesc = tc::idesc_bf16_f32(128, nc);
+        const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+#pragma unroll
+        for (int ks = 0; ks < RK / 16; ++ks)
+          tc::mma_bf16(tmem, tc::desc_noswz_kmajor(a0 + ks * 256, 128, kSBO),
+                       tc::desc_noswz_kmajor(b0 + ks * 256, 128, kSBO), idesc, ks != 0);
+        tc::mma_commit(bar);
+      }
+      ok = __syncthreads_and(tc::mbar_wait(bar, phase)) != 0;  // block-uniform before warp-collective loads
+      phase ^= 1;
+      tc::tc_fence_after();
+      if (ok) {
+        // warps w and w+4 share TMEM lanes 32 (w % 4) .. +31 and split the columns
+        const int m = (warp & 3) * 32 + lane;
+        __nv_bfloat16* yrow = Y + row0 + m;
+        for (int cb = (warp >> 2) * 32; cb < nc; cb += 64) {
+          float v[32];
+          tc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + cb, v);
+          float old[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) old[j] = __bfloat162float(yrow[(int64_t)(col0 + cb + j) * N]);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) yrow[(int64_t)(col0 + cb + j) * N] = __float2bfloat16_rn(old[j] - v[j]);
+        }
+      }
+      tc::tc_fence_before();
+      __syncthreads();
+      tc::tc_fence_after();
+    }
+  }
+  if (!ok && tid == 0) set_status(st, HODLR_ERR_TIMEOUT, c, 1);
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+bool update_tc_supported(int64_t N, int r, int c) {
+  return (r == 32 || r == 64) && ((N >> c) % 128) == 0;
+}
+
+cudaError_t launch_update_tc(int64_t N, int r, int c, __nv_bfloat16* Y, const double* Wbase, int64_t wstride,
+                             DevStatus* st, cudaStream_t s) {
+  ProfScope prof_(KC_UPDATE_TC, s);
+  const int anc = r * (c - 1);
+  if (anc <= 0) return cudaSuccess;
+  note_work(2.0 * (double)N * r + 4.0 * (double)N * anc + 8.0 * (double)(1ll << c) * r * anc,
+            2.0 * N * r * (double)anc);
+  const int64_t tiles = N / 128;
+  int64_t grid = 2 * (int64_t)sm_count();
+  if (grid > tiles) grid = tiles;
+  if (r == 32) {
+    cudaFuncSetAttribute(update_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UpdSmem<32>::kBytes);
+    { update_tc_kernel<32><<<(unsigned)grid, 256, UpdSmem<32>::kBytes, s>>>(N, c, Y, Wbase, wstride, anc, st); note_launches(1); }
+  } else {
+    cudaFuncSetAttribute(update_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UpdSmem<64>::kBytes);
+    { update_tc_kernel<64><<<(unsigned)grid, 256, UpdSmem<64>::kBytes, s>>>(N, c, Y, Wbase, wstride, anc, st); note_launches(1); }
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace hodlr

@@ -25,8 +25,18 @@ Workloads (structure of the paper's Sec. 4 experiments; real field):
 from __future__ import annotations
 
 import math
+import os
+import sys
+import time
 
 import torch
+
+_VERBOSE = os.environ.get("HODLR_SYNTH_VERBOSE", "") not in ("", "0")
+
+
+def _log(msg):
+    if _VERBOSE:
+        sys.stderr.write(f"[synth] {msg}\n")
 
 from .generators import HodlrShape
 
@@ -92,7 +102,16 @@ def kd_order(pts: torch.Tensor, m: int) -> torch.Tensor:
 
 # ------------------------------------------------------------------ compression
 def _qr(Y):
+    """Orthonormal basis of the range of each (tall) matrix in the batch, in
+    the matrix's own precision on its own device."""
     return torch.linalg.qr(Y, mode="reduced")[0]
+
+
+def _svd(B):
+    """SVD of small wide matrices (rank-r core factors): on the CPU in FP64,
+    where LAPACK handles batches of small matrices quickly."""
+    U, S, Vh = torch.linalg.svd(B.double().cpu(), full_matrices=False)
+    return U.to(B.device, B.dtype), S.to(B.device, B.dtype), Vh.to(B.device, B.dtype)
 
 
 def _rsvd_blocks(entries, row_start, col_start, n, r, g, device, oversample=10, budget=1 << 27):
@@ -134,7 +153,7 @@ def _rsvd_blocks(entries, row_start, col_start, n, r, g, device, oversample=10, 
         Q = _qr(times(Om))
         Q = _qr(times(_qr(ttimes(Q))))
         Bt = ttimes(Q)                                  # block^T Q
-        Ub_, S, Vh = torch.linalg.svd(Bt.transpose(1, 2), full_matrices=False)
+        Ub_, S, Vh = _svd(Bt.transpose(1, 2))
         sq = torch.sqrt(S[:, :r])
         Uo[b0:b1] = (Q @ Ub_[:, :, :r]) * sq[:, None, :]
         Vo[b0:b1] = Vh[:, :r, :].transpose(1, 2) * sq[:, None, :]
@@ -158,16 +177,19 @@ def _cur_blocks(entries, row_start, col_start, n, r, s, g, device, budget=1 << 2
         I = torch.rand(nb, n, generator=g, device=device).argsort(dim=1)[:, :s].sort(dim=1).values
         rows = row_start[b0:b1, None] + ar[None, :]
         cols = col_start[b0:b1, None] + ar[None, :]
-        C = entries(rows, col_start[b0:b1, None] + J).double()                 # (nb, n, s)
-        R = entries(row_start[b0:b1, None] + I, cols).double()                 # (nb, s, n)
-        W = entries(row_start[b0:b1, None] + I, col_start[b0:b1, None] + J).double()
-        Qc, Rc = torch.linalg.qr(C, mode="reduced")
+        C = entries(rows, col_start[b0:b1, None] + J)                          # (nb, n, s)
+        R = entries(row_start[b0:b1, None] + I, cols)                          # (nb, s, n)
+        W = entries(row_start[b0:b1, None] + I, col_start[b0:b1, None] + J)
+        Qc, Rc = torch.linalg.qr(C, mode="reduced")                            # tall QRs: device, FP32
         Qr, Rr = torch.linalg.qr(R.transpose(1, 2), mode="reduced")
+        Rc, Rr, W = (t.double().cpu() for t in (Rc, Rr, W))                    # s x s cores: CPU, FP64
         M = Rc @ torch.linalg.pinv(W, rtol=1e-12) @ Rr.transpose(1, 2)
         Um, Sm, Vmh = torch.linalg.svd(M)
         sq = torch.sqrt(Sm[:, :r])
-        Uo[b0:b1] = ((Qc @ Um[:, :, :r]) * sq[:, None, :]).float()
-        Vo[b0:b1] = ((Qr @ Vmh.transpose(1, 2)[:, :, :r]) * sq[:, None, :]).float()
+        Ucore = (Um[:, :, :r] * sq[:, None, :]).float().to(device)
+        Vcore = (Vmh.transpose(1, 2)[:, :, :r] * sq[:, None, :]).float().to(device)
+        Uo[b0:b1] = Qc @ Ucore
+        Vo[b0:b1] = Qr @ Vcore
     return Uo, Vo
 
 
@@ -195,6 +217,7 @@ def _assemble(shape: HodlrShape, leaf_fn, entries, seed, device, symmetric):
     Vt = torch.empty(shape.rL, N, device=device, dtype=torch.float64)
     for c in range(1, L + 1):
         n = N >> c
+        t0 = time.time()
         cols = slice((c - 1) * r, c * r)
         if symmetric:
             # blocks A(I_left, I_right) of the 2^(c-1) pairs; U = V by the symmetric split
@@ -210,6 +233,10 @@ def _assemble(shape: HodlrShape, leaf_fn, entries, seed, device, symmetric):
             Ub, Vb = compress_blocks(entries, b * n, (b ^ 1) * n, n, r, g, device)
             Ut[cols] = Ub.transpose(1, 2).permute(1, 0, 2).reshape(r, N).double()
             Vt[cols] = Vb[b ^ 1].transpose(1, 2).permute(1, 0, 2).reshape(r, N).double()
+        if _VERBOSE:
+            if Ut.is_cuda:
+                torch.cuda.synchronize()
+            _log(f"level {c}: blocks of {n} rows in {time.time() - t0:.2f} s")
     return D, Ut.T, Vt.T
 
 
