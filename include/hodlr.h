@@ -62,7 +62,8 @@ typedef enum {
   HODLR_ERR_SINGULAR_COUPLING = 5, /* exact zero pivot in a 2r x 2r coupling LU (where = heap node, detail = column) */
   HODLR_ERR_NONFINITE = 6,         /* NaN or Inf in D (where = leaf) */
   HODLR_ERR_NOT_CONVERGED = 7,     /* refinement / GMRES hit its iteration limit */
-  HODLR_ERR_TIMEOUT = 8            /* a device-side wait gave up after its spin limit (where = child level) */
+  HODLR_ERR_TIMEOUT = 8,           /* a device-side wait gave up after its spin limit (where = child level) */
+  HODLR_ERR_SCRATCH_LIMIT = 9      /* problem too large for hodlr_matvec_noalloc's fixed scratch */
 } hodlr_status;
 
 /* Arithmetic of the factorization (not of the input, which is always FP64).
@@ -163,6 +164,25 @@ HODLR_API hodlr_status hodlr_matvec_workspace_size(const hodlr_desc* desc, int32
 HODLR_API hodlr_status hodlr_matvec(const hodlr_desc* desc, const double* D, const double* U, const double* V,
                           const double* X, int64_t ldx, double* Y, int64_t ldy, int32_t k,
                           void* workspace, size_t workspace_bytes, hodlr_stream_t stream);
+
+/* Allocation-free variant of hodlr_matvec (no counterpart in the paper; a
+ * service for callers that cannot allocate device memory where they need
+ * A X: code inside a CUDA-graph capture that must not add allocation nodes,
+ * plug-ins whose host application owns all device memory, real-time loops
+ * where allocation latency or failure is not acceptable). It computes the
+ * same FP64 Y = A X with the same kernels, but takes its scratch from one
+ * fixed 32 MiB array of device memory defined by the library itself (every
+ * GPU that loads the library holds it until the process exits) instead of a
+ * caller workspace; it calls no allocator. The scratch needed is
+ * hodlr_matvec_workspace_size(desc, k); larger problems are rejected with
+ * HODLR_ERR_SCRATCH_LIMIT before anything is enqueued. The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture. All
+ * calls share the array: calls that overlap on the GPU race and must be
+ * serialized by the caller. Nothing in the scratch needs to start at zero. */
+HODLR_API hodlr_status hodlr_matvec_noalloc(const hodlr_desc* desc, const double* D, const double* U, const double* V,
+                                            const double* X, int64_t ldx, double* Y, int64_t ldy, int32_t k,
+                                            hodlr_stream_t stream);
 
 /* ------------------------------------------------------- refined solvers --
  * Mixed-precision solves recovered to FP64 accuracy. The factor f (any

@@ -30,6 +30,7 @@ HODLR_ERR_SINGULAR_COUPLING = 5
 HODLR_ERR_NONFINITE = 6
 HODLR_ERR_NOT_CONVERGED = 7
 HODLR_ERR_TIMEOUT = 8
+HODLR_ERR_SCRATCH_LIMIT = 9
 
 PREC = {"fp64": 0, "fp32": 1, "bf16": 3}
 
@@ -39,6 +40,7 @@ EXPORTED = (
     "hodlr_matvec_workspace_size", "hodlr_matvec", "hodlr_refine_workspace_size", "hodlr_solve_refined",
     "hodlr_gmres", "hodlr_launch_count", "hodlr_profile_enable", "hodlr_profile_reset", "hodlr_profile_read",
     "hodlr_profile_name", "hodlr_profile_work", "hodlr_tc_enable", "hodlr_grad_workspace_size", "hodlr_grad",
+    "hodlr_matvec_noalloc",
 )
 
 
@@ -79,6 +81,7 @@ _SIGS = {
     "hodlr_profile_name": ([_i32], _c.c_char_p),
     "hodlr_profile_work": ([_c.POINTER(_dbl), _c.POINTER(_dbl), _i32], _i32),
     "hodlr_tc_enable": ([_i32], None),
+    "hodlr_matvec_noalloc": ([_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64, _i32, _vp], _c.c_int),
     "hodlr_grad_workspace_size": ([_vp, _i32, _c.POINTER(_sz)], _c.c_int),
     "hodlr_grad": ([_vp, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp, _i64, _vp, _sz, _vp, _c.POINTER(_dbl)],
                    _c.c_int),
@@ -352,3 +355,16 @@ def hodlr_grad(F: FactorHandle, U, V, B, want_loss: bool = True):
                            _ptr(ws), ws.numel(), _stream(), ctypes.byref(loss) if want_loss else None),
            "hodlr_grad: ")
     return (loss.value if want_loss else None), dD, dU, dV, dB
+
+
+def hodlr_matvec_noalloc(D, U, V, L: int, r: int, X: torch.Tensor, Y: torch.Tensor) -> torch.Tensor:
+    """Y = A X in FP64 without any allocation by the library or this wrapper:
+    the library's fixed device scratch replaces the workspace. Y must be
+    preallocated (column-major)."""
+    N = U.shape[0]
+    _check_D(D, N, L)
+    desc = make_desc(N, L, r, U, V)
+    ldx, ldy = _ld(X, N), _ld(Y, N)
+    _check(_LIB.hodlr_matvec_noalloc(ctypes.byref(desc), _ptr(D), _ptr(U), _ptr(V), _ptr(X), ldx, _ptr(Y), ldy,
+                                     X.shape[1], _stream()), "hodlr_matvec_noalloc: ")
+    return Y

@@ -266,6 +266,13 @@ bool valid_factor(const Factor* F) { return F != nullptr; }
 
 size_t factor_workspace_bytes(const hodlr_desc& d, hodlr_prec prec) { return factor_layout(d, prec).total; }
 
+// Entry points for the allocation-free matvec (noalloc.cu).
+hodlr_status matvec_core_ext(const hodlr_desc& d, const double* D, const double* U, const double* V, const double* X,
+                             int64_t ldx, double* Y, int64_t ldy, int k, void* work, cudaStream_t s) {
+  return matvec_core(d, D, U, V, X, ldx, Y, ldy, k, work, s);
+}
+size_t matvec_scratch_bytes(const hodlr_desc& d, int k) { return matvec_ws_bytes(d, k); }
+
 }  // namespace hodlr
 
 using namespace hodlr;
@@ -285,6 +292,7 @@ const char* hodlr_strerror(hodlr_status s) {
     case HODLR_ERR_NONFINITE: return "non-finite input";
     case HODLR_ERR_NOT_CONVERGED: return "iteration did not converge";
     case HODLR_ERR_TIMEOUT: return "device-side wait timed out";
+    case HODLR_ERR_SCRATCH_LIMIT: return "problem exceeds the fixed scratch of the allocation-free entry point";
   }
   return "unknown status";
 }
