@@ -39,6 +39,9 @@ WORKLOADS = {
     "bie-2^20": dict(N=1 << 20, L=13, r=32, k=1, prec="bf16", solver="gmres", shift=4.0, seed=2,
                      data="bie", desc="2D Laplace second-kind BIE on the star curve, N=2^20, leaf 128, rank 32, "
                                       "1 RHS; BF16-panel factor as FGMRES preconditioner to relres 1e-10"),
+    "bie-2^17": dict(N=1 << 17, L=10, r=32, k=1, prec="bf16", solver="gmres", shift=4.0, seed=2,
+                     data="bie", desc="2D Laplace BIE on the star curve, N=2^17, leaf 128, rank 32, 1 RHS (small "
+                                      "case of the same structure, for profiler captures)"),
     "synthetic-4096": dict(N=4096, L=6, r=16, k=1, prec="fp64", solver="direct", shift=4.0, seed=0,
                            data="synthetic", desc="synthetic HODLR N=4096, leaf 64, rank 16, FP64"),
     "gaussian-2^18": dict(N=1 << 18, L=10, r=64, k=16, prec="fp32", solver="refine", shift=0.0, seed=1,

@@ -105,4 +105,36 @@ __device__ void gj_invert_smem(T* A, int n, int lda, int* spiv, T* spv, T* scol,
   __syncthreads();
 }
 
+// C (m x n, ldc) = alpha * A (m x k, lda) * B (k x n, ldb) + beta * C, all in
+// shared memory, column-major, by the whole CTA (warps over columns of C,
+// lanes over rows). Callers separate dependent calls with __syncthreads.
+template <typename T>
+__device__ void smem_gemm(int m, int n, int k, T alpha, const T* A, int lda, const T* B, int ldb, T beta, T* C,
+                          int ldc) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = warp; j < n; j += nw) {
+    for (int i = lane; i < m; i += 32) {
+      T acc = T(0);
+      for (int t = 0; t < k; ++t) acc += A[(size_t)t * lda + i] * B[(size_t)j * ldb + t];
+      C[(size_t)j * ldc + i] = alpha * acc + (beta != T(0) ? beta * C[(size_t)j * ldc + i] : T(0));
+    }
+  }
+}
+
+// After gj_invert_smem: put the inverse's columns in order (column j of the
+// inverse is column spos[j] of A), using tmp (n x n, ld n) as scratch.
+template <typename T>
+__device__ void gj_unscramble(T* A, int n, int lda, const int* spos, T* tmp) {
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    tmp[(size_t)j * n + i] = A[(size_t)spos[j] * lda + i];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    A[(size_t)j * lda + i] = tmp[(size_t)j * n + i];
+  }
+  __syncthreads();
+}
+
 }  // namespace hodlr

@@ -10,42 +10,78 @@ namespace hodlr {
 
 // One CTA per leaf: D_b (FP64) -> FP32 in shared memory -> D_b^{-1} (FP32) in
 // the factor's leaf buffer, log|det D_b| and sign, status on a zero pivot or
-// a non-finite entry.
+// a non-finite entry. Leaves of up to 64 rows are inverted by Gauss-Jordan
+// with partial pivoting directly; larger leaves (up to 128 rows) as 2 x 2
+// blocks [[A, B], [C, E]] with a 64-row leading block:
+//   X = A^{-1} B, S = E - C X, Y = C A^{-1}, Z = S^{-1} Y,
+//   D^{-1} = [[A^{-1} + X Z, -X S^{-1}], [-Z, S^{-1}]],
+// each of A and S inverted by Gauss-Jordan with partial pivoting within the
+// block (log|det D| = log|det A| + log|det S|).
 __global__ void __launch_bounds__(256) leaf_inv_kernel(int m, const double* __restrict__ D, float* __restrict__ Dinv,
                                                        double* __restrict__ leaf_ld, DevStatus* st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lda = m + 1;
   float* A = reinterpret_cast<float*>(smem_raw);
-  float* scol = A + (size_t)m * lda;
-  float* srow = scol + m;
-  float* spv = srow + m;
-  int* spiv = reinterpret_cast<int*>(spv + m);
-  int* spos = spiv + m;
-  __shared__ double s_la;
-  __shared__ int s_neg, s_sing, s_bad;
+  float* T = A + (size_t)m * lda;  // 64 x 64 scratch
+  float* scol = T + 64 * 64;
+  float* srow = scol + 64;
+  float* spv = srow + 64;
+  int* spiv = reinterpret_cast<int*>(spv + 64);
+  int* spos = spiv + 64;
+  __shared__ double s_la1, s_la2;
+  __shared__ int s_neg1, s_neg2, s_sing1, s_sing2, s_bad;
   const int b = blockIdx.x;
-  if (threadIdx.x == 0) s_bad = 0;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) { s_bad = 0; s_la2 = 0.0; s_neg2 = 0; s_sing2 = -1; }
   __syncthreads();
   const double* Db = D + (size_t)b * m * m;
   int bad = 0;
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+  for (int e = tid; e < m * m; e += nt) {
     const double v = Db[e];
     bad |= !isfinite(v);
     A[(size_t)(e / m) * lda + (e % m)] = (float)v;
   }
   if (bad) atomicOr(&s_bad, 1);
   __syncthreads();
-  if (s_bad && threadIdx.x == 0) set_status(st, HODLR_ERR_NONFINITE, b, 0);
-  gj_invert_smem<float>(A, m, lda, spiv, spv, scol, srow, spos, &s_la, &s_neg, &s_sing);
-  float* out = Dinv + (size_t)b * m * m;
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    const int i = e % m, j = e / m;
-    out[e] = A[(size_t)spos[j] * lda + i];
+  if (s_bad && tid == 0) set_status(st, HODLR_ERR_NONFINITE, b, 0);
+  const int m1 = m > 64 ? 64 : m, m2 = m - m1;
+  float* A11 = A;
+  float* A12 = A + (size_t)m1 * lda;
+  float* A21 = A + m1;
+  float* A22 = A + (size_t)m1 * lda + m1;
+  gj_invert_smem<float>(A11, m1, lda, spiv, spv, scol, srow, spos, &s_la1, &s_neg1, &s_sing1);
+  gj_unscramble<float>(A11, m1, lda, spos, T);
+  if (m2 > 0) {
+    smem_gemm<float>(m1, m2, m1, 1.f, A11, lda, A12, lda, 0.f, T, m1);  // X = A^{-1} B
+    __syncthreads();
+    for (int e = tid; e < m1 * m2; e += nt) A12[(size_t)(e / m1) * lda + e % m1] = T[e];
+    __syncthreads();
+    smem_gemm<float>(m2, m2, m1, -1.f, A21, lda, A12, lda, 1.f, A22, lda);  // S = E - C X
+    __syncthreads();
+    smem_gemm<float>(m2, m1, m1, 1.f, A21, lda, A11, lda, 0.f, T, m2);  // Y = C A^{-1}
+    __syncthreads();
+    for (int e = tid; e < m2 * m1; e += nt) A21[(size_t)(e / m2) * lda + e % m2] = T[e];
+    __syncthreads();
+    gj_invert_smem<float>(A22, m2, lda, spiv, spv, scol, srow, spos, &s_la2, &s_neg2, &s_sing2);
+    gj_unscramble<float>(A22, m2, lda, spos, T);
+    smem_gemm<float>(m2, m1, m2, 1.f, A22, lda, A21, lda, 0.f, T, m2);  // Z = S^{-1} Y
+    __syncthreads();
+    for (int e = tid; e < m2 * m1; e += nt) A21[(size_t)(e / m2) * lda + e % m2] = -T[e];  // [21] = -Z
+    __syncthreads();
+    smem_gemm<float>(m1, m1, m2, -1.f, A12, lda, A21, lda, 1.f, A11, lda);  // [11] = A^{-1} + X Z
+    __syncthreads();
+    smem_gemm<float>(m1, m2, m2, 1.f, A12, lda, A22, lda, 0.f, T, m1);  // X S^{-1}
+    __syncthreads();
+    for (int e = tid; e < m1 * m2; e += nt) A12[(size_t)(e / m1) * lda + e % m1] = -T[e];  // [12]
+    __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    leaf_ld[2 * b] = s_la;
-    leaf_ld[2 * b + 1] = s_sing >= 0 ? 0.0 : (s_neg ? -1.0 : 1.0);
-    if (s_sing >= 0) set_status(st, HODLR_ERR_SINGULAR_LEAF, b, s_sing);
+  float* out = Dinv + (size_t)b * m * m;
+  for (int e = tid; e < m * m; e += nt) out[e] = A[(size_t)(e / m) * lda + (e % m)];
+  if (tid == 0) {
+    const int sing = s_sing1 >= 0 ? s_sing1 : (s_sing2 >= 0 ? m1 + s_sing2 : -1);
+    leaf_ld[2 * b] = s_la1 + s_la2;
+    leaf_ld[2 * b + 1] = sing >= 0 ? 0.0 : ((s_neg1 ^ s_neg2) ? -1.0 : 1.0);
+    if (sing >= 0) set_status(st, HODLR_ERR_SINGULAR_LEAF, b, sing);
   }
 }
 
@@ -54,7 +90,7 @@ bool leaf_uses_inverse(const Factor& F) { return F.prec != HODLR_PREC_FP64 && F.
 cudaError_t launch_leaf_inv(const Factor& F, const double* D, cudaStream_t s) {
   const int m = F.d.m;
   const int nleaf = 1 << F.d.L;
-  const size_t sm = (size_t)m * (m + 1) * 4 + 3 * (size_t)m * 4 + 2 * (size_t)m * 4;
+  const size_t sm = (size_t)m * (m + 1) * 4 + 64 * 64 * 4 + 3 * 64 * 4 + 2 * 64 * 4;
   note_work((8.0 + 4.0) * nleaf * m * m, 2.0 * (double)m * m * m * nleaf);
   cudaFuncSetAttribute(leaf_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   { leaf_inv_kernel<<<nleaf, 256, sm, s>>>(m, D, static_cast<float*>(F.lu), F.leaf_ld, F.status); note_launches(1); }

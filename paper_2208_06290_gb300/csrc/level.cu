@@ -363,24 +363,29 @@ cudaError_t launch_update(int64_t N, int r, int c, const TB* Bas, int64_t ldb, i
 
 // ---------------------------------------------------------------------------
 // K4: coupling matrices of the parents of child level c, in FP64.
-// K~ = [[I, T_beta], [T_alpha, I]] with T_x = V_x^T Y_x summed over the chunk
-// partials of child x (own block = slot columns r(c-1) .. rc-1). The inverse
-// is computed in place by Gauss-Jordan elimination with partial pivoting; its
-// pivots and row swaps are those of LU with partial pivoting, which gives
-// log|det K~| and its sign.
+// K~ = [[I, T_b], [T_a, I]] with T_x = V_x^T Y_x summed over the chunk
+// partials of child x (own block = slot columns r(c-1) .. rc-1). Its diagonal
+// blocks are identities, so (the pivot-free use of this form) its inverse
+// follows from the Schur complement S = I - T_a T_b (r x r):
+//   K~^{-1} = [[I + T_b S^{-1} T_a, -T_b S^{-1}], [-S^{-1} T_a, S^{-1}]],
+// det K~ = det S. S is inverted in shared memory by Gauss-Jordan with partial
+// pivoting (gj.cuh), which also gives log|det S| and its sign.
 __global__ void __launch_bounds__(256) coupling_factor_kernel(int64_t N, int r, int c,
                                                               const double* __restrict__ P, int64_t cpn_read,
                                                               double* __restrict__ Kinv,
                                                               double* __restrict__ node_ld, DevStatus* st,
                                                               int64_t heap_first) {
   extern __shared__ double sK[];
-  const int n = 2 * r;
-  const int lda = n + 1;
-  double* scol = sK + (size_t)n * lda;
-  double* srow = scol + n;
-  double* spv = srow + n;
-  int* spiv = reinterpret_cast<int*>(spv + n);
-  int* spos = spiv + n;
+  const int lds = r + 1;
+  double* Sm = sK;                       // r x r (ld r+1): S, then S^{-1}
+  double* Ta = Sm + (size_t)r * lds;     // r x r (ld r)
+  double* Tb = Ta + (size_t)r * r;       // r x r (ld r)
+  double* M1 = Tb + (size_t)r * r;       // r x r (ld r): S^{-1} T_a, also GJ scratch
+  double* scol = M1 + (size_t)r * r;
+  double* srow = scol + r;
+  double* spv = srow + r;
+  int* spiv = reinterpret_cast<int*>(spv + r);
+  int* spos = spiv + r;
   __shared__ double s_la;
   __shared__ int s_neg, s_sing;
   const int64_t j = blockIdx.x;
@@ -389,31 +394,52 @@ __global__ void __launch_bounds__(256) coupling_factor_kernel(int64_t N, int r, 
   const size_t slot = (size_t)r * r * c;
   const int anc = r * (c - 1);
   const int64_t qa = 2 * j * cpn, qb = (2 * j + 1) * cpn;
-  for (int e = tid; e < n * n; e += nt) {
-    const int row = e % n, col = e / n;
-    double v = (row == col) ? 1.0 : 0.0;
-    if (row < r && col >= r) {
-      double acc = 0.0;
-      for (int64_t q = 0; q < cpn_read; ++q) acc += P[(qb + q) * slot + (size_t)(anc + col - r) * r + row];
-      v = acc;
-    } else if (row >= r && col < r) {
-      double acc = 0.0;
-      for (int64_t q = 0; q < cpn_read; ++q) acc += P[(qa + q) * slot + (size_t)(anc + col) * r + (row - r)];
-      v = acc;
+  for (int e = tid; e < r * r; e += nt) {
+    const int row = e % r, col = e / r;
+    double a = 0.0, b = 0.0;
+    for (int64_t q = 0; q < cpn_read; ++q) {
+      a += P[(qa + q) * slot + (size_t)(anc + col) * r + row];
+      b += P[(qb + q) * slot + (size_t)(anc + col) * r + row];
     }
-    sK[(size_t)col * lda + row] = v;
+    Ta[e] = a;
+    Tb[e] = b;
   }
   __syncthreads();
-  gj_invert_smem<double>(sK, n, lda, spiv, spv, scol, srow, spos, &s_la, &s_neg, &s_sing);
+  smem_gemm<double>(r, r, r, -1.0, Ta, r, Tb, r, 0.0, Sm, lds);  // S = -T_a T_b
+  __syncthreads();
+  for (int e = tid; e < r; e += nt) Sm[(size_t)e * lds + e] += 1.0;  // S = I - T_a T_b
+  __syncthreads();
+  gj_invert_smem<double>(Sm, r, lds, spiv, spv, scol, srow, spos, &s_la, &s_neg, &s_sing);
+  gj_unscramble<double>(Sm, r, lds, spos, M1);
+  smem_gemm<double>(r, r, r, 1.0, Sm, lds, Ta, r, 0.0, M1, r);  // M1 = S^{-1} T_a
+  __syncthreads();
+  const int n = 2 * r;
   double* out = Kinv + (size_t)j * n * n;
-  for (int e = tid; e < n * n; e += nt) {
-    const int i = e % n, jj = e / n;
-    out[e] = sK[(size_t)spos[jj] * lda + i];
+  // [11] = I + T_b M1, [12] = -T_b S^{-1}, [21] = -M1, [22] = S^{-1}
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int col = warp; col < n; col += nw) {
+    for (int row = lane; row < n; row += 32) {
+      double v;
+      if (row < r && col < r) {
+        double acc = (row == col) ? 1.0 : 0.0;
+        for (int t = 0; t < r; ++t) acc += Tb[(size_t)t * r + row] * M1[(size_t)col * r + t];
+        v = acc;
+      } else if (row < r) {
+        double acc = 0.0;
+        for (int t = 0; t < r; ++t) acc += Tb[(size_t)t * r + row] * Sm[(size_t)(col - r) * lds + t];
+        v = -acc;
+      } else if (col < r) {
+        v = -M1[(size_t)col * r + (row - r)];
+      } else {
+        v = Sm[(size_t)(col - r) * lds + (row - r)];
+      }
+      out[(size_t)col * n + row] = v;
+    }
   }
   if (tid == 0) {
     node_ld[2 * j] = s_la;
     node_ld[2 * j + 1] = (s_sing >= 0) ? 0.0 : (s_neg ? -1.0 : 1.0);
-    if (s_sing >= 0) set_status(st, HODLR_ERR_SINGULAR_COUPLING, heap_first + j, s_sing);
+    if (s_sing >= 0) set_status(st, HODLR_ERR_SINGULAR_COUPLING, heap_first + j, r + s_sing);
   }
 }
 
@@ -422,8 +448,10 @@ cudaError_t launch_coupling_factor(const Factor& F, int c, cudaStream_t s) {
   const int r = F.d.r;
   const int n = 2 * r;
   const int64_t parents = (int64_t)1 << (c - 1);
-  const size_t sm = (size_t)n * (n + 1) * sizeof(double) + 3 * (size_t)n * sizeof(double) + 2 * (size_t)n * sizeof(int);
-  cudaFuncSetAttribute(coupling_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const size_t sm = ((size_t)r * (r + 1) + 3 * (size_t)r * r + 3 * (size_t)r) * sizeof(double) +
+                    2 * (size_t)r * sizeof(int);
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute(coupling_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   note_work(8.0 * num_chunks(F.d.N, c) * r * r + 8.0 * parents * n * n, parents * 2.0 / 3.0 * n * n * (double)n);
   { coupling_factor_kernel<<<(unsigned)parents, 256, sm, s>>>(F.d.N, r, c, F.P, F.P_reduced ? 1 : chunks_per_node(F.d.N, c), F.K + F.Koff[c] * n * n,
                                                              F.node_ld + 2 * F.Koff[c], F.status,

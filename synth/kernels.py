@@ -101,10 +101,27 @@ def kd_order(pts: torch.Tensor, m: int) -> torch.Tensor:
 
 
 # ------------------------------------------------------------------ compression
+def _orth(Y, rtol=1e-13):
+    """(Q, R) with Y ~= Q R and Q's columns orthonormal, spanning the
+    numerically significant range of each (tall) matrix of the batch: the
+    Gram matrix Y^T Y is formed by a device matmul in FP64, its (small)
+    eigendecomposition is done on the CPU, Q = Y E diag(lambda)^{-1/2} on the
+    device; directions with lambda <= rtol * lambda_max are dropped (their
+    columns of Q are zero). Only matmuls and elementwise operations run on
+    the device."""
+    Yd = Y.double()
+    G = (Yd.transpose(1, 2) @ Yd).cpu()
+    lam, E = torch.linalg.eigh(G)
+    keep = lam > rtol * lam[:, -1:].clamp(min=1e-300)
+    inv_sqrt = torch.where(keep, lam.clamp(min=1e-300).rsqrt(), torch.zeros_like(lam))
+    sq = torch.where(keep, lam.clamp(min=0).sqrt(), torch.zeros_like(lam))
+    Q = (Yd @ (E * inv_sqrt[:, None, :]).to(Y.device)).to(Y.dtype)
+    R = (sq[:, :, None] * E.transpose(1, 2))                      # CPU, FP64
+    return Q, R
+
+
 def _qr(Y):
-    """Orthonormal basis of the range of each (tall) matrix in the batch, in
-    the matrix's own precision on its own device."""
-    return torch.linalg.qr(Y, mode="reduced")[0]
+    return _orth(Y)[0]
 
 
 def _svd(B):
@@ -180,9 +197,9 @@ def _cur_blocks(entries, row_start, col_start, n, r, s, g, device, budget=1 << 2
         C = entries(rows, col_start[b0:b1, None] + J)                          # (nb, n, s)
         R = entries(row_start[b0:b1, None] + I, cols)                          # (nb, s, n)
         W = entries(row_start[b0:b1, None] + I, col_start[b0:b1, None] + J)
-        Qc, Rc = torch.linalg.qr(C, mode="reduced")                            # tall QRs: device, FP32
-        Qr, Rr = torch.linalg.qr(R.transpose(1, 2), mode="reduced")
-        Rc, Rr, W = (t.double().cpu() for t in (Rc, Rr, W))                    # s x s cores: CPU, FP64
+        Qc, Rc = _orth(C)                                                      # Q on the device, R on the CPU
+        Qr, Rr = _orth(R.transpose(1, 2))
+        W = W.double().cpu()                                                   # s x s cores: CPU, FP64
         M = Rc @ torch.linalg.pinv(W, rtol=1e-12) @ Rr.transpose(1, 2)
         Um, Sm, Vmh = torch.linalg.svd(M)
         sq = torch.sqrt(Sm[:, :r])
