@@ -92,7 +92,7 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t status, ld_out, leaf_ld, node_ld, lu, perm, Y, Vp, K, P, total;
+  size_t status, ld_out, leaf_ld, node_ld, lu, perm, Y, Vp, K, P, rhs16, total;
 };
 
 size_t panel_elem_bytes(hodlr_prec p) {
@@ -133,6 +133,7 @@ Layout factor_layout(const hodlr_desc& d, hodlr_prec prec) {
   l.Vp = prec == HODLR_PREC_FP64 ? 0 : take(N * rL * tp);
   l.K = take((nleaf - 1) * 4 * (size_t)d.r * d.r * sizeof(double) + 16);
   l.P = take(max_partial_elems(d, 1, 0) * sizeof(double));
+  l.rhs16 = prec == HODLR_PREC_BF16 ? take(rhs_bf16_bytes(d)) : 0;
   l.total = off;
   return l;
 }
@@ -178,17 +179,19 @@ hodlr_status factor_levels(Factor& F, cudaStream_t s) {
     if (F.P_reduced) HODLR_CUDA(launch_reduce_chunks(d.N, d.r, c, F.P, rc, s));
     HODLR_CUDA(launch_coupling_factor(F, c, s));
     if (anc > 0) {
-      HODLR_CUDA(launch_coupling_factor_apply(F, c, s));
       const int64_t wstride = chunks_per_node(d.N, c) * (int64_t)d.r * rc;
       bool done = false;
       if constexpr (std::is_same<TP, __nv_bfloat16>::value) {
         if (g_use_tc && update_tc_supported(d.N, d.r, c)) {
-          HODLR_CUDA(launch_update_tc(d.N, d.r, c, Y, F.P, wstride, F.status, s));
+          // W' = K~^{-1} [W_beta; W_alpha] applied inside the update
+          HODLR_CUDA(launch_update_coupled_tc(F, c, s));
           done = true;
         }
       }
-      if (!done)
+      if (!done) {
+        HODLR_CUDA(launch_coupling_factor_apply(F, c, s));
         HODLR_CUDA(launch_update<TP, TP>(d.N, d.r, c, Y, d.N, c - 1, Y, d.N, anc, F.P, wstride, 0, -1.0, 0, s));
+      }
     }
     F.P_reduced = false;
   }
@@ -245,11 +248,23 @@ size_t solve_ws_bytes(const Factor& F, int k) {
   return b;
 }
 
-size_t matvec_ws_bytes(const hodlr_desc& d, int k) { return solve_partials_bytes(d, k); }
+// Minimum matvec scratch (per-level partials); with k = 1 a workspace of
+// matvec_ws_bytes also enables the four-launch path of matvec1.cu.
+size_t matvec_min_bytes(const hodlr_desc& d, int k) { return solve_partials_bytes(d, k); }
+size_t matvec_fast_bytes(const hodlr_desc& d) { return align_up(matvec1_scratch_elems(d) * sizeof(double)); }
+size_t matvec_ws_bytes(const hodlr_desc& d, int k) {
+  const size_t a = matvec_min_bytes(d, k);
+  return k == 1 ? std::max(a, matvec_fast_bytes(d)) : a;
+}
 
 hodlr_status matvec_core(const hodlr_desc& d, const double* D, const double* U, const double* V, const double* X,
-                         int64_t ldx, double* Y, int64_t ldy, int k, void* work, cudaStream_t s) {
+                         int64_t ldx, double* Y, int64_t ldy, int k, void* work, cudaStream_t s,
+                         size_t work_bytes = 0) {
   double* Ps = static_cast<double*>(work);
+  if (k == 1 && work_bytes >= matvec_fast_bytes(d)) {
+    HODLR_CUDA(launch_matvec1(d, D, U, V, X, Y, Ps, s));
+    return HODLR_OK;
+  }
   HODLR_CUDA(launch_leaf_matvec(d, D, X, ldx, Y, ldy, k, s));
   for (int c = 1; c <= d.L; ++c) {
     HODLR_CUDA((launch_project<double, double>(d.N, d.r, c, V, d.ldv, c - 1, X, ldx, k, Ps, 1, s)));
@@ -268,10 +283,11 @@ size_t factor_workspace_bytes(const hodlr_desc& d, hodlr_prec prec) { return fac
 
 // Entry points for the allocation-free matvec (noalloc.cu).
 hodlr_status matvec_core_ext(const hodlr_desc& d, const double* D, const double* U, const double* V, const double* X,
-                             int64_t ldx, double* Y, int64_t ldy, int k, void* work, cudaStream_t s) {
-  return matvec_core(d, D, U, V, X, ldx, Y, ldy, k, work, s);
+                             int64_t ldx, double* Y, int64_t ldy, int k, void* work, cudaStream_t s,
+                             size_t work_bytes) {
+  return matvec_core(d, D, U, V, X, ldx, Y, ldy, k, work, s, work_bytes);
 }
-size_t matvec_scratch_bytes(const hodlr_desc& d, int k) { return matvec_ws_bytes(d, k); }
+size_t matvec_scratch_bytes(const hodlr_desc& d, int k) { return matvec_min_bytes(d, k); }
 
 }  // namespace hodlr
 
@@ -332,6 +348,7 @@ hodlr_status hodlr_factor(const hodlr_desc* desc, const double* D, const double*
   F->K = reinterpret_cast<double*>(w + lay.K);
   F->P = reinterpret_cast<double*>(w + lay.P);
   F->P_elems = max_partial_elems(d, 1, 0);
+  F->rhs16 = prec == HODLR_PREC_BF16 ? reinterpret_cast<uint8_t*>(w + lay.rhs16) : nullptr;
   for (int c = 0; c < 26; ++c) F->Koff[c] = 0;
   for (int c = 1; c <= d.L; ++c) F->Koff[c] = ((int64_t)1 << (c - 1)) - 1;
   if (prec == HODLR_PREC_FP64) {
@@ -436,9 +453,10 @@ hodlr_status hodlr_matvec(const hodlr_desc* desc, const double* D, const double*
   if (st != HODLR_OK) return st;
   if (!D || !U || !V || !X || !Y || k < 1 || ldx < desc->N || ldy < desc->N) return HODLR_ERR_ARG;
   if (X == Y) return HODLR_ERR_ARG;
-  if (!workspace || !aligned(workspace, kAlign) || workspace_bytes < matvec_ws_bytes(*desc, k))
+  if (!workspace || !aligned(workspace, kAlign) || workspace_bytes < matvec_min_bytes(*desc, k))
     return HODLR_ERR_WORKSPACE;
-  return matvec_core(*desc, D, U, V, X, ldx, Y, ldy, k, workspace, reinterpret_cast<cudaStream_t>(stream));
+  return matvec_core(*desc, D, U, V, X, ldx, Y, ldy, k, workspace, reinterpret_cast<cudaStream_t>(stream),
+                     workspace_bytes);
 }
 
 // ------------------------------------------------------------ refined solvers
@@ -511,7 +529,7 @@ hodlr_status hodlr_solve_refined(hodlr_factor_t f, const double* D, const double
   int grew = 0, it = 0;
   double worst = INFINITY;
   for (;;) {
-    if ((st = matvec_core(d, D, U, V, X, ldx, R, N, k, mw, s)) != HODLR_OK) return st;
+    if ((st = matvec_core(d, D, U, V, X, ldx, R, N, k, mw, s, matvec_ws_bytes(d, k))) != HODLR_OK) return st;
     HODLR_CUDA(launch_axpby_cols(N, k, 1.0, B, ldb, -1.0, R, N, s));  // R = B - A X
     if ((st = col_norms2(N, k, R, N, dev_n, scratch, nr.data(), s)) != HODLR_OK) return st;
     worst = 0.0;
@@ -573,7 +591,7 @@ hodlr_status hodlr_gmres(hodlr_factor_t f, const double* D, const double* U, con
     double rel = INFINITY;
     for (;;) {
       // true residual r = b - A x
-      if ((st = matvec_core(d, D, U, V, x, N, r, N, 1, mw, s)) != HODLR_OK) return st;
+      if ((st = matvec_core(d, D, U, V, x, N, r, N, 1, mw, s, matvec_ws_bytes(d, 1))) != HODLR_OK) return st;
       HODLR_CUDA(launch_axpby_cols(N, 1, 1.0, b, N, -1.0, r, N, s));
       double beta2 = 0.0;
       if ((st = col_norms2(N, 1, r, N, dev_h, scratch, &beta2, s)) != HODLR_OK) return st;
@@ -589,7 +607,7 @@ hodlr_status hodlr_gmres(hodlr_factor_t f, const double* D, const double* U, con
         double* zi = Zk + (int64_t)i * N;
         HODLR_CUDA(launch_copy_cols<double, double>(N, 1, vi, N, zi, N, s));
         if ((st = solve_any(*f, zi, N, 1, sw, 0, s)) != HODLR_OK) return st;  // z_i = M^{-1} v_i
-        if ((st = matvec_core(d, D, U, V, zi, N, wv, N, 1, mw, s)) != HODLR_OK) return st;  // w = A z_i
+        if ((st = matvec_core(d, D, U, V, zi, N, wv, N, 1, mw, s, matvec_ws_bytes(d, 1))) != HODLR_OK) return st;  // w = A z_i
         // classical Gram-Schmidt, twice
         for (int pass = 0; pass < 2; ++pass) {
           HODLR_CUDA(launch_multidot(N, i + 1, Vk, N, wv, dev_h, scratch, s));

@@ -108,17 +108,47 @@ __device__ void gj_invert_smem(T* A, int n, int lda, int* spiv, T* spv, T* scol,
 // C (m x n, ldc) = alpha * A (m x k, lda) * B (k x n, ldb) + beta * C, all in
 // shared memory, column-major, by the whole CTA (warps over columns of C,
 // lanes over rows). Callers separate dependent calls with __syncthreads.
+// Each thread owns 4 x 4 outputs (rows tx + 16a, columns ty + 16b of a
+// 64 x 64 tile, tx = tid % 16, ty = tid / 16 for 256 threads), so every
+// k step costs 8 shared loads for 16 FMAs.
 template <typename T>
 __device__ void smem_gemm(int m, int n, int k, T alpha, const T* A, int lda, const T* B, int ldb, T beta, T* C,
                           int ldc) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = warp; j < n; j += nw) {
-    for (int i = lane; i < m; i += 32) {
-      T acc = T(0);
-      for (int t = 0; t < k; ++t) acc += A[(size_t)t * lda + i] * B[(size_t)j * ldb + t];
-      C[(size_t)j * ldc + i] = alpha * acc + (beta != T(0) ? beta * C[(size_t)j * ldc + i] : T(0));
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int tyn = blockDim.x >> 4;
+  for (int i0 = 0; i0 < m; i0 += 64)
+    for (int j0 = 0; j0 < n; j0 += 4 * tyn) {
+      T acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+      int ii[4], jj[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        ii[a] = i0 + tx + 16 * a;
+        jj[a] = j0 + ty + tyn * a;
+      }
+      for (int t = 0; t < k; ++t) {
+        T av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = ii[a] < m ? A[(size_t)t * lda + ii[a]] : T(0);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bv[b] = jj[b] < n ? B[(size_t)jj[b] * ldb + t] : T(0);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if (ii[a] < m && jj[b] < n) {
+            T* cp = C + (size_t)jj[b] * ldc + ii[a];
+            *cp = alpha * acc[a][b] + (beta != T(0) ? beta * *cp : T(0));
+          }
     }
-  }
 }
 
 // After gj_invert_smem: put the inverse's columns in order (column j of the

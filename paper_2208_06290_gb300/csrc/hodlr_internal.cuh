@@ -83,6 +83,9 @@ struct Factor {
   // projection partials (FP64): max over levels of num_chunks * r * r*c
   double* P;
   size_t P_elems;
+  // BF16 factor: per-parent right-hand sides [W_beta; W_alpha]^T of one level
+  // in the tensor cores' operand layout (rhs_bf16_bytes)
+  uint8_t* rhs16;
   // set while the factor's level loop has already summed each node's chunk
   // partials into its first slot (top levels), so the coupling kernels read
   // one slot per node
@@ -143,6 +146,9 @@ cudaError_t launch_update(int64_t N, int r, int c, const TB* Bas, int64_t ldb, i
 // LU, log|det|, solve for the ancestor columns; W' written to each child's
 // first chunk slot. Solve modes reuse the stored LU.
 cudaError_t launch_coupling_factor(const Factor& F, int c, cudaStream_t s);
+// FP32 warp-per-parent variant for the low-precision factors (r <= 32)
+bool coupling_warp_supported(const Factor& F);
+cudaError_t launch_coupling_factor_warp(const Factor& F, int c, cudaStream_t s);
 cudaError_t launch_coupling_solve(const Factor& F, int c, double* P, int k, int trans, cudaStream_t s);
 // Sum the chunk partials of every node into the node's first chunk slot.
 cudaError_t launch_reduce_chunks(int64_t N, int r, int c, double* P, int ncols, cudaStream_t s);
@@ -163,6 +169,11 @@ cudaError_t launch_leaf_identity(int64_t N, int m, double* E, cudaStream_t s);
 cudaError_t launch_leaf_outer(int64_t N, int m, int K, const double* A, int64_t lda, const double* B, int64_t ldb,
                               double alpha, double beta, const double* Tadd, double* out, cudaStream_t s);
 cudaError_t launch_coupling_h(const Factor& F, int c, double* H, double* HT, cudaStream_t s);
+
+// One-right-hand-side matvec in three launches (matvec1.cu).
+size_t matvec1_scratch_elems(const hodlr_desc& d);
+cudaError_t launch_matvec1(const hodlr_desc& d, const double* D, const double* U, const double* V, const double* x,
+                           double* y, double* scratch, cudaStream_t s);
 
 // Leaf stage of the matvec: Y_b = D_b X_b (FP64).
 cudaError_t launch_leaf_matvec(const hodlr_desc& d, const double* D, const double* X, int64_t ldx,
@@ -190,9 +201,12 @@ cudaError_t launch_logdet_reduce(const Factor& F, cudaStream_t s);
 bool project_tc_supported(int64_t N, int r, int c);
 cudaError_t launch_project_tc(int64_t N, int r, int L, int c, const __nv_bfloat16* Vp, int64_t ldv,
                               const __nv_bfloat16* Y, double* P, DevStatus* st, cudaStream_t s);
+// Coupling solve fused into the tensor-core ancestor update (BF16 factor):
+// uses the raw projections in each node's first slot, the coupling inverses
+// and the BF16 right-hand-side staging area rhs16 (rhs_bf16_bytes).
 bool update_tc_supported(int64_t N, int r, int c);
-cudaError_t launch_update_tc(int64_t N, int r, int c, __nv_bfloat16* Y, const double* Wbase, int64_t wstride,
-                             DevStatus* st, cudaStream_t s);
+size_t rhs_bf16_bytes(const hodlr_desc& d);
+cudaError_t launch_update_coupled_tc(const Factor& F, int c, cudaStream_t s);
 // Set by hodlr_tc_enable (process-wide; default on).
 extern bool g_use_tc;
 

@@ -453,6 +453,7 @@ cudaError_t launch_coupling_factor(const Factor& F, int c, cudaStream_t s) {
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(coupling_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   note_work(8.0 * num_chunks(F.d.N, c) * r * r + 8.0 * parents * n * n, parents * 2.0 / 3.0 * n * n * (double)n);
+  if (coupling_warp_supported(F)) return launch_coupling_factor_warp(F, c, s);
   { coupling_factor_kernel<<<(unsigned)parents, 256, sm, s>>>(F.d.N, r, c, F.P, F.P_reduced ? 1 : chunks_per_node(F.d.N, c), F.K + F.Koff[c] * n * n,
                                                              F.node_ld + 2 * F.Koff[c], F.status,
                                                              (int64_t)1 << (c - 1)); note_launches(1); }
@@ -654,8 +655,20 @@ cudaError_t launch_coupling_solve(const Factor& F, int c, double* P, int k, int 
 // ---------------------------------------------------------------------------
 // Sum the chunk partials of each node into the node's first slot (FP64,
 // fixed order).
-// One warp per slot element: lanes sum strided chunks, then a fixed-order
-// butterfly; the result goes to the node's first slot.
+// Few chunks per node: one thread per slot element sums them in order.
+__global__ void reduce_chunks_thread_kernel(int64_t N, int r, int c, double* P, int ncols) {
+  const int64_t cpn = chunks_per_node(N, c);
+  const int64_t node = blockIdx.x;
+  const size_t slot = (size_t)r * ncols;
+  const int64_t e = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)slot) return;
+  double acc = 0.0;
+  for (int64_t q = 0; q < cpn; ++q) acc += P[(node * cpn + q) * slot + e];
+  P[node * cpn * slot + e] = acc;
+}
+
+// Many chunks per node: one warp per slot element, lanes sum strided chunks,
+// then a fixed-order butterfly; the result goes to the node's first slot.
 __global__ void reduce_chunks_kernel(int64_t N, int r, int c, double* P, int ncols) {
   const int64_t cpn = chunks_per_node(N, c);
   const int64_t node = blockIdx.x;
@@ -674,6 +687,12 @@ cudaError_t launch_reduce_chunks(int64_t N, int r, int c, double* P, int ncols, 
   ProfScope prof_(KC_REDUCE, s);
   if (chunks_per_node(N, c) == 1) return cudaSuccess;
   const size_t slot = (size_t)r * ncols;
+  if (chunks_per_node(N, c) < 32) {
+    dim3 g1(1u << c, (unsigned)((slot + 255) / 256));
+    note_work(8.0 * ((double)num_chunks(N, c) + (double)(1ll << c)) * slot, (double)num_chunks(N, c) * slot);
+    { reduce_chunks_thread_kernel<<<g1, 256, 0, s>>>(N, r, c, P, ncols); note_launches(1); }
+    return cudaGetLastError();
+  }
   dim3 grid(1u << c, (unsigned)((slot + 7) / 8));
   note_work(8.0 * ((double)num_chunks(N, c) + (double)(1ll << c)) * slot, (double)num_chunks(N, c) * slot);
   { reduce_chunks_kernel<<<grid, 256, 0, s>>>(N, r, c, P, ncols); note_launches(1); }

@@ -1,0 +1,171 @@
+// FP64 HODLR matvec y = A x for one right-hand side in four launches
+// (Eq. e:rank: y = D x + sum over levels and siblings of U_alpha (V_beta^T x_beta)):
+//   1. per leaf b: the projections of x(I_b) on every basis column,
+//      p_b = V(I_b, 0:rL)^T x(I_b)  (all levels at once, V streamed once);
+//   2. per level c and node alpha: s_c(alpha) = sum of p_b(block c-1) over
+//      the leaves of alpha (fixed order; runs of 64 leaves, then runs per node);
+//   3. per leaf b: y(I_b) = D_b x(I_b) + U(I_b, 0:rL) t_b, where block c-1 of
+//      t_b is s_c(sibling of b's level-c ancestor)  (U and D streamed once).
+// The levels are independent in a matvec, unlike in the solves.
+#include "hodlr_internal.cuh"
+
+namespace hodlr {
+
+template <typename TA>
+__device__ __forceinline__ TA butterfly_reduce32(TA (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool upper = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const TA send = upper ? v[i] : v[i + s];
+      const TA keep = upper ? v[i + s] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  return v[0];
+}
+
+// 1. One CTA (4 warps) per leaf; warp w takes 32-column groups w, w+4, ...;
+// lane l accumulates rows l, l+32, ... of the leaf; the butterfly leaves the
+// column total of group column l in lane l.
+__global__ void __launch_bounds__(128) mv1_leaf_project_kernel(int m, int rL, const double* __restrict__ V,
+                                                               int64_t ldv, const double* __restrict__ x,
+                                                               double* __restrict__ pleaf) {
+  const int b = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row0 = (int64_t)b * m;
+  for (int g = warp; g * 32 < rL; g += 4) {
+    double acc[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] = 0.0;
+    for (int i = lane; i < m; i += 32) {
+      const double xv = x[row0 + i];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int col = g * 32 + j;
+        if (col < rL) acc[j] += V[(int64_t)col * ldv + row0 + i] * xv;
+      }
+    }
+    const double t = butterfly_reduce32(acc);
+    if (g * 32 + lane < rL) pleaf[(size_t)b * rL + g * 32 + lane] = t;
+  }
+}
+
+// 2a. Partial sums over runs of at most 64 consecutive leaves (never across
+// a node boundary), all levels in one launch: one CTA of r threads per
+// (level c, run), runs numbered level by level; thread j sums column
+// (c-1) r + j over the run in leaf order.
+// 2b. Per (level c, node), all levels in one launch: the node's runs summed
+// in order.
+constexpr int kMvRun = 64;
+
+__host__ __device__ inline int64_t mv1_runs(int L, int c) {
+  const int64_t per_node = (int64_t)1 << (L - c);
+  return ((int64_t)1 << c) * ((per_node + kMvRun - 1) / kMvRun);
+}
+
+__host__ __device__ inline int64_t mv1_runs_before(int L, int c) {
+  int64_t t = 0;
+  for (int cc = 1; cc < c; ++cc) t += mv1_runs(L, cc);
+  return t;
+}
+
+__global__ void mv1_run_sum_kernel(int L, int r, const double* __restrict__ pleaf, double* __restrict__ runs) {
+  const int64_t id = blockIdx.x;
+  int c = 1;
+  while (c < L && id >= mv1_runs_before(L, c + 1)) ++c;
+  const int64_t run = id - mv1_runs_before(L, c);
+  const int64_t per_node = (int64_t)1 << (L - c);
+  const int64_t len = per_node < kMvRun ? per_node : kMvRun;
+  const int64_t b0 = run * len;
+  const int rL = r * L;
+  const int j = threadIdx.x;
+  if (j >= r) return;
+  double acc = 0.0;
+  for (int64_t b = 0; b < len; ++b) acc += pleaf[(size_t)(b0 + b) * rL + (c - 1) * r + j];
+  runs[(size_t)id * r + j] = acc;
+}
+
+__global__ void mv1_node_sum_kernel(int L, int r, const double* __restrict__ runs, double* __restrict__ S) {
+  const int64_t id = blockIdx.x;  // = (2^c - 2) + alpha
+  int c = 1;
+  while (id >= ((int64_t)2 << c) - 2) ++c;
+  const int64_t alpha = id - (((int64_t)1 << c) - 2);
+  const int64_t per_node = (int64_t)1 << (L - c);
+  const int64_t rpn = (per_node + kMvRun - 1) / kMvRun;
+  const int64_t base = mv1_runs_before(L, c) + alpha * rpn;
+  const int j = threadIdx.x;
+  if (j >= r) return;
+  double acc = 0.0;
+  for (int64_t q = 0; q < rpn; ++q) acc += runs[(size_t)(base + q) * r + j];
+  S[(size_t)id * r + j] = acc;
+}
+
+// 3. One CTA per leaf: gather t_b (rL values) and x(I_b) into shared memory,
+// then thread per row: y = D_b x_b + U(row, :) t_b.
+__global__ void __launch_bounds__(256) mv1_leaf_apply_kernel(int m, int L, int r, const double* __restrict__ D,
+                                                             const double* __restrict__ U, int64_t ldu,
+                                                             const double* __restrict__ x,
+                                                             const double* __restrict__ S, double* __restrict__ y) {
+  extern __shared__ double sh[];
+  const int rL = r * L;
+  double* t = sh;          // rL
+  double* xs = sh + rL;    // m
+  const int b = blockIdx.x;
+  const int64_t row0 = (int64_t)b * m;
+  for (int e = threadIdx.x; e < rL; e += blockDim.x) {
+    const int c = e / r + 1, j = e % r;
+    const int64_t alpha = (int64_t)b >> (L - c);            // b's ancestor at level c
+    const int64_t id = (((int64_t)1 << c) - 2) + (alpha ^ 1);  // its sibling
+    t[e] = S[(size_t)id * r + j];
+  }
+  for (int e = threadIdx.x; e < m; e += blockDim.x) xs[e] = x[row0 + e];
+  __syncthreads();
+  const double* Db = D + (size_t)b * m * m;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    double acc = 0.0;
+    for (int jj = 0; jj < m; ++jj) acc += Db[(size_t)jj * m + i] * xs[jj];
+    for (int e = 0; e < rL; ++e) acc += U[(int64_t)e * ldu + row0 + i] * t[e];
+    y[row0 + i] = acc;
+  }
+}
+
+size_t matvec1_scratch_elems(const hodlr_desc& d) {
+  const size_t nleaf = (size_t)1 << d.L;
+  const size_t runs = (size_t)mv1_runs_before(d.L, d.L + 1);
+  return nleaf * (size_t)d.r * d.L + ((size_t)2 << d.L) * (size_t)d.r + runs * (size_t)d.r;
+}
+
+cudaError_t launch_matvec1(const hodlr_desc& d, const double* D, const double* U, const double* V, const double* x,
+                           double* y, double* scratch, cudaStream_t s) {
+  const int m = d.m, L = d.L, r = d.r, rL = r * L;
+  const int64_t nleaf = (int64_t)1 << L;
+  double* pleaf = scratch;
+  double* S = scratch + (size_t)nleaf * rL;
+  double* runs = S + ((size_t)2 << L) * r;
+  {
+    ProfScope prof_(KC_PROJECT, s);
+    note_work(8.0 * ((double)d.N * rL + d.N + nleaf * rL), 2.0 * d.N * rL);
+    { mv1_leaf_project_kernel<<<(unsigned)nleaf, 128, 0, s>>>(m, rL, V, d.ldv, x, pleaf); note_launches(1); }
+  }
+  {
+    ProfScope prof_(KC_REDUCE, s);
+    const int64_t pairs = ((int64_t)2 << L) - 2;
+    note_work(8.0 * ((double)nleaf * rL + pairs * r), (double)nleaf * rL);
+    const int th = ((r + 31) / 32) * 32;
+    { mv1_run_sum_kernel<<<(unsigned)mv1_runs_before(L, L + 1), th, 0, s>>>(L, r, pleaf, runs); note_launches(1); }
+    { mv1_node_sum_kernel<<<(unsigned)pairs, th, 0, s>>>(L, r, runs, S); note_launches(1); }
+  }
+  {
+    ProfScope prof_(KC_LEAF_MATVEC, s);
+    note_work(8.0 * ((double)d.N * m + (double)d.N * rL + 2.0 * d.N), 2.0 * d.N * (m + rL));
+    const size_t sm = (size_t)(rL + m) * sizeof(double);
+    const int th = m >= 256 ? 256 : ((m + 31) / 32) * 32;
+    { mv1_leaf_apply_kernel<<<(unsigned)nleaf, th, sm, s>>>(m, L, r, D, U, d.ldu, x, S, y); note_launches(1); }
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace hodlr

@@ -25,7 +25,8 @@
 namespace hodlr {
 
 hodlr_status matvec_core_ext(const hodlr_desc& d, const double* D, const double* U, const double* V, const double* X,
-                             int64_t ldx, double* Y, int64_t ldy, int k, void* work, cudaStream_t s);
+                             int64_t ldx, double* Y, int64_t ldy, int k, void* work, cudaStream_t s,
+                             size_t work_bytes);
 size_t matvec_scratch_bytes(const hodlr_desc& d, int k);
 
 namespace {
@@ -64,5 +65,6 @@ extern "C" hodlr_status hodlr_matvec_noalloc(const hodlr_desc* desc, const doubl
     }
     scratch = g_noalloc_addr[dev];
   }
-  return matvec_core_ext(*desc, D, U, V, X, ldx, Y, ldy, k, scratch, reinterpret_cast<cudaStream_t>(stream));
+  return matvec_core_ext(*desc, D, U, V, X, ldx, Y, ldy, k, scratch, reinterpret_cast<cudaStream_t>(stream),
+                         kNoAllocScratchBytes);
 }

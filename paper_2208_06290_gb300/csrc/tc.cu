@@ -218,46 +218,144 @@ cudaError_t launch_project_tc(int64_t N, int r, int L, int c, const __nv_bfloat1
 
 
 // ===========================================================================
-// Tensor-core ancestor update of the BF16 factor (Eq. e:node2):
-//   Y(rows, 0:anc) -= Y(rows, own block) * W'(node),  W' FP64 r x anc (ld r).
-// Tile = 128 rows of one node (M = 128), N = up to 256 ancestor columns per
-// MMA, K = r. Y's own block is column-major, i.e. M-contiguous for this
-// product, so the CTA's threads transpose it into the K-major canonical
-// layout without swizzle (8-row x 16-byte core matrices, LBO = 128 B between
-// cores along K, SBO = r/8 * 128 B between 8-row groups); W' is converted to
-// BF16 into the same layout (N rows). The FP32 accumulator in TMEM is then
-// subtracted from the old BF16 values, 32 columns per tcgen05.ld.
+// Coupling solve fused into the tensor-core ancestor update of the BF16 factor
+// (Eq. e:node1 and Eq. e:node2, Alg. 3). With Rhs = [W_beta; W_alpha] the raw
+// projections of the two children of a parent (2r x anc, rows 0..r-1 from the
+// second child, as the right-hand side of K~ [w_first; w_second]) and K~^{-1}
+// the parent's coupling inverse,
+//   W'_alpha = K~^{-1}(rows of alpha, :) Rhs,
+//   Y(rows, 0:anc) -= Y_own W'_alpha = (Y_own K~^{-1}(rows of alpha, :)) Rhs.
+//
+// Step 1 (rhs_bf16_kernel, once per level): Rhs^T of every parent rounded to
+// BF16 and stored in the K-major core-matrix layout of a tcgen05 B operand
+// (8-row x 16-byte cores, LBO = 128 B between cores along K, SBO = 2r/8 * 128 B
+// between 8-row groups), one contiguous block per kFuNC ancestor columns, so
+// that one bulk copy stages it.
+// Step 2 (update_coupled_tc_kernel): per 128-row tile of a node, TMA brings the
+// own block Y_own (128 x r); Z = Y_own K~^{-1}(alpha rows, :) (128 x 2r) is
+// formed on the CUDA cores in FP32 and rounded to BF16 into the A layout; per
+// chunk of kFuNC ancestor columns a bulk copy brings Rhs^T and TMA the old Y
+// tile, one tcgen05.mma kind::f16 chain (K = 2r) accumulates Z Rhs in TMEM,
+// and the epilogue subtracts it from the staged tile, which TMA stores back.
 namespace {
 
-constexpr int kUpdNC = 256;  // ancestor columns per MMA chunk
+constexpr int kFuNC = 128;   // ancestor columns per MMA chunk (N of the MMA)
+constexpr int kFuBox = 32;   // columns per TMA box of Y (box = 128 rows x 32 columns)
 
 template <int RK>
-struct UpdSmem {
-  static constexpr uint32_t kABytes = 128 * RK * 2;
-  static constexpr uint32_t kBBytes = kUpdNC * RK * 2;
-  // padded so that at most two CTAs (2 x 256 TMEM columns) share an SM
-  static constexpr uint32_t kBytes = (kABytes + kBBytes + 192) > 100 * 1024 ? (kABytes + kBBytes + 192) : 100 * 1024;
+struct FusedSmem {
+  static constexpr int K2 = 2 * RK;
+  static constexpr uint32_t kABytes = 128 * K2 * 2;       // Z, K-major cores
+  static constexpr uint32_t kBBytes = kFuNC * K2 * 2;     // Rhs^T chunk
+  static constexpr int kKLd = K2 + 4;                     // padded row: 4-way instead of 32-way store conflicts
+  static constexpr uint32_t kKBytes = RK * kKLd * 4;      // K~^{-1}(alpha rows, :), FP32
+  static constexpr uint32_t kOwnBytes = 128 * RK * 2;     // Y_own tile [k][m]
+  static constexpr uint32_t kYBytes = 128 * kFuNC * 2;    // old / new Y tile [j][m]
+  static constexpr uint32_t kBarOff = kABytes + kBBytes + kKBytes + kOwnBytes + kYBytes;
+  static constexpr uint32_t kBytes = kBarOff + 64 + 128;  // 3 mbarriers + TMEM slot, + alignment slack
 };
+
+// Rhs^T of every parent of child level c into the B layout above. Thread per
+// 16-byte core row (8 consecutive K entries of one ancestor column); threads
+// with consecutive (nn & 7) write one 128-byte core matrix together.
+template <int RK>
+__global__ void rhs_bf16_kernel(int c, const double* __restrict__ P, int64_t pstride, int anc,
+                                uint8_t* __restrict__ out) {
+  constexpr int K2 = 2 * RK;
+  constexpr int KG = K2 / 8;
+  constexpr uint32_t kSBO = KG * 128;
+  const int64_t parents = (int64_t)1 << (c - 1);
+  const int64_t per_parent = (int64_t)anc * KG;
+  const int64_t total = parents * per_parent;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / per_parent;
+    const int64_t w = e % per_parent;
+    const int lo = (int)(w & 7);
+    const int64_t g = w >> 3;              // (nn >> 3) * KG + kg
+    const int kg = (int)(g % KG);
+    const int nn = (int)((g / KG) * 8 + lo);
+    // rows 0..r-1: second child 2j+1; rows r..2r-1: first child 2j
+    const int k0 = kg * 8;
+    const double* src = k0 < RK ? P + (2 * j + 1) * pstride + (int64_t)nn * RK + k0
+                                : P + (2 * j) * pstride + (int64_t)nn * RK + (k0 - RK);
+    const double2 a = *reinterpret_cast<const double2*>(src);
+    const double2 b = *reinterpret_cast<const double2*>(src + 2);
+    const double2 cc = *reinterpret_cast<const double2*>(src + 4);
+    const double2 d = *reinterpret_cast<const double2*>(src + 6);
+    auto pack = [](double x, double y) {
+      return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)x)) |
+             ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)y)) << 16);
+    };
+    const int chunk = nn / kFuNC, nl = nn % kFuNC;
+    uint8_t* dst = out + (size_t)j * anc * K2 * 2 + (size_t)chunk * kFuNC * K2 * 2 + (size_t)(nl >> 3) * kSBO +
+                   (size_t)kg * 128 + (size_t)(nl & 7) * 16;
+    *reinterpret_cast<uint4*>(dst) = make_uint4(pack(a.x, a.y), pack(b.x, b.y), pack(cc.x, cc.y), pack(d.x, d.y));
+  }
+}
+
+__device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   tc::smem_u32(dst)),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(tc::smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int32_t x, int32_t y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(tc::smem_u32(src))
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// 2-D BF16 tensor map without swizzle over the column-major N x cols matrix Y
+// (ld N): box = 128 rows x kFuBox columns, stored in shared memory as
+// [column][row] (column j of the box at j * 256 bytes).
+bool make_map_plain(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {128, (cuuint32_t)kFuBox};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 }  // namespace
 
 template <int RK>
-__global__ void __launch_bounds__(256) update_tc_kernel(int64_t N, int c, __nv_bfloat16* __restrict__ Y,
-                                                        const double* __restrict__ Wbase, int64_t wstride, int anc,
-                                                        DevStatus* st) {
-  using S = UpdSmem<RK>;
-  extern __shared__ __align__(128) uint8_t smem_raw[];
-  uint8_t* sA = smem_raw;
-  uint8_t* sB = smem_raw + S::kABytes;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sB + S::kBBytes);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
+__global__ void __launch_bounds__(256, RK == 32 ? 2 : 1) update_coupled_tc_kernel(const __grid_constant__ CUtensorMap mapY, int64_t N,
+                                                                int c, const uint8_t* __restrict__ rhs,
+                                                                const double* __restrict__ Kinv, int anc,
+                                                                DevStatus* st) {
+  using S = FusedSmem<RK>;
+  constexpr int K2 = 2 * RK;
+  constexpr uint32_t kSBO = (K2 / 8) * 128;
+  constexpr uint32_t kTmemCols = kFuNC;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  uint8_t* sA = smem;
+  uint8_t* sB = sA + S::kABytes;
+  float* sK = reinterpret_cast<float*>(sB + S::kBBytes);
+  __nv_bfloat16* sOwn = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<uint8_t*>(sK) + S::kKBytes);
+  __nv_bfloat16* sY = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<uint8_t*>(sOwn) + S::kOwnBytes);
+  uint64_t* bar_own = reinterpret_cast<uint64_t*>(smem + S::kBarOff);
+  uint64_t* bar_ld = bar_own + 1;
+  uint64_t* bar_mma = bar_own + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_own + 3);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  constexpr uint32_t kSBO = (RK / 8) * 128;
-  constexpr uint32_t kTmemCols = kUpdNC;
 
   if (tid == 0) {
-    tc::mbar_init(bar, 1);
+    tc::mbar_init(bar_own, 1);
+    tc::mbar_init(bar_ld, 1);
+    tc::mbar_init(bar_mma, 1);
     tc::fence_mbar_init();
+    tc::prefetch_tmap(&mapY);
   }
   if (warp == 0) tc::tmem_alloc(tmem_slot, kTmemCols);
   tc::tc_fence_before();
@@ -267,103 +365,204 @@ __global__ void __launch_bounds__(256) update_tc_kernel(int64_t N, int c, __nv_b
 
   const int64_t n = N >> c;
   const int64_t tiles = N / 128;
-  const int rk = RK;
+  const int nchunks = (anc + kFuNC - 1) / kFuNC;
   bool ok = true;
-  uint32_t phase = 0;
+  uint32_t ph_own = 0, ph_ld = 0, ph_mma = 0;
+  // copies / MMAs issued by thread 0 and not yet waited for (thread 0's view)
+  bool own_pending = false, ld_pending = false, mma_pending = false;
   for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
     const int64_t row0 = t * 128;
     const int64_t node = row0 / n;
-    const double* W = Wbase + node * wstride;
-    const __nv_bfloat16* Yown = Y + (int64_t)(c - 1) * rk * N + row0;
-    // A: 128 rows x RK of the own block, K-major cores
-    for (int e = tid; e < 128 * (RK / 8); e += blockDim.x) {
-      const int m = e & 127, kg = e >> 7;
-      uint32_t pk[4];
+    const int64_t parent = node >> 1;
+    const int first = (node & 1) == 0;
+    const uint8_t* rhs_j = rhs + (size_t)parent * anc * K2 * 2;
+    if (tid == 0) {
+      // the previous tile's last store must have left sY before it is refilled
+      bulk_wait_read0();
+      tc::mbar_expect_tx(bar_own, S::kOwnBytes);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const __nv_bfloat16 lo = Yown[(int64_t)(kg * 8 + 2 * q) * N + m];
-        const __nv_bfloat16 hi = Yown[(int64_t)(kg * 8 + 2 * q + 1) * N + m];
-        pk[q] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-      }
-      *reinterpret_cast<uint4*>(sA + kg * 128 + (m >> 3) * kSBO + (m & 7) * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      for (int b = 0; b < RK / kFuBox; ++b)
+        tc::tma_load_2d(sOwn + b * 128 * kFuBox, &mapY, (int32_t)row0, (c - 1) * RK + b * kFuBox, bar_own);
+      const int nc = anc < kFuNC ? anc : kFuNC;
+      tc::mbar_expect_tx(bar_ld, (uint32_t)nc * K2 * 2 + (uint32_t)nc * 128 * 2);
+      bulk_load_1d(sB, rhs_j, (uint32_t)nc * K2 * 2, bar_ld);
+      for (int b = 0; b < nc / kFuBox; ++b) tc::tma_load_2d(sY + b * 128 * kFuBox, &mapY, (int32_t)row0, b * kFuBox, bar_ld);
+      own_pending = ld_pending = true;
     }
-    for (int col0 = 0; col0 < anc && ok; col0 += kUpdNC) {
-      const int nc = (anc - col0) < kUpdNC ? (anc - col0) : kUpdNC;  // multiple of 16 (anc = r (c-1))
-      // B: nc rows (ancestor columns) x RK, K-major cores, from FP64 W'
-      for (int e = tid; e < nc * (RK / 8); e += blockDim.x) {
-        const int nn = e % nc, kg = e / nc;
-        const double* w = W + (int64_t)(col0 + nn) * rk + kg * 8;
+    // K~^{-1}(alpha rows, :) -> sK[k][q]  (FP64 column-major 2r x 2r)
+    const double* Kj = Kinv + (size_t)parent * K2 * K2;
+    const int rowoff = first ? 0 : RK;
+    for (int e = tid; e < RK * K2; e += blockDim.x) {
+      const int k = e % RK, q = e / RK;
+      sK[k * S::kKLd + q] = (float)Kj[(size_t)q * K2 + rowoff + k];
+    }
+    __syncthreads();
+    ok = __syncthreads_and(tc::mbar_wait(bar_own, ph_own)) != 0;
+    if (!ok) break;
+    ph_own ^= 1;
+    own_pending = false;
+    // Z = Y_own K~^{-1}(alpha rows, :): thread pair per row, each half of 2r
+    {
+      const int m = tid & 127, half = tid >> 7;
+      float yv[RK];
+#pragma unroll
+      for (int k = 0; k < RK; ++k) yv[k] = __bfloat162float(sOwn[k * 128 + m]);
+#pragma unroll
+      for (int g = 0; g < RK / 8; ++g) {  // 8 output columns -> one 16-byte core row
+        const int q0 = half * RK + g * 8;
+        float z[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) z[u] = 0.f;
+#pragma unroll
+        for (int k = 0; k < RK; ++k) {
+          const float4 k0 = *reinterpret_cast<const float4*>(sK + k * S::kKLd + q0);
+          const float4 k1 = *reinterpret_cast<const float4*>(sK + k * S::kKLd + q0 + 4);
+          z[0] = fmaf(yv[k], k0.x, z[0]);
+          z[1] = fmaf(yv[k], k0.y, z[1]);
+          z[2] = fmaf(yv[k], k0.z, z[2]);
+          z[3] = fmaf(yv[k], k0.w, z[3]);
+          z[4] = fmaf(yv[k], k1.x, z[4]);
+          z[5] = fmaf(yv[k], k1.y, z[5]);
+          z[6] = fmaf(yv[k], k1.z, z[6]);
+          z[7] = fmaf(yv[k], k1.w, z[7]);
+        }
         uint32_t pk[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const __nv_bfloat16 lo = __float2bfloat16_rn((float)w[2 * q]);
-          const __nv_bfloat16 hi = __float2bfloat16_rn((float)w[2 * q + 1]);
-          pk[q] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-        }
-        *reinterpret_cast<uint4*>(sB + kg * 128 + (nn >> 3) * kSBO + (nn & 7) * 16) =
+        for (int u = 0; u < 4; ++u)
+          pk[u] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(z[2 * u])) |
+                  ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(z[2 * u + 1])) << 16);
+        const int kg = q0 / 8;
+        *reinterpret_cast<uint4*>(sA + kg * 128 + (m >> 3) * kSBO + (m & 7) * 16) =
             make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    for (int ch = 0; ch < nchunks && ok; ++ch) {
+      const int col0 = ch * kFuNC;
+      const int nc = (anc - col0) < kFuNC ? (anc - col0) : kFuNC;  // multiple of 32 (anc = r (c-1))
+      if (ch > 0 && tid == 0) {
+        bulk_wait_read0();
+        tc::mbar_expect_tx(bar_ld, (uint32_t)nc * K2 * 2 + (uint32_t)nc * 128 * 2);
+        bulk_load_1d(sB, rhs_j + (size_t)col0 * K2 * 2, (uint32_t)nc * K2 * 2, bar_ld);
+        for (int b = 0; b < nc / kFuBox; ++b)
+          tc::tma_load_2d(sY + b * 128 * kFuBox, &mapY, (int32_t)row0, col0 + b * kFuBox, bar_ld);
+        ld_pending = true;
+      }
+      tc::tc_fence_before();
+      ok = __syncthreads_and(tc::mbar_wait(bar_ld, ph_ld)) != 0;  // also orders the Z writes before the MMA
+      if (!ok) break;
+      ph_ld ^= 1;
+      ld_pending = false;
+      tc::tc_fence_after();
+      if (tid == 0) {
+        const uint32_t idesc = tc::idesc_bf16_f32(128, nc);
+        const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+#pragma unroll
+        for (int ks = 0; ks < K2 / 16; ++ks)
+          tc::mma_bf16(tmem, tc::desc_noswz_kmajor(a0 + ks * 256, 128, kSBO),
+                       tc::desc_noswz_kmajor(b0 + ks * 256, 128, kSBO), idesc, ks != 0);
+        tc::mma_commit(bar_mma);
+        mma_pending = true;
+      }
+      ok = __syncthreads_and(tc::mbar_wait(bar_mma, ph_mma)) != 0;  // block-uniform before warp-collective loads
+      if (!ok) break;
+      ph_mma ^= 1;
+      mma_pending = false;
+      tc::tc_fence_after();
+      // warps w and w+4 share TMEM lanes 32 (w % 4) .. +31 and split the columns
+      const int m = (warp & 3) * 32 + lane;
+      for (int cb = (warp >> 2) * 32; cb < nc; cb += 64) {
+        float v[32];
+        tc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + cb, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          __nv_bfloat16* p = sY + (cb + j) * 128 + m;
+          *p = __float2bfloat16_rn(__bfloat162float(*p) - v[j]);
+        }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tc::tc_fence_before();
       __syncthreads();
       tc::tc_fence_after();
       if (tid == 0) {
-        const uint32_t idesc = tc::idesc_bf16_f32(128, nc);
-        const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
-#pragma unroll
-        for (int ks = 0; ks < RK / 16; ++ks)
-          tc::mma_bf16(tmem, tc::desc_noswz_kmajor(a0 + ks * 256, 128, kSBO),
-                       tc::desc_noswz_kmajor(b0 + ks * 256, 128, kSBO), idesc, ks != 0);
-        tc::mma_commit(bar);
+        for (int b = 0; b < nc / kFuBox; ++b)
+          tma_store_2d(&mapY, sY + b * 128 * kFuBox, (int32_t)row0, col0 + b * kFuBox);
+        bulk_commit();
       }
-      ok = __syncthreads_and(tc::mbar_wait(bar, phase)) != 0;  // block-uniform before warp-collective loads
-      phase ^= 1;
-      tc::tc_fence_after();
-      if (ok) {
-        // warps w and w+4 share TMEM lanes 32 (w % 4) .. +31 and split the columns
-        const int m = (warp & 3) * 32 + lane;
-        __nv_bfloat16* yrow = Y + row0 + m;
-        for (int cb = (warp >> 2) * 32; cb < nc; cb += 64) {
-          float v[32];
-          tc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + cb, v);
-          float old[32];
-#pragma unroll
-          for (int j = 0; j < 32; ++j) old[j] = __bfloat162float(yrow[(int64_t)(col0 + cb + j) * N]);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) yrow[(int64_t)(col0 + cb + j) * N] = __float2bfloat16_rn(old[j] - v[j]);
-        }
-      }
-      tc::tc_fence_before();
-      __syncthreads();
-      tc::tc_fence_after();
     }
   }
-  if (!ok && tid == 0) set_status(st, HODLR_ERR_TIMEOUT, c, 1);
+  if (tid == 0) {
+    // a wait that gave up leaves its copies / MMAs in flight: let them land
+    // (bounded) before the shared memory and TMEM are released
+    if (own_pending) tc::mbar_wait(bar_own, ph_own);
+    if (ld_pending) tc::mbar_wait(bar_ld, ph_ld);
+    if (mma_pending) tc::mbar_wait(bar_mma, ph_mma);
+    bulk_wait0();
+    if (!ok) set_status(st, HODLR_ERR_TIMEOUT, c, 2);
+  }
   tc::tc_fence_before();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
 bool update_tc_supported(int64_t N, int r, int c) {
-  return (r == 32 || r == 64) && ((N >> c) % 128) == 0;
+  return (r == 32 || r == 64) && ((N >> c) % 128) == 0 && encode_fn() != nullptr;
 }
 
-cudaError_t launch_update_tc(int64_t N, int r, int c, __nv_bfloat16* Y, const double* Wbase, int64_t wstride,
-                             DevStatus* st, cudaStream_t s) {
-  ProfScope prof_(KC_UPDATE_TC, s);
+size_t rhs_bf16_bytes(const hodlr_desc& d) {
+  // max over child levels c of 2^(c-1) parents x (r (c-1)) x 2r BF16
+  size_t best = 0;
+  for (int c = 2; c <= d.L; ++c) {
+    const size_t b = ((size_t)1 << (c - 1)) * (size_t)d.r * (c - 1) * 2 * d.r * 2;
+    if (b > best) best = b;
+  }
+  return best;
+}
+
+cudaError_t launch_update_coupled_tc(const Factor& F, int c, cudaStream_t s) {
+  const int64_t N = F.d.N;
+  const int r = F.d.r;
   const int anc = r * (c - 1);
   if (anc <= 0) return cudaSuccess;
-  note_work(2.0 * (double)N * r + 4.0 * (double)N * anc + 8.0 * (double)(1ll << c) * r * anc,
-            2.0 * N * r * (double)anc);
+  const int64_t cpn = chunks_per_node(N, c);
+  const int64_t pstride = cpn * (int64_t)r * r * c;  // node -> its first chunk's slot (reduced)
+  const int64_t parents = (int64_t)1 << (c - 1);
+  {
+    ProfScope prof_(KC_COUPLING_APPLY, s);
+    note_work(8.0 * (double)(1ll << c) * r * anc + 2.0 * (double)parents * anc * 2 * r, 0.0);
+    const int64_t total = parents * (int64_t)anc * (2 * r / 8);
+    int64_t grid = (total + 255) / 256;
+    if (grid > 16 * (int64_t)sm_count()) grid = 16 * (int64_t)sm_count();
+    if (r == 32) {
+      rhs_bf16_kernel<32><<<(unsigned)grid, 256, 0, s>>>(c, F.P, pstride, anc, F.rhs16);
+    } else {
+      rhs_bf16_kernel<64><<<(unsigned)grid, 256, 0, s>>>(c, F.P, pstride, anc, F.rhs16);
+    }
+    note_launches(1);
+  }
+  ProfScope prof_(KC_UPDATE_TC, s);
+  note_work(2.0 * (double)N * r + 4.0 * (double)N * anc + 4.0 * (double)parents * anc * r +
+                32.0 * (double)parents * r * r,
+            4.0 * N * r * (double)anc + 4.0 * N * r * (double)r);
+  CUtensorMap mY;
+  __nv_bfloat16* Y = static_cast<__nv_bfloat16*>(F.Y);
+  if (!make_map_plain(&mY, Y, N, (int64_t)r * F.d.L, N)) return cudaErrorInvalidValue;
+  const double* Kc = F.K + F.Koff[c] * 4 * r * r;
   const int64_t tiles = N / 128;
-  int64_t grid = 2 * (int64_t)sm_count();
-  if (grid > tiles) grid = tiles;
   if (r == 32) {
-    cudaFuncSetAttribute(update_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UpdSmem<32>::kBytes);
-    { update_tc_kernel<32><<<(unsigned)grid, 256, UpdSmem<32>::kBytes, s>>>(N, c, Y, Wbase, wstride, anc, st); note_launches(1); }
+    using S = FusedSmem<32>;
+    const int per_sm = (int)((227 * 1024) / S::kBytes);
+    int64_t grid = (int64_t)sm_count() * (per_sm < 1 ? 1 : per_sm);
+    if (grid > tiles) grid = tiles;
+    cudaFuncSetAttribute(update_coupled_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kBytes);
+    { update_coupled_tc_kernel<32><<<(unsigned)grid, 256, S::kBytes, s>>>(mY, N, c, F.rhs16, Kc, anc, F.status); note_launches(1); }
   } else {
-    cudaFuncSetAttribute(update_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UpdSmem<64>::kBytes);
-    { update_tc_kernel<64><<<(unsigned)grid, 256, UpdSmem<64>::kBytes, s>>>(N, c, Y, Wbase, wstride, anc, st); note_launches(1); }
+    using S = FusedSmem<64>;
+    const int per_sm = (int)((227 * 1024) / S::kBytes);
+    int64_t grid = (int64_t)sm_count() * (per_sm < 1 ? 1 : per_sm);
+    if (grid > tiles) grid = tiles;
+    cudaFuncSetAttribute(update_coupled_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kBytes);
+    { update_coupled_tc_kernel<64><<<(unsigned)grid, 256, S::kBytes, s>>>(mY, N, c, F.rhs16, Kc, anc, F.status); note_launches(1); }
   }
   return cudaGetLastError();
 }

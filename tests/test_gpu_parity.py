@@ -95,7 +95,7 @@ def test_dense_c0_configuration(cuda_lib):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
-@pytest.mark.parametrize("N,L,r", [(256, 2, 4), (4096, 6, 16), (2048, 3, 32), (1 << 14, 6, 8)])
+@pytest.mark.parametrize("N,L,r", [(256, 2, 4), (384, 3, 5), (4096, 6, 16), (2048, 3, 32), (1024, 4, 64), (1 << 14, 6, 8)])
 def test_mixed_refined_reaches_1e10(cuda_lib, prec, N, L, r):
     hb = cuda_lib
     (Dm, Um, Vm, Bm), (D, U, V, B) = make_case(N, L, r, seed=11 * N + r, k=2)
@@ -153,10 +153,12 @@ def test_nonfinite_reported(cuda_lib):
     assert code == hb.HODLR_ERR_NONFINITE and where == 2
 
 
-def test_singular_coupling_reported(cuda_lib):
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_singular_coupling_reported(cuda_lib, prec):
     """D = I, only the level-1 bases nonzero with U_a = V_a = e_1 (alpha) and
     U_b = V_b = e_1 (beta): rows 1 and N/2+1 of A coincide and the root's
-    K~ = [[1, 1], [1, 1]] has an exact zero second pivot."""
+    K~ = [[1, 1], [1, 1]] has an exact zero second pivot (exact in every
+    precision: the projections are exactly 1)."""
     hb = cuda_lib
     N, L, r = 256, 2, 1
     m = N >> L
@@ -166,7 +168,7 @@ def test_singular_coupling_reported(cuda_lib):
     U[N // 2, 0] = 1.0
     V = U.clone().T.contiguous().T
     D, U, V = (t.to("cuda") for t in (D, U, V))
-    F = hb.hodlr_factor(D, U, V, L, r, "fp64")
+    F = hb.hodlr_factor(D, U, V, L, r, prec)
     code, where, detail = hb.hodlr_factor_status(F)
     assert code == hb.HODLR_ERR_SINGULAR_COUPLING and where == 1 and detail == 1
     with pytest.raises(hb.HodlrError):
@@ -199,3 +201,14 @@ def test_bf16_tensor_core_factor_matches_cuda_core(cuda_lib, N, L, r):
     assert lt[0] == lc[0] and abs(lt[1] - lc[1]) < 1e-6 * max(1.0, abs(lc[1]))
     # and the BF16 factor is a BF16-accurate inverse of the FP64 operator
     assert relerr(Xt, RecursiveHODLR(Dm, Um, Vm, L).solve(Bm)) < 5e-2
+
+
+@pytest.mark.parametrize("N,L,r", [(256, 2, 4), (384, 3, 5), (128, 1, 3), (4096, 6, 16), (2048, 3, 32),
+                                   (1 << 14, 6, 64)])
+def test_matvec_fp64_single_rhs(cuda_lib, N, L, r):
+    """k = 1 takes the four-launch path (all levels' projections per leaf)."""
+    hb = cuda_lib
+    (Dm, Um, Vm, Bm), (D, U, V, B) = make_case(N, L, r, seed=5 * N + r, k=1)
+    Y = hb.hodlr_matvec(D, U, V, L, r, B)
+    ref = o_matvec(Dm, Um, Vm, L, Bm)
+    assert relerr(Y.cpu().numpy(), ref) < 1e-13
