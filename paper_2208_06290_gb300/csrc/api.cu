@@ -132,7 +132,12 @@ Layout factor_layout(const hodlr_desc& d, hodlr_prec prec) {
   l.Y = take(N * rL * tp);
   l.Vp = prec == HODLR_PREC_FP64 ? 0 : take(N * rL * tp);
   l.K = take((nleaf - 1) * 4 * (size_t)d.r * d.r * sizeof(double) + 16);
-  l.P = take(max_partial_elems(d, 1, 0) * sizeof(double));
+  {
+    // P also holds the tensor-core copy of the leaf inverses before the level loop
+    const size_t pb = max_partial_elems(d, 1, 0) * sizeof(double);
+    const size_t tcb = (prec == HODLR_PREC_BF16 && d.m == 128) ? nleaf * (size_t)d.m * d.m * 4 : 0;
+    l.P = take(pb > tcb ? pb : tcb);
+  }
   l.rhs16 = prec == HODLR_PREC_BF16 ? take(rhs_bf16_bytes(d)) : 0;
   l.total = off;
   return l;
@@ -360,6 +365,7 @@ hodlr_status hodlr_factor(const hodlr_desc* desc, const double* D, const double*
   }
   auto fail = [&](hodlr_status e) { delete F; return e; };
   if (cudaMemsetAsync(F->status, 0, sizeof(DevStatus), s) != cudaSuccess) return fail(HODLR_ERR_CUDA);
+  F->leaf_tc = leaf_apply_tc_supported(*F) && aligned(U, 16) && d.ldu % 2 == 0;
   if (launch_leaf_lu(*F, D, s) != cudaSuccess) return fail(HODLR_ERR_CUDA);
   const int rL = d.r * d.L;
   hodlr_status r = HODLR_OK;
@@ -379,9 +385,11 @@ hodlr_status hodlr_factor(const hodlr_desc* desc, const double* D, const double*
                                                 static_cast<__nv_bfloat16*>(const_cast<void*>(F->Vp)), d.N,
                                                 s) != cudaSuccess)
       return fail(HODLR_ERR_CUDA);
-    if (launch_leaf_solve<double, __nv_bfloat16>(*F, U, d.ldu, static_cast<__nv_bfloat16*>(F->Y), d.N, rL, 0, s) !=
-        cudaSuccess)
-      return fail(HODLR_ERR_CUDA);
+    const cudaError_t e =
+        F->leaf_tc ? launch_leaf_apply_tc(*F, U, d.ldu, s)
+                   : launch_leaf_solve<double, __nv_bfloat16>(*F, U, d.ldu, static_cast<__nv_bfloat16*>(F->Y), d.N,
+                                                              rL, 0, s);
+    if (e != cudaSuccess) return fail(HODLR_ERR_CUDA);
     r = factor_levels<__nv_bfloat16>(*F, s);
   }
   if (r != HODLR_OK) return fail(r);

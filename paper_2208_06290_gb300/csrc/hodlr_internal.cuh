@@ -86,6 +86,10 @@ struct Factor {
   // BF16 factor: per-parent right-hand sides [W_beta; W_alpha]^T of one level
   // in the tensor cores' operand layout (rhs_bf16_bytes)
   uint8_t* rhs16;
+  // BF16 factor with m = 128: the leaf stage runs on the tensor cores; the
+  // leaf inverse then also writes D_b^{-1} in operand layout into P (P is
+  // free until the level loop starts)
+  bool leaf_tc = false;
   // set while the factor's level loop has already summed each node's chunk
   // partials into its first slot (top levels), so the coupling kernels read
   // one slot per node
@@ -207,6 +211,10 @@ cudaError_t launch_project_tc(int64_t N, int r, int L, int c, const __nv_bfloat1
 bool update_tc_supported(int64_t N, int r, int c);
 size_t rhs_bf16_bytes(const hodlr_desc& d);
 cudaError_t launch_update_coupled_tc(const Factor& F, int c, cudaStream_t s);
+// Tensor-core (kind::tf32) leaf stage Y = D_b^{-1} U of the BF16 factor
+// (m = 128, r L a multiple of 32; U 16-byte aligned with even ldu).
+bool leaf_apply_tc_supported(const Factor& F);
+cudaError_t launch_leaf_apply_tc(const Factor& F, const double* U, int64_t ldu, cudaStream_t s);
 // Set by hodlr_tc_enable (process-wide; default on).
 extern bool g_use_tc;
 

@@ -1,87 +1,204 @@
 // Leaf stage of the low-precision factor for leaves of at most 128 rows: each
-// leaf block is inverted in shared memory (FP32 Gauss-Jordan elimination with
-// partial pivoting, whose pivots and row swaps are those of getrf, so the
-// log-determinant is unchanged) and the leaf "solves" of Alg. 1 / Alg. 2
+// leaf block is inverted (FP32 Gauss-Jordan elimination with partial
+// pivoting, whose pivots are those of getrf, so the log-determinant is
+// unchanged) and the leaf "solves" of Alg. 1 / Alg. 2
 // (D_b^{-1} applied to Y_big rows or to right-hand sides) become small dense
 // GEMMs with D_b^{-1}, free of the serial dependence of substitutions.
-#include "gj.cuh"
+#include "hodlr_internal.cuh"
 
 namespace hodlr {
 
-// One CTA per leaf: D_b (FP64) -> FP32 in shared memory -> D_b^{-1} (FP32) in
-// the factor's leaf buffer, log|det D_b| and sign, status on a zero pivot or
-// a non-finite entry. Leaves of up to 64 rows are inverted by Gauss-Jordan
-// with partial pivoting directly; larger leaves (up to 128 rows) as 2 x 2
-// blocks [[A, B], [C, E]] with a 64-row leading block:
-//   X = A^{-1} B, S = E - C X, Y = C A^{-1}, Z = S^{-1} Y,
-//   D^{-1} = [[A^{-1} + X Z, -X S^{-1}], [-Z, S^{-1}]],
-// each of A and S inverted by Gauss-Jordan with partial pivoting within the
-// block (log|det D| = log|det A| + log|det S|).
-__global__ void __launch_bounds__(256) leaf_inv_kernel(int m, const double* __restrict__ D, float* __restrict__ Dinv,
-                                                       double* __restrict__ leaf_ld, DevStatus* st) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lda = m + 1;
-  float* A = reinterpret_cast<float*>(smem_raw);
-  float* T = A + (size_t)m * lda;  // 64 x 64 scratch
-  float* scol = T + 64 * 64;
-  float* srow = scol + 64;
-  float* spv = srow + 64;
-  int* spiv = reinterpret_cast<int*>(spv + 64);
-  int* spos = spiv + 64;
-  __shared__ double s_la1, s_la2;
-  __shared__ int s_neg1, s_neg2, s_sing1, s_sing2, s_bad;
+// One CTA (256 threads, 16 x 16) per leaf: D_b (FP64) -> FP32, padded to an
+// MB x MB matrix with the identity (MB = 64 or 128), inverted in registers by
+// Gauss-Jordan elimination with partial pivoting over all MB rows; thread
+// (ty, tx) holds the TT x TT block (TT = MB / 16) of rows ty*TT.. and columns
+// tx*TT... Rows are never exchanged: at step k the pivot row p_k is the unused
+// row with the largest |a_ik| (lowest row on ties, as getrf's first maximum)
+// and the exchange step turns row p_k into unknown k and column k into
+// equation p_k, so that at the end entry (r, c) of the tableau is
+// D^{-1}(step(r), p_c) and is written there. Per step, two barriers: (1) the
+// owners of column k publish it (the multipliers) and their pivot candidates,
+// (2) the owners of row p_k publish it scaled by 1/pivot; every thread then
+// applies the rank-1 update to its block. The pivots are getrf's pivots with
+// rows in the order p_0, p_1, ..., so log|det D_b| = sum log|pivot| and the
+// sign is the parity of the negative pivots and of the inversions of (p_k).
+// Writes D_b^{-1} (FP32, column-major) to the factor's leaf buffer, the
+// log-determinant pieces, and the status on a zero pivot or a non-finite entry.
+// If Dtc is given (m = MB = 128), D_b^{-1} is also written in the K-major
+// core-matrix layout of a tcgen05 operand (8-row x 16-byte cores: element
+// (i, k) at float (i/8)*1024 + (k/4)*32 + (i%8)*4 + k%4), the A operand of
+// the tensor-core leaf apply.
+template <int MB>
+__global__ void __launch_bounds__(256, 2) leaf_inv_kernel(int m, const double* __restrict__ D,
+                                                          float* __restrict__ Dinv, float* __restrict__ Dtc,
+                                                          double* __restrict__ leaf_ld, DevStatus* st) {
+  constexpr int TT = MB / 16;
+  constexpr int LD = MB + 1;
+  extern __shared__ float s_stage[];  // MB x LD: input, then output staging
+  __shared__ float s_f[2][MB];        // column k (multipliers), double-buffered by step parity
+  __shared__ float s_q[2][MB];        // pivot row scaled by 1/pivot
+  __shared__ float4 s_cand[2][8];     // per warp: |v| (-1: none), v, row
+  __shared__ int s_prow[MB];          // p_k
+  __shared__ int s_step[MB];          // step that took row r
+  __shared__ float s_piv[MB];
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, warp = tid >> 5, lane = tid & 31;
   const int b = blockIdx.x;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) { s_bad = 0; s_la2 = 0.0; s_neg2 = 0; s_sing2 = -1; }
-  __syncthreads();
+  if (tid == 0) s_bad = 0;
   const double* Db = D + (size_t)b * m * m;
-  int bad = 0;
-  for (int e = tid; e < m * m; e += nt) {
-    const double v = Db[e];
-    bad |= !isfinite(v);
-    A[(size_t)(e / m) * lda + (e % m)] = (float)v;
+  bool bad = false;
+  for (int e = tid; e < MB * MB; e += 256) {
+    const int c = e / MB, r = e % MB;
+    float v;
+    if (r < m && c < m) {
+      const double x = Db[(size_t)c * m + r];
+      bad |= !isfinite(x);
+      v = (float)x;
+    } else {
+      v = r == c ? 1.f : 0.f;
+    }
+    s_stage[c * LD + r] = v;
   }
-  if (bad) atomicOr(&s_bad, 1);
   __syncthreads();
-  if (s_bad && tid == 0) set_status(st, HODLR_ERR_NONFINITE, b, 0);
-  const int m1 = m > 64 ? 64 : m, m2 = m - m1;
-  float* A11 = A;
-  float* A12 = A + (size_t)m1 * lda;
-  float* A21 = A + m1;
-  float* A22 = A + (size_t)m1 * lda + m1;
-  gj_invert_smem<float>(A11, m1, lda, spiv, spv, scol, srow, spos, &s_la1, &s_neg1, &s_sing1);
-  gj_unscramble<float>(A11, m1, lda, spos, T);
-  if (m2 > 0) {
-    smem_gemm<float>(m1, m2, m1, 1.f, A11, lda, A12, lda, 0.f, T, m1);  // X = A^{-1} B
-    __syncthreads();
-    for (int e = tid; e < m1 * m2; e += nt) A12[(size_t)(e / m1) * lda + e % m1] = T[e];
-    __syncthreads();
-    smem_gemm<float>(m2, m2, m1, -1.f, A21, lda, A12, lda, 1.f, A22, lda);  // S = E - C X
-    __syncthreads();
-    smem_gemm<float>(m2, m1, m1, 1.f, A21, lda, A11, lda, 0.f, T, m2);  // Y = C A^{-1}
-    __syncthreads();
-    for (int e = tid; e < m2 * m1; e += nt) A21[(size_t)(e / m2) * lda + e % m2] = T[e];
-    __syncthreads();
-    gj_invert_smem<float>(A22, m2, lda, spiv, spv, scol, srow, spos, &s_la2, &s_neg2, &s_sing2);
-    gj_unscramble<float>(A22, m2, lda, spos, T);
-    smem_gemm<float>(m2, m1, m2, 1.f, A22, lda, A21, lda, 0.f, T, m2);  // Z = S^{-1} Y
-    __syncthreads();
-    for (int e = tid; e < m2 * m1; e += nt) A21[(size_t)(e / m2) * lda + e % m2] = -T[e];  // [21] = -Z
-    __syncthreads();
-    smem_gemm<float>(m1, m1, m2, -1.f, A12, lda, A21, lda, 1.f, A11, lda);  // [11] = A^{-1} + X Z
-    __syncthreads();
-    smem_gemm<float>(m1, m2, m2, 1.f, A12, lda, A22, lda, 0.f, T, m1);  // X S^{-1}
-    __syncthreads();
-    for (int e = tid; e < m1 * m2; e += nt) A12[(size_t)(e / m1) * lda + e % m1] = -T[e];  // [12]
-    __syncthreads();
+  if (bad) atomicOr(&s_bad, 1);
+  float a[TT][TT];
+#pragma unroll
+  for (int ii = 0; ii < TT; ++ii)
+#pragma unroll
+    for (int jj = 0; jj < TT; ++jj) a[ii][jj] = s_stage[(tx * TT + jj) * LD + ty * TT + ii];
+  uint32_t used = 0;  // bit ii: row ty*TT+ii has been a pivot row
+
+  for (int kb = 0; kb < 16; ++kb) {
+#pragma unroll
+    for (int kk = 0; kk < TT; ++kk) {
+      const int k = kb * TT + kk;
+      const int buf = k & 1;
+      // (1) owners of column k: multipliers, candidates; column k is zeroed so
+      // that the update below writes -f_i / pivot there
+      float bv = -1.f, bval = 0.f;
+      int brow = MB;
+      if (tx == kb) {
+#pragma unroll
+        for (int ii = 0; ii < TT; ++ii) {
+          const float x = a[ii][kk];
+          s_f[buf][ty * TT + ii] = x;
+          a[ii][kk] = 0.f;
+          float v = ((used >> ii) & 1u) ? -1.f : fabsf(x);
+          if (v != v) v = __int_as_float(0x7f800000);  // NaN ranks first: a total order keeps p uniform
+          if (v > bv) {
+            bv = v;
+            bval = x;
+            brow = ty * TT + ii;
+          }
+        }
+      }
+      {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, 16);
+        const float oval = __shfl_xor_sync(0xffffffffu, bval, 16);
+        const int orow = __shfl_xor_sync(0xffffffffu, brow, 16);
+        if (ov > bv || (ov == bv && orow < brow)) {
+          bv = ov;
+          bval = oval;
+          brow = orow;
+        }
+        if (lane == kb) s_cand[buf][warp] = make_float4(bv, bval, __int_as_float(brow), 0.f);
+      }
+      __syncthreads();
+      float pv = -1.f, piv = 0.f;
+      int p = MB;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        const float4 cd = s_cand[buf][w];
+        const int cr = __float_as_int(cd.z);
+        if (cd.x > pv || (cd.x == pv && cr < p)) {
+          pv = cd.x;
+          piv = cd.y;
+          p = cr;
+        }
+      }
+      const float rp = piv != 0.f ? 1.f / piv : 0.f;
+      const int pg = p / TT, pi = p % TT;
+      // (2) owners of row p: the pivot row scaled by 1/pivot (entry k: 1/pivot)
+      float q[TT];
+      if (ty == pg) {
+#pragma unroll
+        for (int jj = 0; jj < TT; ++jj) {
+          float x = 0.f;
+#pragma unroll
+          for (int ii = 0; ii < TT; ++ii) x = ii == pi ? a[ii][jj] : x;
+          q[jj] = (tx * TT + jj == k) ? rp : x * rp;
+          s_q[buf][tx * TT + jj] = q[jj];
+        }
+        used |= 1u << pi;
+      }
+      if (tid == 0) {
+        s_prow[k] = p;
+        s_step[p] = k;
+        s_piv[k] = piv;
+      }
+      __syncthreads();
+      // rank-1 update of every block; row p is then overwritten with q
+      float f[TT], qq[TT];
+#pragma unroll
+      for (int ii = 0; ii < TT; ++ii) f[ii] = s_f[buf][ty * TT + ii];
+#pragma unroll
+      for (int jj = 0; jj < TT; ++jj) qq[jj] = s_q[buf][tx * TT + jj];
+#pragma unroll
+      for (int ii = 0; ii < TT; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < TT; ++jj) a[ii][jj] = fmaf(-f[ii], qq[jj], a[ii][jj]);
+      if (ty == pg) {
+#pragma unroll
+        for (int ii = 0; ii < TT; ++ii)
+#pragma unroll
+          for (int jj = 0; jj < TT; ++jj) a[ii][jj] = ii == pi ? q[jj] : a[ii][jj];
+      }
+    }
   }
+  // D^{-1}(step(r), p_c) = tableau(r, c): staged, then written column-major
+#pragma unroll
+  for (int ii = 0; ii < TT; ++ii)
+#pragma unroll
+    for (int jj = 0; jj < TT; ++jj) {
+      const int r = ty * TT + ii, c = tx * TT + jj;
+      s_stage[s_prow[c] * LD + s_step[r]] = a[ii][jj];
+    }
+  __syncthreads();
   float* out = Dinv + (size_t)b * m * m;
-  for (int e = tid; e < m * m; e += nt) out[e] = A[(size_t)(e / m) * lda + (e % m)];
-  if (tid == 0) {
-    const int sing = s_sing1 >= 0 ? s_sing1 : (s_sing2 >= 0 ? m1 + s_sing2 : -1);
-    leaf_ld[2 * b] = s_la1 + s_la2;
-    leaf_ld[2 * b + 1] = sing >= 0 ? 0.0 : ((s_neg1 ^ s_neg2) ? -1.0 : 1.0);
-    if (sing >= 0) set_status(st, HODLR_ERR_SINGULAR_LEAF, b, sing);
+  for (int e = tid; e < m * m; e += 256) out[e] = s_stage[(e / m) * LD + (e % m)];
+  if (Dtc) {
+    float4* o = reinterpret_cast<float4*>(Dtc + (size_t)b * MB * MB);
+    for (int e4 = tid; e4 < MB * MB / 4; e4 += 256) {
+      const int il = e4 & 7, kq = (e4 >> 3) % (MB / 4), ig = e4 / (2 * MB);
+      const int i = ig * 8 + il, k = kq * 4;
+      o[e4] = make_float4(s_stage[k * LD + i], s_stage[(k + 1) * LD + i], s_stage[(k + 2) * LD + i],
+                          s_stage[(k + 3) * LD + i]);
+    }
+  }
+  if (warp == 0) {
+    double la = 0.0;
+    int ng = 0, sg = m, inv = 0;
+    for (int k = lane; k < m; k += 32) {
+      const float v = s_piv[k];
+      la += log(fabs((double)v));
+      ng ^= v < 0.f ? 1 : 0;
+      if (v == 0.f && k < sg) sg = k;
+      const int pk = s_prow[k];
+      for (int k2 = k + 1; k2 < m; ++k2) inv += s_prow[k2] < pk ? 1 : 0;
+    }
+    ng ^= inv & 1;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      la += __shfl_down_sync(0xffffffffu, la, off);
+      ng ^= __shfl_down_sync(0xffffffffu, ng, off);
+      sg = min(sg, __shfl_down_sync(0xffffffffu, sg, off));
+    }
+    if (lane == 0) {
+      if (s_bad) set_status(st, HODLR_ERR_NONFINITE, b, 0);
+      leaf_ld[2 * b] = la;
+      leaf_ld[2 * b + 1] = sg < m ? 0.0 : (ng ? -1.0 : 1.0);
+      if (sg < m) set_status(st, HODLR_ERR_SINGULAR_LEAF, b, sg);
+    }
   }
 }
 
@@ -90,10 +207,16 @@ bool leaf_uses_inverse(const Factor& F) { return F.prec != HODLR_PREC_FP64 && F.
 cudaError_t launch_leaf_inv(const Factor& F, const double* D, cudaStream_t s) {
   const int m = F.d.m;
   const int nleaf = 1 << F.d.L;
-  const size_t sm = (size_t)m * (m + 1) * 4 + 64 * 64 * 4 + 3 * 64 * 4 + 2 * 64 * 4;
   note_work((8.0 + 4.0) * nleaf * m * m, 2.0 * (double)m * m * m * nleaf);
-  cudaFuncSetAttribute(leaf_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  { leaf_inv_kernel<<<nleaf, 256, sm, s>>>(m, D, static_cast<float*>(F.lu), F.leaf_ld, F.status); note_launches(1); }
+  if (m > 64) {
+    const size_t sm = (size_t)128 * 129 * 4;
+    cudaFuncSetAttribute(leaf_inv_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    float* Dtc = F.leaf_tc ? reinterpret_cast<float*>(F.P) : nullptr;  // m == 128 here
+    { leaf_inv_kernel<128><<<nleaf, 256, sm, s>>>(m, D, static_cast<float*>(F.lu), Dtc, F.leaf_ld, F.status); note_launches(1); }
+  } else {
+    const size_t sm = (size_t)64 * 65 * 4;
+    { leaf_inv_kernel<64><<<nleaf, 256, sm, s>>>(m, D, static_cast<float*>(F.lu), nullptr, F.leaf_ld, F.status); note_launches(1); }
+  }
   return cudaGetLastError();
 }
 

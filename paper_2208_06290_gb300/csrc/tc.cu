@@ -568,3 +568,218 @@ cudaError_t launch_update_coupled_tc(const Factor& F, int c, cudaStream_t s) {
 }
 
 }  // namespace hodlr
+
+namespace hodlr {
+
+// ===========================================================================
+// Tensor-core leaf stage of the BF16 factor (Alg. 3, first step; Eq. e:u):
+// Y(I_b, :) = D_b^{-1} U_big(I_b, :) for every leaf b of m = 128 rows, with
+// tcgen05.mma kind::tf32 (FP32 operands read as TF32, FP32 accumulation):
+// M = 128 rows of the leaf, N = kLaNC columns of U per MMA chain, K = 128.
+//   A = D_b^{-1}: written by the leaf inverse in the K-major core-matrix
+//       layout (8-row x 16-byte cores, LBO = 128 B along K, SBO = 4096 B
+//       between 8-row groups), 64 KB per leaf, staged by one bulk copy;
+//   B = U(I_b, cols)^T: U is column-major, i.e. K-contiguous per column; each
+//       thread converts 4 consecutive FP64 rows of one column to FP32 and
+//       stores one 16-byte core row;
+//   D (TMEM, FP32) -> BF16 into a [column][row] tile, stored by TMA.
+// FP64 -> FP32 for the TF32 operand: the FP64 sign and exponent are rebiased
+// and the top 23 significand bits kept (truncation; the MMA uses the top 10),
+// on the integer pipe; magnitudes below 2^-126 become zero.
+namespace {
+
+constexpr int kLaNC = 64;  // columns of U per MMA chain
+
+struct LeafTcSmem {
+  static constexpr uint32_t kABytes = 128 * 128 * 4;
+  static constexpr uint32_t kBBytes = kLaNC * 128 * 4;
+  static constexpr uint32_t kYBytes = 128 * kLaNC * 2;
+  static constexpr uint32_t kBarOff = kABytes + kBBytes + kYBytes;
+  static constexpr uint32_t kBytes = kBarOff + 64 + 128;
+};
+
+__device__ __forceinline__ uint32_t f64_to_f32_trunc_bits(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const uint32_t sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  const uint32_t mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  uint32_t bits = sign | ((uint32_t)(e - 896) << 23) | mant;
+  if (e <= 896) bits = sign;                                                 // tiny -> signed zero
+  if (e >= 1151) bits = sign | 0x7F800000u | ((hi & 0xFFFFFu) | lo ? 0x400000u : 0u);  // inf / NaN
+  return bits;
+}
+
+__host__ __device__ constexpr uint32_t idesc_tf32_f32(int M, int N) {
+  return (1u << 4)                     // D format: F32
+         | (2u << 7)                   // A format: TF32
+         | (2u << 10)                  // B format: TF32
+         | ((uint32_t)(N >> 3) << 17)  // N / 8
+         | ((uint32_t)(M >> 4) << 24); // M / 16
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256, 2) leaf_apply_tc_kernel(const __grid_constant__ CUtensorMap mapY,
+                                                               int64_t nleaf, int rL,
+                                                               const float* __restrict__ Acore,
+                                                               const double* __restrict__ U, int64_t ldu,
+                                                               DevStatus* st) {
+  using S = LeafTcSmem;
+  constexpr uint32_t kSBO = 4096;  // 32 cores along K x 128 B
+  constexpr uint32_t kTmemCols = kLaNC;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  uint8_t* sA = smem;
+  uint8_t* sB = sA + S::kABytes;
+  __nv_bfloat16* sY = reinterpret_cast<__nv_bfloat16*>(sB + S::kBBytes);
+  uint64_t* bar_a = reinterpret_cast<uint64_t*>(smem + S::kBarOff);
+  uint64_t* bar_mma = bar_a + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_a + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (tid == 0) {
+    tc::mbar_init(bar_a, 1);
+    tc::mbar_init(bar_mma, 1);
+    tc::fence_mbar_init();
+    tc::prefetch_tmap(&mapY);
+  }
+  if (warp == 0) tc::tmem_alloc(tmem_slot, kTmemCols);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const int nchunks = rL / kLaNC + (rL % kLaNC ? 1 : 0);
+  bool ok = true;
+  uint32_t ph_a = 0, ph_mma = 0;
+  bool a_pending = false, mma_pending = false;  // thread 0's view
+  for (int64_t b = blockIdx.x; b < nleaf && ok; b += gridDim.x) {
+    const int64_t row0 = b * 128;
+    if (tid == 0) {
+      tc::mbar_expect_tx(bar_a, S::kABytes);
+      bulk_load_1d(sA, Acore + (size_t)b * 128 * 128, S::kABytes, bar_a);
+      a_pending = true;
+    }
+    for (int ch = 0; ch < nchunks && ok; ++ch) {
+      const int col0 = ch * kLaNC;
+      const int nc = (rL - col0) < kLaNC ? (rL - col0) : kLaNC;  // multiple of 32
+      // B: nc columns x 128 rows; item = (8-column group, k quad, column in group)
+      {
+        constexpr int kItems = kLaNC * 32;  // 16-byte core rows of a full chunk
+        constexpr int kPer = kItems / 256;
+        double2 v0[kPer], v1[kPer];
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+          const int it = tid + u * 256;
+          const int jl = it & 7, kq = (it >> 3) & 31, jg = it >> 8;
+          const int j = jg * 8 + jl;
+          if (j < nc) {
+            const double* src = U + (int64_t)(col0 + j) * ldu + row0 + kq * 4;
+            v0[u] = *reinterpret_cast<const double2*>(src);
+            v1[u] = *reinterpret_cast<const double2*>(src + 2);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+          const int it = tid + u * 256;
+          const int jl = it & 7, kq = (it >> 3) & 31, jg = it >> 8;
+          if (jg * 8 + jl < nc)
+            *reinterpret_cast<uint4*>(sB + jg * kSBO + kq * 128 + jl * 16) =
+                make_uint4(f64_to_f32_trunc_bits(v0[u].x), f64_to_f32_trunc_bits(v0[u].y),
+                           f64_to_f32_trunc_bits(v1[u].x), f64_to_f32_trunc_bits(v1[u].y));
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc::tc_fence_before();
+      if (ch == 0) {
+        ok = __syncthreads_and(tc::mbar_wait(bar_a, ph_a)) != 0;
+        if (!ok) break;
+        ph_a ^= 1;
+        a_pending = false;
+      } else {
+        __syncthreads();
+      }
+      tc::tc_fence_after();
+      if (tid == 0) {
+        const uint32_t idesc = idesc_tf32_f32(128, nc);
+        const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+#pragma unroll
+        for (int ks = 0; ks < 16; ++ks)  // K = 8 per MMA: two cores along K
+          mma_tf32(tmem, tc::desc_noswz_kmajor(a0 + ks * 256, 128, kSBO),
+                   tc::desc_noswz_kmajor(b0 + ks * 256, 128, kSBO), idesc, ks != 0);
+        tc::mma_commit(bar_mma);
+        mma_pending = true;
+        bulk_wait_read0();  // the previous chunk's store has left sY
+      }
+      ok = __syncthreads_and(tc::mbar_wait(bar_mma, ph_mma)) != 0;
+      if (!ok) break;
+      ph_mma ^= 1;
+      mma_pending = false;
+      tc::tc_fence_after();
+      // warps w and w+4 share TMEM lanes 32 (w % 4) .. +31 and split the columns
+      const int m = (warp & 3) * 32 + lane;
+      for (int cb = (warp >> 2) * 32; cb < nc; cb += 64) {
+        float v[32];
+        tc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + cb, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) sY[(cb + j) * 128 + m] = __float2bfloat16_rn(v[j]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc::tc_fence_before();
+      __syncthreads();
+      tc::tc_fence_after();
+      if (tid == 0) {
+        for (int bx = 0; bx < nc / kFuBox; ++bx)
+          tma_store_2d(&mapY, sY + bx * 128 * kFuBox, (int32_t)row0, col0 + bx * kFuBox);
+        bulk_commit();
+      }
+    }
+  }
+  if (tid == 0) {
+    if (a_pending) tc::mbar_wait(bar_a, ph_a);
+    if (mma_pending) tc::mbar_wait(bar_mma, ph_mma);
+    bulk_wait0();
+    if (!ok) set_status(st, HODLR_ERR_TIMEOUT, 0, 3);
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+bool leaf_apply_tc_supported(const Factor& F) {
+  return g_use_tc && F.prec == HODLR_PREC_BF16 && F.d.m == 128 && (F.d.r * F.d.L) % 32 == 0 &&
+         encode_fn() != nullptr;
+}
+
+cudaError_t launch_leaf_apply_tc(const Factor& F, const double* U, int64_t ldu, cudaStream_t s) {
+  ProfScope prof_(KC_LEAF_SOLVE, s);
+  const int64_t N = F.d.N;
+  const int rL = F.d.r * F.d.L;
+  const int64_t nleaf = (int64_t)1 << F.d.L;
+  note_work(8.0 * (double)N * rL + 2.0 * (double)N * rL + 4.0 * (double)nleaf * 128 * 128,
+            2.0 * (double)N * 128 * rL);
+  CUtensorMap mY;
+  if (!make_map_plain(&mY, F.Y, N, rL, N)) return cudaErrorInvalidValue;
+  using S = LeafTcSmem;
+  const int per_sm = (int)((227 * 1024) / (S::kBytes + 1024));
+  int64_t grid = (int64_t)sm_count() * (per_sm < 1 ? 1 : per_sm);
+  if (grid > nleaf) grid = nleaf;
+  cudaFuncSetAttribute(leaf_apply_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kBytes);
+  {
+    leaf_apply_tc_kernel<<<(unsigned)grid, 256, S::kBytes, s>>>(mY, nleaf, rL, reinterpret_cast<const float*>(F.P),
+                                                                 U, ldu, F.status);
+    note_launches(1);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace hodlr

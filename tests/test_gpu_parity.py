@@ -95,7 +95,8 @@ def test_dense_c0_configuration(cuda_lib):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
-@pytest.mark.parametrize("N,L,r", [(256, 2, 4), (384, 3, 5), (4096, 6, 16), (2048, 3, 32), (1024, 4, 64), (1 << 14, 6, 8)])
+@pytest.mark.parametrize("N,L,r", [(256, 2, 4), (384, 3, 5), (800, 3, 8), (4096, 6, 16), (2048, 3, 32),
+                                   (1024, 4, 64), (1 << 14, 6, 8), (1 << 13, 6, 16), (1 << 14, 7, 32)])
 def test_mixed_refined_reaches_1e10(cuda_lib, prec, N, L, r):
     hb = cuda_lib
     (Dm, Um, Vm, Bm), (D, U, V, B) = make_case(N, L, r, seed=11 * N + r, k=2)
