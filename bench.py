@@ -67,13 +67,37 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
 
-# FP64 FMA-pipe peak used for ALU-bound kernels: derived in the design notes
-# from the sampled SM clock (see fp64_peak_tflops).
+# ALU peaks for kernels bound by plain arithmetic, from the unit counts and the
+# sampled SM clock: FP64 FMA pipe 2 FMA/clk/SM (4 flop), FP32 128 FMA/clk/SM
+# (256 flop), 152 SMs.
 FP64_FLOP_PER_CLK_PER_SM = 4.0
+FP32_FLOP_PER_CLK_PER_SM = 256.0
 
 
 def fp64_peak_tflops(sm_mhz):
     return 152 * FP64_FLOP_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
+
+
+def fp32_peak_tflops(sm_mhz):
+    return 152 * FP32_FLOP_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
+
+
+def class_bound(cls, prec):
+    """Resource that bounds each kernel class of the library's profiler:
+    'hbm' (bytes), 'alu64' / 'alu32' (flops on the FP64 / FP32 pipes)."""
+    if cls in ("vector", "reduce_chunks", "logdet"):
+        return "hbm"
+    if cls in ("matvec", "leaf_matvec"):
+        return "alu64"          # FP64 residual matvec: 0.25 flop/B > FP64 ridge ~0.17 flop/B
+    if prec == "fp64":
+        return "alu64"
+    if cls == "coupling":
+        return "alu32" if prec == "bf16" else "alu64"
+    if cls == "leaf_lu":
+        return "alu32"
+    if prec == "fp32" and cls in ("leaf_solve", "project", "update", "coupling_apply"):
+        return "alu32"
+    return "hbm"
 
 
 # ----------------------------------------------------------------- inputs
@@ -271,26 +295,36 @@ def run_native(args, w, rank, world):
         e2e = {"value": world * flops / float(te.item()) / 1e12, "unit": "TFLOP/s", "seconds": float(te.item()),
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
-    # roofline of the dominant kernel class, from the live CUDA-event brackets
+    # roofline of every kernel class, from the live CUDA-event brackets; the
+    # line's roofline is the dominant (longest) class
     pk = peaks()
-    dom = max(prof, key=lambda c: prof[c][0])
-    dms, dn = prof[dom]
-    dbytes, dflops = work[dom]
-    sm_mhz = clocks.get("sm_mhz") or 1462.0
-    if dom in ("coupling",) or prec == "fp64":
-        achieved = dflops / (dms / 1e3) / 1e12
-        peak = fp64_peak_tflops(sm_mhz)
-        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": f"FP64 FMA pipe, {FP64_FLOP_PER_CLK_PER_SM:g} flop/clk/SM x 152 SMs x median "
-                               f"{sm_mhz:.0f} MHz"}
-    else:
-        achieved = dbytes / (dms / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": pk["source"]}
-    roof["launches_in_region"] = dn
-    roof["avg_launch_us"] = dms * 1e3 / max(dn, 1)
-    roof["bytes_per_launch"] = dbytes / max(dn, 1)
+    sm_mhz = clocks.get("sm_mhz") or 1920.0
+
+    def roof_of(cls):
+        cms, cn = prof[cls]
+        cbytes, cflops = work[cls]
+        bound = class_bound(cls, prec)
+        if bound == "hbm":
+            ach, peak, unit = cbytes / (cms / 1e3) / 1e9, pk["hbm_gbs"], "GB/s"
+            src = f"MEASURED_PEAKS.json hbm_gbs ({pk['source']})"
+        else:
+            per_clk = FP64_FLOP_PER_CLK_PER_SM if bound == "alu64" else FP32_FLOP_PER_CLK_PER_SM
+            ach = cflops / (cms / 1e3) / 1e12
+            peak = fp64_peak_tflops(sm_mhz) if bound == "alu64" else fp32_peak_tflops(sm_mhz)
+            unit = "TFLOP/s"
+            src = f"{'FP64' if bound == 'alu64' else 'FP32'} pipe {per_clk:g} flop/clk/SM x 152 SMs x median " \
+                  f"{sm_mhz:.0f} MHz"
+        return {"bound": "hbm" if bound == "hbm" else "alu", "pipe": bound, "kernel": cls, "achieved": ach,
+                "peak": peak, "unit": unit, "frac": ach / peak, "traffic": None, "peak_source": src,
+                "launches_in_region": cn, "avg_launch_us": cms * 1e3 / max(cn, 1),
+                "bytes_per_launch": cbytes / max(cn, 1), "flops_per_launch": cflops / max(cn, 1),
+                "ms": cms / args.steps}
+
+    active = [c for c in prof if prof[c][1] and prof[c][0] > 0]
+    dom = max(active, key=lambda c: prof[c][0])
+    roof = roof_of(dom)
+    classes = {c: {k2: (round(v, 4) if isinstance(v, float) else v) for k2, v in roof_of(c).items()
+                   if k2 in ("pipe", "ms", "launches_in_region", "achieved", "unit", "frac")} for c in active}
     share = {c: round(prof[c][0] / max(sum(v[0] for v in prof.values()), 1e-9), 4) for c in prof if prof[c][1]}
 
     line = {
@@ -300,7 +334,8 @@ def run_native(args, w, rank, world):
         "dtype": "bf16" if prec == "bf16" else ("f32" if prec == "fp32" else "f64"),
         "data": "synthetic",
         "config": {"workload": args.workload, "description": w["desc"], "N": N, "leaf": m, "levels": L, "rank": r,
-                   "rhs": k, "factor_precision": prec, "coupling_precision": "fp64",
+                   "rhs": k, "factor_precision": prec,
+                   "coupling_precision": "fp32" if (prec == "bf16" and r <= 32) else "fp64",
                    "residual_precision": "fp64", "solver": w["solver"], "tol": 1e-10,
                    "flops_per_step": flops, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (D, U, V = %.1f GB FP64)" % (8.0 * (m * N + 2 * r * N * L) / 1e9)},
@@ -309,6 +344,7 @@ def run_native(args, w, rank, world):
         "e2e": e2e,
         "roofline": roof,
         "kernel_time_share": share,
+        "kernel_classes": classes,
         "gpu_launches": launches,
         "clocks": clocks,
     }

@@ -38,7 +38,7 @@ long long g_n[KC_COUNT];
 double g_bytes[KC_COUNT], g_flops[KC_COUNT];
 const char* kClassName[KC_COUNT] = {"leaf_lu", "leaf_solve", "project", "coupling", "coupling_apply",
                                     "update", "reduce_chunks", "leaf_matvec", "vector", "logdet",
-                                    "project_tc", "update_tc"};
+                                    "project_tc", "update_tc", "matvec"};
 
 cudaEvent_t pool_get() {
   std::lock_guard<std::mutex> g(g_mu);

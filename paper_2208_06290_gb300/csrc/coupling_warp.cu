@@ -1,14 +1,15 @@
-// Coupling matrices of the low-precision (FP32 / BF16) factors: one warp per
-// parent, FP32 arithmetic, r <= 32.
+// Coupling matrices of the BF16 factor: one warp per parent, FP32
+// arithmetic, r <= 32 (the FP32 and FP64 factors keep the FP64 CTA kernel).
 //
 // Same quantities as the FP64 CTA kernel (level.cu): with
 // K~ = [[I, T_b], [T_a, I]] (Eq. e:k) and the Schur complement
 // S = I - T_a T_b,
 //   K~^{-1} = [[I + T_b S^{-1} T_a, -T_b S^{-1}], [-S^{-1} T_a, S^{-1}]],
 //   det K~ = det S,
-// written in FP64 so that every consumer reads one layout. The factor these
-// inverses belong to is BF16- or FP32-accurate, so FP32 here costs nothing in
-// accuracy, and FP32 runs at 64x the FP64 rate of this GPU.
+// written in FP64 so that every consumer reads one layout. T_a and T_b are
+// products of BF16 panels, so FP32 here adds nothing to their error (the
+// paper's single-precision runs do every step in FP32), and FP32 runs at 64x
+// the FP64 rate of this GPU.
 //
 // Lane i holds row i of S (padded to 32 x 32 with the identity) in registers.
 // Gauss-Jordan with partial pivoting runs without moving rows: at step k the
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(32 * kCwWarps) coupling_factor_warp_kernel(int
   }
 }
 
-bool coupling_warp_supported(const Factor& F) { return F.prec != HODLR_PREC_FP64 && F.d.r <= 32; }
+bool coupling_warp_supported(const Factor& F) { return F.prec == HODLR_PREC_BF16 && F.d.r <= 32; }
 
 cudaError_t launch_coupling_factor_warp(const Factor& F, int c, cudaStream_t s) {
   const int r = F.d.r;

@@ -43,6 +43,53 @@ __device__ __forceinline__ TD conv(TS s) {
   return d;
 }
 
+// Four consecutive elements (16-byte aligned for float / double, 8-byte for
+// BF16) loaded in one or two vector accesses and converted; store4 likewise.
+template <typename TA>
+__device__ __forceinline__ void load4(const __nv_bfloat16* p, TA (&o)[4]) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  o[0] = (TA)__uint_as_float(u.x << 16);
+  o[1] = (TA)__uint_as_float(u.x & 0xffff0000u);
+  o[2] = (TA)__uint_as_float(u.y << 16);
+  o[3] = (TA)__uint_as_float(u.y & 0xffff0000u);
+}
+template <typename TA>
+__device__ __forceinline__ void load4(const float* p, TA (&o)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = (TA)v.x;
+  o[1] = (TA)v.y;
+  o[2] = (TA)v.z;
+  o[3] = (TA)v.w;
+}
+template <typename TA>
+__device__ __forceinline__ void load4(const double* p, TA (&o)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  const double2 b = *reinterpret_cast<const double2*>(p + 2);
+  o[0] = (TA)a.x;
+  o[1] = (TA)a.y;
+  o[2] = (TA)b.x;
+  o[3] = (TA)b.y;
+}
+template <typename TA>
+__device__ __forceinline__ void store4(float* p, const TA (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+}
+template <typename TA>
+__device__ __forceinline__ void store4(double* p, const TA (&v)[4]) {
+  *reinterpret_cast<double2*>(p) = make_double2((double)v[0], (double)v[1]);
+  *reinterpret_cast<double2*>(p + 2) = make_double2((double)v[2], (double)v[3]);
+}
+template <typename TA>
+__device__ __forceinline__ void store4(__nv_bfloat16* p, const TA (&v)[4]) {
+  __nv_bfloat16 b[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) b[i] = __float2bfloat16_rn((float)v[i]);
+  uint2 u;
+  u.x = (uint32_t)__bfloat16_as_ushort(b[0]) | ((uint32_t)__bfloat16_as_ushort(b[1]) << 16);
+  u.y = (uint32_t)__bfloat16_as_ushort(b[2]) | ((uint32_t)__bfloat16_as_ushort(b[3]) << 16);
+  *reinterpret_cast<uint2*>(p) = u;
+}
+
 // ---------------------------------------------------------------- tree geometry
 // Child level c (1..L): nodes of n_c = N >> c = m * 2^(L-c) rows. Projections
 // are split into row chunks of ch(c) rows, n_c halved until it is at most
@@ -106,7 +153,7 @@ size_t factor_workspace_bytes(const hodlr_desc& d, hodlr_prec prec);
 // ---------------------------------------------------------------- launch accounting
 enum KernelClass {
   KC_LEAF_LU = 0, KC_LEAF_SOLVE, KC_PROJECT, KC_COUPLING, KC_COUPLING_APPLY, KC_UPDATE, KC_REDUCE,
-  KC_LEAF_MATVEC, KC_VECTOR, KC_LOGDET, KC_PROJECT_TC, KC_UPDATE_TC, KC_COUNT
+  KC_LEAF_MATVEC, KC_VECTOR, KC_LOGDET, KC_PROJECT_TC, KC_UPDATE_TC, KC_MATVEC, KC_COUNT
 };
 // Called by every launcher right after its kernel launch(es): counts them and,
 // when profiling is on, records the closing event of the bracket that
@@ -150,7 +197,7 @@ cudaError_t launch_update(int64_t N, int r, int c, const TB* Bas, int64_t ldb, i
 // LU, log|det|, solve for the ancestor columns; W' written to each child's
 // first chunk slot. Solve modes reuse the stored LU.
 cudaError_t launch_coupling_factor(const Factor& F, int c, cudaStream_t s);
-// FP32 warp-per-parent variant for the low-precision factors (r <= 32)
+// FP32 warp-per-parent variant for the BF16 factor (r <= 32)
 bool coupling_warp_supported(const Factor& F);
 cudaError_t launch_coupling_factor_warp(const Factor& F, int c, cudaStream_t s);
 cudaError_t launch_coupling_solve(const Factor& F, int c, double* P, int k, int trans, cudaStream_t s);

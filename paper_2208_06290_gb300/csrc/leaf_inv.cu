@@ -12,22 +12,48 @@ namespace hodlr {
 // MB x MB matrix with the identity (MB = 64 or 128), inverted in registers by
 // Gauss-Jordan elimination with partial pivoting over all MB rows; thread
 // (ty, tx) holds the TT x TT block (TT = MB / 16) of rows ty*TT.. and columns
-// tx*TT... Rows are never exchanged: at step k the pivot row p_k is the unused
-// row with the largest |a_ik| (lowest row on ties, as getrf's first maximum)
-// and the exchange step turns row p_k into unknown k and column k into
-// equation p_k, so that at the end entry (r, c) of the tableau is
-// D^{-1}(step(r), p_c) and is written there. Per step, two barriers: (1) the
-// owners of column k publish it (the multipliers) and their pivot candidates,
-// (2) the owners of row p_k publish it scaled by 1/pivot; every thread then
-// applies the rank-1 update to its block. The pivots are getrf's pivots with
-// rows in the order p_0, p_1, ..., so log|det D_b| = sum log|pivot| and the
-// sign is the parity of the negative pivots and of the inversions of (p_k).
-// Writes D_b^{-1} (FP32, column-major) to the factor's leaf buffer, the
-// log-determinant pieces, and the status on a zero pivot or a non-finite entry.
+// tx*TT.., with ty = lane % 16 and tx = 2 warp + lane / 16, so that each
+// column group lives in one half-warp. Rows are never exchanged: at step k the
+// pivot row p_k is the unused row with the largest |a_ik| (lowest row on
+// ties, as getrf's first maximum) and the exchange step turns row p_k into
+// unknown k and column k into equation p_k, so that at the end entry (r, c) of
+// the tableau is D^{-1}(step(r), p_c) and is written there. Per step, two
+// barriers: (1) the half-warp owning column k publishes it (the multipliers)
+// and the pivot it found with shuffles, (2) the owners of row p_k publish it
+// scaled by 1/pivot; every thread then applies the rank-1 update to its block.
+// The pivots are getrf's pivots with rows in the order p_0, p_1, ..., so
+// log|det D_b| = sum log|pivot| and the sign is the parity of the negative
+// pivots and of the inversions of (p_k). Writes D_b^{-1} (FP32, column-major)
+// to the factor's leaf buffer, the log-determinant pieces, and the status on a
+// zero pivot or a non-finite entry.
 // If Dtc is given (m = MB = 128), D_b^{-1} is also written in the K-major
 // core-matrix layout of a tcgen05 operand (8-row x 16-byte cores: element
 // (i, k) at float (i/8)*1024 + (k/4)*32 + (i%8)*4 + k%4), the A operand of
 // the tensor-core leaf apply.
+template <int TT, int II = 0>
+__device__ __forceinline__ void get_row(const float (&a)[TT][TT], int pi, float (&q)[TT]) {
+  if constexpr (II < TT) {
+    if (pi == II) {
+#pragma unroll
+      for (int jj = 0; jj < TT; ++jj) q[jj] = a[II][jj];
+    } else {
+      get_row<TT, II + 1>(a, pi, q);
+    }
+  }
+}
+
+template <int TT, int II = 0>
+__device__ __forceinline__ void set_row(float (&a)[TT][TT], int pi, const float (&q)[TT]) {
+  if constexpr (II < TT) {
+    if (pi == II) {
+#pragma unroll
+      for (int jj = 0; jj < TT; ++jj) a[II][jj] = q[jj];
+    } else {
+      set_row<TT, II + 1>(a, pi, q);
+    }
+  }
+}
+
 template <int MB>
 __global__ void __launch_bounds__(256, 2) leaf_inv_kernel(int m, const double* __restrict__ D,
                                                           float* __restrict__ Dinv, float* __restrict__ Dtc,
@@ -37,12 +63,13 @@ __global__ void __launch_bounds__(256, 2) leaf_inv_kernel(int m, const double* _
   extern __shared__ float s_stage[];  // MB x LD: input, then output staging
   __shared__ float s_f[2][MB];        // column k (multipliers), double-buffered by step parity
   __shared__ float s_q[2][MB];        // pivot row scaled by 1/pivot
-  __shared__ float4 s_cand[2][8];     // per warp: |v| (-1: none), v, row
+  __shared__ float2 s_pv[2];          // (pivot value, pivot row as int bits)
   __shared__ int s_prow[MB];          // p_k
   __shared__ int s_step[MB];          // step that took row r
   __shared__ float s_piv[MB];
   __shared__ int s_bad;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ty = lane & 15, tx = (warp << 1) | (lane >> 4);
   const int b = blockIdx.x;
   if (tid == 0) s_bad = 0;
   const double* Db = D + (size_t)b * m * m;
@@ -69,72 +96,66 @@ __global__ void __launch_bounds__(256, 2) leaf_inv_kernel(int m, const double* _
   uint32_t used = 0;  // bit ii: row ty*TT+ii has been a pivot row
 
   for (int kb = 0; kb < 16; ++kb) {
+    const bool col_owner = tx == kb;  // one half-warp
 #pragma unroll
     for (int kk = 0; kk < TT; ++kk) {
       const int k = kb * TT + kk;
       const int buf = k & 1;
-      // (1) owners of column k: multipliers, candidates; column k is zeroed so
-      // that the update below writes -f_i / pivot there
-      float bv = -1.f, bval = 0.f;
-      int brow = MB;
-      if (tx == kb) {
+      // (1) the half-warp owning column k: multipliers and the pivot; column k
+      // is zeroed so that the update below writes -f_i / pivot there
+      if (warp == (kb >> 1)) {
+        float bv = -1.f, bval = 0.f;
+        int brow = MB;
+        if (col_owner) {
 #pragma unroll
-        for (int ii = 0; ii < TT; ++ii) {
-          const float x = a[ii][kk];
-          s_f[buf][ty * TT + ii] = x;
-          a[ii][kk] = 0.f;
-          float v = ((used >> ii) & 1u) ? -1.f : fabsf(x);
-          if (v != v) v = __int_as_float(0x7f800000);  // NaN ranks first: a total order keeps p uniform
-          if (v > bv) {
-            bv = v;
-            bval = x;
-            brow = ty * TT + ii;
+          for (int ii = 0; ii < TT; ++ii) {
+            const float x = a[ii][kk];
+            s_f[buf][ty * TT + ii] = x;
+            a[ii][kk] = 0.f;
+            float v = ((used >> ii) & 1u) ? -1.f : fabsf(x);
+            if (v != v) v = __int_as_float(0x7f800000);  // NaN ranks first: a total order keeps p uniform
+            if (v > bv) {
+              bv = v;
+              bval = x;
+              brow = ty * TT + ii;
+            }
           }
         }
-      }
-      {
-        const float ov = __shfl_xor_sync(0xffffffffu, bv, 16);
-        const float oval = __shfl_xor_sync(0xffffffffu, bval, 16);
-        const int orow = __shfl_xor_sync(0xffffffffu, brow, 16);
-        if (ov > bv || (ov == bv && orow < brow)) {
-          bv = ov;
-          bval = oval;
-          brow = orow;
+#pragma unroll
+        for (int off = 8; off > 0; off >>= 1) {  // within each half-warp
+          const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
+          const float oval = __shfl_xor_sync(0xffffffffu, bval, off);
+          const int orow = __shfl_xor_sync(0xffffffffu, brow, off);
+          if (ov > bv || (ov == bv && orow < brow)) {
+            bv = ov;
+            bval = oval;
+            brow = orow;
+          }
         }
-        if (lane == kb) s_cand[buf][warp] = make_float4(bv, bval, __int_as_float(brow), 0.f);
+        if (col_owner && ty == 0) {
+          s_pv[buf] = make_float2(bval, __int_as_float(brow));
+          s_prow[k] = brow;
+          s_step[brow] = k;
+          s_piv[k] = bval;
+        }
       }
       __syncthreads();
-      float pv = -1.f, piv = 0.f;
-      int p = MB;
-#pragma unroll
-      for (int w = 0; w < 8; ++w) {
-        const float4 cd = s_cand[buf][w];
-        const int cr = __float_as_int(cd.z);
-        if (cd.x > pv || (cd.x == pv && cr < p)) {
-          pv = cd.x;
-          piv = cd.y;
-          p = cr;
-        }
-      }
+      const float2 pvv = s_pv[buf];
+      const float piv = pvv.x;
+      const int p = __float_as_int(pvv.y);
       const float rp = piv != 0.f ? 1.f / piv : 0.f;
       const int pg = p / TT, pi = p % TT;
       // (2) owners of row p: the pivot row scaled by 1/pivot (entry k: 1/pivot)
       float q[TT];
-      if (ty == pg) {
+      const bool row_owner = ty == pg;
+      if (row_owner) {
+        get_row<TT>(a, pi, q);
 #pragma unroll
         for (int jj = 0; jj < TT; ++jj) {
-          float x = 0.f;
-#pragma unroll
-          for (int ii = 0; ii < TT; ++ii) x = ii == pi ? a[ii][jj] : x;
-          q[jj] = (tx * TT + jj == k) ? rp : x * rp;
+          q[jj] = (tx * TT + jj == k) ? rp : q[jj] * rp;
           s_q[buf][tx * TT + jj] = q[jj];
         }
         used |= 1u << pi;
-      }
-      if (tid == 0) {
-        s_prow[k] = p;
-        s_step[p] = k;
-        s_piv[k] = piv;
       }
       __syncthreads();
       // rank-1 update of every block; row p is then overwritten with q
@@ -147,12 +168,7 @@ __global__ void __launch_bounds__(256, 2) leaf_inv_kernel(int m, const double* _
       for (int ii = 0; ii < TT; ++ii)
 #pragma unroll
         for (int jj = 0; jj < TT; ++jj) a[ii][jj] = fmaf(-f[ii], qq[jj], a[ii][jj]);
-      if (ty == pg) {
-#pragma unroll
-        for (int ii = 0; ii < TT; ++ii)
-#pragma unroll
-          for (int jj = 0; jj < TT; ++jj) a[ii][jj] = ii == pi ? q[jj] : a[ii][jj];
-      }
+      if (row_owner) set_row<TT>(a, pi, q);
     }
   }
   // D^{-1}(step(r), p_c) = tableau(r, c): staged, then written column-major

@@ -143,36 +143,110 @@ __device__ __forceinline__ TA warp_transpose_reduce32(TA (&v)[32]) {
   return v[0];
 }
 
+// One right-hand side: wpc warps (1, 2, 4 or 8) per row chunk, 8 / wpc chunks
+// per CTA; warp w of a chunk sums rows [w ch/wpc, (w+1) ch/wpc) (lane l rows
+// l, l+32, ...), the transposed butterfly leaves column j's sum in lane j, and
+// the chunk's warps are added in a fixed order through shared memory.
 template <typename TB, typename TR, typename TA, int RT>
 __global__ void __launch_bounds__(256) project_k1_kernel(int64_t N, int r, int c, const TB* __restrict__ Bas,
                                                          int64_t ldb, int bas_block, const TR* __restrict__ R,
-                                                         double* __restrict__ P) {
-  const int lane = threadIdx.x & 31;
-  const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (q >= num_chunks(N, c)) return;
+                                                         double* __restrict__ P, int wpc) {
+  __shared__ TA sPart[8][RT];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int cpb = 8 / wpc;
+  const int sub = warp / wpc, w = warp % wpc;
+  const int64_t q = (int64_t)blockIdx.x * cpb + sub;
+  const bool active = q < num_chunks(N, c);
   const int64_t ch = chunk_rows(N, c);
-  const int64_t row0 = q * ch;
-  const TB* B0 = Bas + (int64_t)bas_block * r * ldb + row0;
-  const TR* R0 = R + row0;
+  const int64_t rpw = ch / wpc;
+  const int64_t row0 = q * ch + w * rpw;
   TA acc[RT];
 #pragma unroll
   for (int j = 0; j < RT; ++j) acc[j] = TA(0);
-  for (int64_t i = lane; i < ch; i += 32) {
-    const TA x = conv<TA>(R0[i]);
+  if (active) {
+    const TB* B0 = Bas + (int64_t)bas_block * r * ldb + row0;
+    const TR* R0 = R + row0;
+    for (int64_t i = lane; i < rpw; i += 32) {
+      const TA x = conv<TA>(R0[i]);
 #pragma unroll
-    for (int j = 0; j < RT; ++j)
-      if (j < r) acc[j] += conv<TA>(B0[(int64_t)j * ldb + i]) * x;
+      for (int j = 0; j < RT; ++j)
+        if (j < r) acc[j] += conv<TA>(B0[(int64_t)j * ldb + i]) * x;
+    }
   }
-  double* Pq = P + (size_t)q * r;
 #pragma unroll
   for (int g = 0; g < RT / 32; ++g) {
     TA v[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) v[j] = acc[g * 32 + j];
-    const TA t = warp_transpose_reduce32(v);
-    const int j = g * 32 + lane;
-    if (j < r) Pq[j] = (double)t;
+    sPart[warp][g * 32 + lane] = warp_transpose_reduce32(v);
   }
+  __syncthreads();
+  if (active && w == 0) {
+    double* Pq = P + (size_t)q * r;
+    for (int j = lane; j < r; j += 32) {
+      TA t = sPart[sub * wpc][j];
+      for (int ww = 1; ww < wpc; ++ww) t += sPart[sub * wpc + ww][j];
+      Pq[j] = (double)t;
+    }
+  }
+}
+
+// Vector variant of the one-column projection: lane l of a warp covers rows
+// 4l .. 4l+3 of each 128-row slab of its range (one 8- or 16-byte access per
+// rank column), then the same transposed butterfly and in-order warp sums.
+template <typename TB, typename TR, typename TA, int RT>
+__global__ void __launch_bounds__(256) project_k1v_kernel(int64_t N, int r, int c, const TB* __restrict__ Bas,
+                                                          int64_t ldb, int bas_block, const TR* __restrict__ R,
+                                                          double* __restrict__ P, int wpc) {
+  __shared__ TA sPart[8][RT];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int cpb = 8 / wpc;
+  const int sub = warp / wpc, w = warp % wpc;
+  const int64_t q = (int64_t)blockIdx.x * cpb + sub;
+  const bool active = q < num_chunks(N, c);
+  const int64_t ch = chunk_rows(N, c);
+  const int64_t rpw = ch / wpc;
+  const int64_t row0 = q * ch + w * rpw;
+  TA acc[RT];
+#pragma unroll
+  for (int j = 0; j < RT; ++j) acc[j] = TA(0);
+  if (active) {
+    const TB* B0 = Bas + (int64_t)bas_block * r * ldb + row0 + 4 * lane;
+    const TR* R0 = R + row0 + 4 * lane;
+    for (int64_t i = 0; i < rpw; i += 128) {
+      TA x[4];
+      load4(R0 + i, x);
+#pragma unroll
+      for (int j = 0; j < RT; ++j)
+        if (j < r) {
+          TA b[4];
+          load4(B0 + (int64_t)j * ldb + i, b);
+          acc[j] += b[0] * x[0] + b[1] * x[1] + b[2] * x[2] + b[3] * x[3];
+        }
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < RT / 32; ++g) {
+    TA v[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = acc[g * 32 + j];
+    sPart[warp][g * 32 + lane] = warp_transpose_reduce32(v);
+  }
+  __syncthreads();
+  if (active && w == 0) {
+    double* Pq = P + (size_t)q * r;
+    for (int j = lane; j < r; j += 32) {
+      TA t = sPart[sub * wpc][j];
+      for (int ww = 1; ww < wpc; ++ww) t += sPart[sub * wpc + ww][j];
+      Pq[j] = (double)t;
+    }
+  }
+}
+
+int project_k1_warps(int64_t ch) {
+  int w = 1;
+  while (w < 8 && ch >= (int64_t)256 * w && ch % (2 * w) == 0) w *= 2;  // >= 128 rows per warp
+  return w;
 }
 
 template <typename TB, typename TR>
@@ -185,11 +259,19 @@ cudaError_t launch_project(int64_t N, int r, int c, const TB* Bas, int64_t ldb, 
   note_work(sizeof(TB) * (double)N * r + sizeof(TR) * (double)N * ncols + 8.0 * num_chunks(N, c) * r * ncols,
             2.0 * N * r * (double)ncols);
   if (ncols == 1 && r > 16) {
-    const unsigned g1 = (unsigned)((num_chunks(N, c) + 7) / 8);
-    if (r <= 32)
-      { project_k1_kernel<TB, TR, TA, 32><<<g1, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, P); note_launches(1); }
+    const int wpc = project_k1_warps(chunk_rows(N, c));
+    const int64_t cpb = 8 / wpc;
+    const unsigned g1 = (unsigned)((num_chunks(N, c) + cpb - 1) / cpb);
+    const bool vec = (chunk_rows(N, c) / wpc) % 128 == 0 && ldb % 4 == 0 &&
+                     reinterpret_cast<uintptr_t>(Bas) % 16 == 0 && reinterpret_cast<uintptr_t>(R) % 16 == 0;
+    if (vec && r <= 32)
+      { project_k1v_kernel<TB, TR, TA, 32><<<g1, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, P, wpc); note_launches(1); }
+    else if (vec)
+      { project_k1v_kernel<TB, TR, TA, 64><<<g1, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, P, wpc); note_launches(1); }
+    else if (r <= 32)
+      { project_k1_kernel<TB, TR, TA, 32><<<g1, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, P, wpc); note_launches(1); }
     else
-      { project_k1_kernel<TB, TR, TA, 64><<<g1, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, P); note_launches(1); }
+      { project_k1_kernel<TB, TR, TA, 64><<<g1, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, P, wpc); note_launches(1); }
     return cudaGetLastError();
   }
   if (ncols <= 8) {
@@ -322,6 +404,42 @@ __global__ void __launch_bounds__(256) update_skinny_kernel(int64_t N, int r, in
     }
 }
 
+// One right-hand side, rows in fours: thread t of a 1024-row tile (tiles laid
+// out node by node) updates rows 4t .. 4t+3 with vector loads of the basis
+// (one 8- or 16-byte access per rank column) and of x.
+template <typename TB, typename TR, typename TA>
+__global__ void __launch_bounds__(256) update_k1v_kernel(int64_t N, int r, int c, const TB* __restrict__ Bas,
+                                                         int64_t ldb, int bas_block, TR* __restrict__ R,
+                                                         const double* __restrict__ Wbase, int64_t wstride,
+                                                         int swap_sibling, double alpha) {
+  __shared__ TA sW[64];
+  const int64_t n = N >> c;
+  const int64_t tpn = (n + 1023) / 1024;
+  const int64_t node = blockIdx.x / tpn;
+  const int64_t t0 = (blockIdx.x % tpn) * 1024;
+  const double* W = Wbase + (node ^ swap_sibling) * wstride;
+  for (int j = threadIdx.x; j < r; j += 256) sW[j] = conv<TA>(alpha * W[j]);
+  __syncthreads();
+  const int64_t i = t0 + 4 * threadIdx.x;
+  if (i >= n) return;
+  const int64_t row = node * n + i;
+  const TB* B0 = Bas + (int64_t)bas_block * r * ldb + row;
+  TA acc[4] = {TA(0), TA(0), TA(0), TA(0)};
+#pragma unroll 8
+  for (int j = 0; j < r; ++j) {
+    TA b[4];
+    load4(B0 + (int64_t)j * ldb, b);
+    const TA w = sW[j];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] += b[q] * w;
+  }
+  TA x[4];
+  load4(R + row, x);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) x[q] += acc[q];
+  store4(R + row, x);
+}
+
 template <typename TB, typename TR>
 cudaError_t launch_update(int64_t N, int r, int c, const TB* Bas, int64_t ldb, int bas_block, TR* R, int64_t ldr,
                           int ncols, const double* Wbase, int64_t wstride, int swap_sibling, double alpha,
@@ -337,7 +455,13 @@ cudaError_t launch_update(int64_t N, int r, int c, const TB* Bas, int64_t ldb, i
     using TA2 = typename AccOf<TR>::type;
     const int64_t tpn2 = (n + 255) / 256;
     const unsigned g2 = (unsigned)(((int64_t)1 << c) * tpn2);
-    if (ncols == 1)
+    const bool vec1 = ncols == 1 && n % 4 == 0 && ldb % 4 == 0 &&
+                      reinterpret_cast<uintptr_t>(Bas) % 16 == 0 && reinterpret_cast<uintptr_t>(R) % 16 == 0;
+    if (vec1) {
+      const int64_t tpn4 = (n + 1023) / 1024;
+      const unsigned g4 = (unsigned)(((int64_t)1 << c) * tpn4);
+      { update_k1v_kernel<TB, TR, TA2><<<g4, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, Wbase, wstride, swap_sibling, alpha); note_launches(1); }
+    } else if (ncols == 1)
       { update_skinny_kernel<TB, TR, TA2, 1><<<g2, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, ldr, ncols, Wbase, wstride, swap_sibling, alpha); note_launches(1); }
     else if (ncols <= 2)
       { update_skinny_kernel<TB, TR, TA2, 2><<<g2, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, ldr, ncols, Wbase, wstride, swap_sibling, alpha); note_launches(1); }
@@ -611,6 +735,7 @@ __global__ void __launch_bounds__(256) coupling_solve_skinny_kernel(int64_t N, i
   for (int cc = 0; cc < KC; ++cc) acc[cc] = 0.0;
   if (active) {
     const double* Kj = Kinv + (size_t)j * n * n;
+#pragma unroll 16
     for (int jj = 0; jj < n; ++jj) {
       const double kv = trans ? Kj[(size_t)i * n + jj] : Kj[(size_t)jj * n + i];
 #pragma unroll

@@ -53,6 +53,47 @@ __global__ void __launch_bounds__(128) mv1_leaf_project_kernel(int m, int rL, co
   }
 }
 
+// 1 (m = 128, 16-byte aligned V and x, even ldv). One warp per (leaf b, 16
+// basis columns): lane l covers rows 4l .. 4l+3 of the leaf (two 16-byte
+// loads per column, fully coalesced), then a transposed butterfly over the
+// lane bits 3..0 and one exchange across bit 4 leave column l % 16's total in
+// lanes l and l + 16.
+__global__ void __launch_bounds__(256) mv1_leaf_project16_kernel(int rL, int ngroups, int64_t nleaf,
+                                                                 const double* __restrict__ V, int64_t ldv,
+                                                                 const double* __restrict__ x,
+                                                                 double* __restrict__ pleaf) {
+  const int lane = threadIdx.x & 31;
+  const int64_t item = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (item >= nleaf * ngroups) return;  // whole warp
+  const int64_t b = item / ngroups;
+  const int c0 = (int)(item % ngroups) * 16;
+  const int64_t row = b * 128 + 4 * lane;
+  double xv[4];
+  load4(x + row, xv);
+  double v[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    v[j] = 0.0;
+    if (c0 + j < rL) {
+      double a[4];
+      load4(V + (int64_t)(c0 + j) * ldv + row, a);
+      v[j] = fma(a[3], xv[3], fma(a[2], xv[2], fma(a[1], xv[1], a[0] * xv[0])));
+    }
+  }
+#pragma unroll
+  for (int s = 8; s >= 1; s >>= 1) {
+    const bool upper = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const double send = upper ? v[i] : v[i + s];
+      const double keep = upper ? v[i + s] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  const double t = v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
+  if (lane < 16 && c0 + lane < rL) pleaf[(size_t)b * rL + c0 + lane] = t;
+}
+
 // 2a. Partial sums over runs of at most 64 consecutive leaves (never across
 // a node boundary), all levels in one launch: one CTA of r threads per
 // (level c, run), runs numbered level by level; thread j sums column
@@ -146,9 +187,17 @@ cudaError_t launch_matvec1(const hodlr_desc& d, const double* D, const double* U
   double* S = scratch + (size_t)nleaf * rL;
   double* runs = S + ((size_t)2 << L) * r;
   {
-    ProfScope prof_(KC_PROJECT, s);
+    ProfScope prof_(KC_MATVEC, s);
     note_work(8.0 * ((double)d.N * rL + d.N + nleaf * rL), 2.0 * d.N * rL);
-    { mv1_leaf_project_kernel<<<(unsigned)nleaf, 128, 0, s>>>(m, rL, V, d.ldv, x, pleaf); note_launches(1); }
+    const bool vec16 = m == 128 && ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(x)) % 16 == 0) &&
+                       d.ldv % 2 == 0;
+    if (vec16) {
+      const int ngroups = (rL + 15) / 16;
+      const int64_t warps = nleaf * ngroups;
+      { mv1_leaf_project16_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(rL, ngroups, nleaf, V, d.ldv, x, pleaf); note_launches(1); }
+    } else {
+      { mv1_leaf_project_kernel<<<(unsigned)nleaf, 128, 0, s>>>(m, rL, V, d.ldv, x, pleaf); note_launches(1); }
+    }
   }
   {
     ProfScope prof_(KC_REDUCE, s);
@@ -159,7 +208,7 @@ cudaError_t launch_matvec1(const hodlr_desc& d, const double* D, const double* U
     { mv1_node_sum_kernel<<<(unsigned)pairs, th, 0, s>>>(L, r, runs, S); note_launches(1); }
   }
   {
-    ProfScope prof_(KC_LEAF_MATVEC, s);
+    ProfScope prof_(KC_MATVEC, s);
     note_work(8.0 * ((double)d.N * m + (double)d.N * rL + 2.0 * d.N), 2.0 * d.N * (m + rL));
     const size_t sm = (size_t)(rL + m) * sizeof(double);
     const int th = m >= 256 ? 256 : ((m + 31) / 32) * 32;

@@ -1,6 +1,8 @@
 // Column-vector kernels for the solves and the refined solvers: copies with
 // precision change, axpby, and deterministic FP64 dot products (fixed-order
 // two-stage reductions, so results do not depend on scheduling).
+#include <type_traits>
+
 #include "hodlr_internal.cuh"
 
 namespace hodlr {
@@ -18,11 +20,40 @@ static unsigned grid_for(int64_t N) {
   return (unsigned)(b < 4096 ? b : 4096);
 }
 
+// FP64 -> BF16 column copy, eight elements per thread: four 16-byte loads,
+// one 16-byte store (N, lds, ldd multiples of 8; 16-byte aligned bases).
+__global__ void copy_cols_bf16_vec_kernel(int64_t N, int k, const double* __restrict__ src, int64_t lds,
+                                          __nv_bfloat16* __restrict__ dst, int64_t ldd) {
+  const int64_t per_col = N / 8;
+  const int64_t total = per_col * k;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / per_col, i = (e % per_col) * 8;
+    const double2* p = reinterpret_cast<const double2*>(src + j * lds + i);
+    const double2 a = p[0], b = p[1], c = p[2], d = p[3];
+    auto pack = [](double x, double y) {
+      return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)x)) |
+             ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)y)) << 16);
+    };
+    *reinterpret_cast<uint4*>(dst + j * ldd + i) = make_uint4(pack(a.x, a.y), pack(b.x, b.y), pack(c.x, c.y),
+                                                              pack(d.x, d.y));
+  }
+}
+
 template <typename TD, typename TS>
 cudaError_t launch_copy_cols(int64_t N, int k, const TS* src, int64_t lds, TD* dst, int64_t ldd, cudaStream_t s) {
   ProfScope prof_(KC_VECTOR, s);
   if (k <= 0) return cudaSuccess;
   note_work((sizeof(TS) + sizeof(TD)) * (double)N * k, 0.0);
+  if constexpr (std::is_same<TD, __nv_bfloat16>::value && std::is_same<TS, double>::value) {
+    if (N % 8 == 0 && lds % 8 == 0 && ldd % 8 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0 &&
+        reinterpret_cast<uintptr_t>(dst) % 16 == 0) {
+      const int64_t total = N / 8 * k;
+      int64_t grid = (total + 255) / 256;
+      if (grid > 152 * 32) grid = 152 * 32;
+      { copy_cols_bf16_vec_kernel<<<(unsigned)grid, 256, 0, s>>>(N, k, src, lds, dst, ldd); note_launches(1); }
+      return cudaGetLastError();
+    }
+  }
   { copy_cols_kernel<TD, TS><<<dim3(grid_for(N), k), 256, 0, s>>>(N, k, src, lds, dst, ldd); note_launches(1); }
   return cudaGetLastError();
 }
