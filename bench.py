@@ -92,7 +92,7 @@ def class_bound(cls, prec):
     if prec == "fp64":
         return "alu64"
     if cls == "coupling":
-        return "alu32" if prec == "bf16" else "alu64"
+        return "alu64"
     if cls == "leaf_lu":
         return "alu32"
     if prec == "fp32" and cls in ("leaf_solve", "project", "update", "coupling_apply"):
@@ -335,7 +335,7 @@ def run_native(args, w, rank, world):
         "data": "synthetic",
         "config": {"workload": args.workload, "description": w["desc"], "N": N, "leaf": m, "levels": L, "rank": r,
                    "rhs": k, "factor_precision": prec,
-                   "coupling_precision": "fp32" if (prec == "bf16" and r <= 32) else "fp64",
+                   "coupling_precision": "fp64",
                    "residual_precision": "fp64", "solver": w["solver"], "tol": 1e-10,
                    "flops_per_step": flops, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (D, U, V = %.1f GB FP64)" % (8.0 * (m * N + 2 * r * N * L) / 1e9)},

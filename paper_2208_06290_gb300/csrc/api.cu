@@ -92,7 +92,7 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t status, ld_out, leaf_ld, node_ld, lu, perm, Y, Vp, K, P, rhs16, total;
+  size_t status, ld_out, leaf_ld, node_ld, lu, perm, Y, Vp, K, P, rhs16, kf32, total;
 };
 
 size_t panel_elem_bytes(hodlr_prec p) {
@@ -139,6 +139,7 @@ Layout factor_layout(const hodlr_desc& d, hodlr_prec prec) {
     l.P = take(pb > tcb ? pb : tcb);
   }
   l.rhs16 = prec == HODLR_PREC_BF16 ? take(rhs_bf16_bytes(d)) : 0;
+  l.kf32 = prec == HODLR_PREC_BF16 ? take(kf32_bytes(d)) : 0;
   l.total = off;
   return l;
 }
@@ -217,14 +218,18 @@ hodlr_status solve_core(const Factor& F, TX* x, int64_t ldx, int k, double* Ps, 
     HODLR_CUDA((launch_leaf_solve<TX, TX>(F, x, ldx, x, ldx, k, 0, s)));
     for (int c = d.L; c >= 1; --c) {
       HODLR_CUDA((launch_project<TP, TX>(d.N, d.r, c, Vp, F.ldvp, c - 1, x, ldx, k, Ps, 0, s)));
-      HODLR_CUDA(launch_coupling_solve(F, c, Ps, k, 0, s));
+      const bool red = chunks_per_node(d.N, c) >= 8;  // many partials per node: sum them in parallel first
+      if (red) HODLR_CUDA(launch_reduce_chunks(d.N, d.r, c, Ps, k, s));
+      HODLR_CUDA(launch_coupling_solve(F, c, Ps, k, 0, s, red));
       const int64_t wstride = chunks_per_node(d.N, c) * (int64_t)d.r * k;
       HODLR_CUDA((launch_update<TP, TX>(d.N, d.r, c, Y, d.N, c - 1, x, ldx, k, Ps, wstride, 0, -1.0, 0, s)));
     }
   } else {
     for (int c = 1; c <= d.L; ++c) {
       HODLR_CUDA((launch_project<TP, TX>(d.N, d.r, c, Y, d.N, c - 1, x, ldx, k, Ps, 0, s)));
-      HODLR_CUDA(launch_coupling_solve(F, c, Ps, k, 1, s));
+      const bool red = chunks_per_node(d.N, c) >= 8;
+      if (red) HODLR_CUDA(launch_reduce_chunks(d.N, d.r, c, Ps, k, s));
+      HODLR_CUDA(launch_coupling_solve(F, c, Ps, k, 1, s, red));
       const int64_t wstride = chunks_per_node(d.N, c) * (int64_t)d.r * k;
       HODLR_CUDA((launch_update<TP, TX>(d.N, d.r, c, Vp, F.ldvp, c - 1, x, ldx, k, Ps, wstride, 1, -1.0, 0, s)));
     }
@@ -354,6 +359,7 @@ hodlr_status hodlr_factor(const hodlr_desc* desc, const double* D, const double*
   F->P = reinterpret_cast<double*>(w + lay.P);
   F->P_elems = max_partial_elems(d, 1, 0);
   F->rhs16 = prec == HODLR_PREC_BF16 ? reinterpret_cast<uint8_t*>(w + lay.rhs16) : nullptr;
+  F->kf32 = prec == HODLR_PREC_BF16 ? reinterpret_cast<float*>(w + lay.kf32) : nullptr;
   for (int c = 0; c < 26; ++c) F->Koff[c] = 0;
   for (int c = 1; c <= d.L; ++c) F->Koff[c] = ((int64_t)1 << (c - 1)) - 1;
   if (prec == HODLR_PREC_FP64) {
@@ -471,7 +477,7 @@ hodlr_status hodlr_matvec(const hodlr_desc* desc, const double* D, const double*
 namespace {
 
 struct RefineLayout {
-  size_t R, solve, mv, dots, scal, V, Z, w, total;
+  size_t R, solve, mv, dots, scal, V, Z, W, w, total;
 };
 
 RefineLayout refine_layout(const Factor& F, int k, int restart) {
@@ -488,6 +494,7 @@ RefineLayout refine_layout(const Factor& F, int k, int restart) {
   if (restart > 0) {
     l.V = take(N * (restart + 1) * sizeof(double));
     l.Z = take(N * restart * sizeof(double));
+    l.W = take(N * restart * sizeof(double));  // A z_i before orthogonalisation
     l.w = take(N * sizeof(double));
   }
   l.total = off;
@@ -579,6 +586,7 @@ hodlr_status hodlr_gmres(hodlr_factor_t f, const double* D, const double* U, con
   double* dev_h = reinterpret_cast<double*>(w + lay.scal);
   double* Vk = reinterpret_cast<double*>(w + lay.V);
   double* Zk = reinterpret_cast<double*>(w + lay.Z);
+  double* Wk = reinterpret_cast<double*>(w + lay.W);
   double* wv = reinterpret_cast<double*>(w + lay.w);
   const hodlr_desc& d = f->d;
   const int64_t N = d.N;
@@ -597,10 +605,12 @@ hodlr_status hodlr_gmres(hodlr_factor_t f, const double* D, const double* U, con
     if ((st = solve_any(*f, x, N, 1, sw, 0, s)) != HODLR_OK) return st;
     int col_it = 0;
     double rel = INFINITY;
+    // residual r = b - A x of the initial guess (FP64 matvec); after each
+    // cycle r = r - A Z y from the stored FP64 products A z_i, which is
+    // b - A x of the updated x without another matvec
+    if ((st = matvec_core(d, D, U, V, x, N, r, N, 1, mw, s, matvec_ws_bytes(d, 1))) != HODLR_OK) return st;
+    HODLR_CUDA(launch_axpby_cols(N, 1, 1.0, b, N, -1.0, r, N, s));
     for (;;) {
-      // true residual r = b - A x
-      if ((st = matvec_core(d, D, U, V, x, N, r, N, 1, mw, s, matvec_ws_bytes(d, 1))) != HODLR_OK) return st;
-      HODLR_CUDA(launch_axpby_cols(N, 1, 1.0, b, N, -1.0, r, N, s));
       double beta2 = 0.0;
       if ((st = col_norms2(N, 1, r, N, dev_h, scratch, &beta2, s)) != HODLR_OK) return st;
       const double beta = std::sqrt(beta2);
@@ -616,6 +626,7 @@ hodlr_status hodlr_gmres(hodlr_factor_t f, const double* D, const double* U, con
         HODLR_CUDA(launch_copy_cols<double, double>(N, 1, vi, N, zi, N, s));
         if ((st = solve_any(*f, zi, N, 1, sw, 0, s)) != HODLR_OK) return st;  // z_i = M^{-1} v_i
         if ((st = matvec_core(d, D, U, V, zi, N, wv, N, 1, mw, s, matvec_ws_bytes(d, 1))) != HODLR_OK) return st;  // w = A z_i
+        HODLR_CUDA(launch_copy_cols<double, double>(N, 1, wv, N, Wk + (int64_t)i * N, N, s));
         // classical Gram-Schmidt, twice
         for (int pass = 0; pass < 2; ++pass) {
           HODLR_CUDA(launch_multidot(N, i + 1, Vk, N, wv, dev_h, scratch, s));
@@ -657,6 +668,9 @@ hodlr_status hodlr_gmres(hodlr_factor_t f, const double* D, const double* U, con
       for (int q = 0; q < nsteps; ++q) h[q] = -y[q];
       HODLR_CUDA(cudaMemcpyAsync(dev_h, h.data(), (size_t)nsteps * sizeof(double), cudaMemcpyHostToDevice, s));
       HODLR_CUDA(launch_gemv_sub(N, nsteps, Zk, N, dev_h, x, s));  // x -= Z(-y)
+      for (int q = 0; q < nsteps; ++q) h[q] = y[q];
+      HODLR_CUDA(cudaMemcpyAsync(dev_h, h.data(), (size_t)nsteps * sizeof(double), cudaMemcpyHostToDevice, s));
+      HODLR_CUDA(launch_gemv_sub(N, nsteps, Wk, N, dev_h, r, s));  // r -= (A Z) y
       HODLR_CUDA(cudaStreamSynchronize(s));
     }
     total_it += col_it;

@@ -1,15 +1,16 @@
-// Coupling matrices of the BF16 factor: one warp per parent, FP32
-// arithmetic, r <= 32 (the FP32 and FP64 factors keep the FP64 CTA kernel).
+// Coupling matrices, one warp per parent, r <= 32. S = I - T_a T_b, its
+// Gauss-Jordan inverse and log|det S| are FP64 in every factor (the coupling
+// "LU"); the products of the explicit inverse (S^{-1} T_a, T_b S^{-1} T_a,
+// T_b S^{-1}) are FP64 for the FP64 and FP32 factors and FP32 (from the FP64
+// pieces) for the BF16 factor, whose panels are BF16.
 //
-// Same quantities as the FP64 CTA kernel (level.cu): with
+// Same quantities as the CTA kernel of level.cu (used for r > 32): with
 // K~ = [[I, T_b], [T_a, I]] (Eq. e:k) and the Schur complement
 // S = I - T_a T_b,
 //   K~^{-1} = [[I + T_b S^{-1} T_a, -T_b S^{-1}], [-S^{-1} T_a, S^{-1}]],
-//   det K~ = det S,
-// written in FP64 so that every consumer reads one layout. T_a and T_b are
-// products of BF16 panels, so FP32 here adds nothing to their error (the
-// paper's single-precision runs do every step in FP32), and FP32 runs at 64x
-// the FP64 rate of this GPU.
+//   det K~ = det S.
+// A CTA per parent spends most of its time in barriers at these sizes; a
+// warp per parent needs none.
 //
 // Lane i holds row i of S (padded to 32 x 32 with the identity) in registers.
 // Gauss-Jordan with partial pivoting runs without moving rows: at step k the
@@ -20,6 +21,8 @@
 // through shared memory. The pivots are LU's pivots of S with rows taken in
 // the order p_0, p_1, ..., so log|det S| = sum log|pivot| and the sign is the
 // parity of the negative pivots and of the inversions of (p_k).
+#include <type_traits>
+
 #include "hodlr_internal.cuh"
 
 namespace hodlr {
@@ -30,20 +33,22 @@ constexpr int kCwLd = 33;    // padded row stride of the per-warp 32 x 32 tiles
 constexpr unsigned kFull = 0xffffffffu;
 }  // namespace
 
+template <bool FULL>
 __global__ void __launch_bounds__(32 * kCwWarps) coupling_factor_warp_kernel(int64_t N, int r, int c,
                                                                               const double* __restrict__ P,
                                                                               int64_t cpn_read,
                                                                               double* __restrict__ Kinv,
                                                                               double* __restrict__ node_ld,
-                                                                              DevStatus* st, int64_t heap_first) {
-  extern __shared__ float cw_smem[];
+                                                                              DevStatus* st, int64_t heap_first,
+                                                                              float* __restrict__ Kf) {
+  extern __shared__ double cw_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t parents = (int64_t)1 << (c - 1);
   const int64_t j = (int64_t)blockIdx.x * kCwWarps + warp;
   if (j >= parents) return;  // whole warp; only warp-level synchronisation below
-  float* Ta = cw_smem + (size_t)warp * 3 * 32 * kCwLd;  // row-major, ld 33
-  float* Tb = Ta + 32 * kCwLd;
-  float* X = Tb + 32 * kCwLd;
+  double* Ta = cw_smem + (size_t)warp * 3 * 32 * kCwLd;  // row-major, ld 33
+  double* Tb = Ta + 32 * kCwLd;
+  double* X = Tb + 32 * kCwLd;
   const int64_t cpn = chunks_per_node(N, c);
   const size_t slot = (size_t)r * r * c;
   const int anc = r * (c - 1);
@@ -61,34 +66,34 @@ __global__ void __launch_bounds__(32 * kCwWarps) coupling_factor_warp_kernel(int
         b += pb[q * slot];
       }
     }
-    Ta[lane * kCwLd + col] = (float)a;
-    Tb[lane * kCwLd + col] = (float)b;
+    Ta[lane * kCwLd + col] = a;
+    Tb[lane * kCwLd + col] = b;
   }
   __syncwarp();
 
   // row `lane` of S = I - T_a T_b
-  float s[32];
+  double s[32];
 #pragma unroll
-  for (int q = 0; q < 32; ++q) s[q] = lane == q ? 1.f : 0.f;
+  for (int q = 0; q < 32; ++q) s[q] = lane == q ? 1.0 : 0.0;
   for (int t = 0; t < r; ++t) {
-    const float a = Ta[lane * kCwLd + t];
+    const double a = Ta[lane * kCwLd + t];
 #pragma unroll
-    for (int q = 0; q < 32; ++q) s[q] = fmaf(-a, Tb[t * kCwLd + q], s[q]);
+    for (int q = 0; q < 32; ++q) s[q] = fma(-a, Tb[t * kCwLd + q], s[q]);
   }
 
   bool used = false;
-  float mypiv = 1.f;  // lane k: the pivot of step k
+  double mypiv = 1.0;  // lane k: the pivot of step k
   int mypos = lane;   // lane k: the pivot row p_k
   int mystep = lane;  // lane i: the step that took row i as pivot
   int ninv = 0;       // lane k: #{k' > k : p_k' < p_k}
 #pragma unroll
   for (int k = 0; k < 32; ++k) {
-    float v = used ? -1.f : fabsf(s[k]);
-    if (v != v) v = __int_as_float(0x7f800000);  // NaN ranks first: a total order keeps the choice warp-uniform
+    double v = used ? -1.0 : fabs(s[k]);
+    if (v != v) v = __longlong_as_double(0x7ff0000000000000ll);  // NaN ranks first: a total order keeps the choice warp-uniform
     int idx = lane;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-      const float ov = __shfl_xor_sync(kFull, v, off);
+      const double ov = __shfl_xor_sync(kFull, v, off);
       const int oi = __shfl_xor_sync(kFull, idx, off);
       if (ov > v || (ov == v && oi < idx)) {
         v = ov;
@@ -96,8 +101,8 @@ __global__ void __launch_bounds__(32 * kCwWarps) coupling_factor_warp_kernel(int
       }
     }
     const int p = idx;  // an unused lane: at least one has v >= 0 > -1
-    const float piv = __shfl_sync(kFull, s[k], p);
-    const float rp = piv != 0.f ? 1.f / piv : 0.f;
+    const double piv = __shfl_sync(kFull, s[k], p);
+    const double rp = piv != 0.0 ? 1.0 / piv : 0.0;
     if (lane < k) ninv += p < mypos ? 1 : 0;
     if (lane == k) {
       mypiv = piv;
@@ -108,48 +113,77 @@ __global__ void __launch_bounds__(32 * kCwWarps) coupling_factor_warp_kernel(int
       used = true;
       mystep = k;
     }
-    const float f = s[k];
+    // row p: s_pq / pivot; other rows: s_iq - (s_ik / pivot) s_pq; column k:
+    // 1 / pivot on row p, -s_ik / pivot elsewhere (one FMA per entry)
+    const double coef = isp ? rp : -s[k] * rp;
 #pragma unroll
     for (int q = 0; q < 32; ++q) {
       if (q == k) continue;
-      const float w = __shfl_sync(kFull, s[q], p) * rp;
-      s[q] = isp ? w : fmaf(-f, w, s[q]);
+      const double pv = __shfl_sync(kFull, s[q], p);
+      s[q] = fma(coef, pv, isp ? 0.0 : s[q]);
     }
-    s[k] = isp ? rp : -f * rp;
+    s[k] = coef;
   }
 
   // log|det S| (FP64, fixed butterfly), sign, first zero pivot
-  double la = lane < r ? log(fabs((double)mypiv)) : 0.0;
-  int neg = ((lane < r && mypiv < 0.f) ? 1 : 0) ^ (ninv & 1);
+  double la = lane < r ? log(fabs(mypiv)) : 0.0;
+  int neg = ((lane < r && mypiv < 0.0) ? 1 : 0) ^ (ninv & 1);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     la += __shfl_xor_sync(kFull, la, off);
     neg ^= __shfl_xor_sync(kFull, neg, off);
   }
-  const unsigned zero = __ballot_sync(kFull, lane < r && mypiv == 0.f);
+  const unsigned zero = __ballot_sync(kFull, lane < r && mypiv == 0.0);
   const int sing = zero ? __ffs(zero) - 1 : -1;
 
   // S^{-1}(k, i) = tableau(p_k, step of row i)
 #pragma unroll
   for (int q = 0; q < 32; ++q) X[lane * kCwLd + q] = s[q];
   __syncwarp();
-  float sv[32];
+  double sv[32];
 #pragma unroll
   for (int i = 0; i < 32; ++i) sv[i] = X[mypos * kCwLd + __shfl_sync(kFull, mystep, i)];
 
+  __syncwarp();
+  // Products of the explicit inverse in TPR (FP64 when FULL, else FP32 from
+  // the FP64 S^{-1}, T_a, T_b): FP32 copies of T_a and S^{-1} go to the
+  // tableau's area, which the gather above has finished reading.
+  using TPR = typename std::conditional<FULL, double, float>::type;
+  TPR* TaP;
+  TPR* SiP;
+  TPR* M1P;
+  if constexpr (FULL) {
+    TaP = Ta;
+    SiP = Ta;  // overwritten with S^{-1} once M1 is formed
+    M1P = X;
+  } else {
+    float* XF = reinterpret_cast<float*>(X);
+    TaP = XF;               // [32][33]
+    SiP = XF + 32 * kCwLd;  // [32][33]
+    M1P = XF;               // overwrites the T_a copy once M1 is formed
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      XF[lane * kCwLd + q] = (float)Ta[lane * kCwLd + q];
+      SiP[lane * kCwLd + q] = (float)sv[q];
+    }
+    __syncwarp();
+  }
+
   // M1 = S^{-1} T_a (row `lane`)
-  float m1[32];
+  TPR m1[32];
 #pragma unroll
-  for (int q = 0; q < 32; ++q) m1[q] = 0.f;
+  for (int q = 0; q < 32; ++q) m1[q] = TPR(0);
 #pragma unroll
-  for (int i = 0; i < 32; ++i)
+  for (int i = 0; i < 32; ++i) {
+    const TPR si = (TPR)sv[i];
 #pragma unroll
-    for (int q = 0; q < 32; ++q) m1[q] = fmaf(sv[i], Ta[i * kCwLd + q], m1[q]);
+    for (int q = 0; q < 32; ++q) m1[q] = fma(si, TaP[i * kCwLd + q], m1[q]);
+  }
   __syncwarp();
 #pragma unroll
   for (int q = 0; q < 32; ++q) {
-    Ta[lane * kCwLd + q] = sv[q];  // S^{-1}
-    X[lane * kCwLd + q] = m1[q];   // M1
+    if constexpr (FULL) Ta[lane * kCwLd + q] = sv[q];  // S^{-1}
+    M1P[lane * kCwLd + q] = m1[q];
   }
   __syncwarp();
 
@@ -161,22 +195,37 @@ __global__ void __launch_bounds__(32 * kCwWarps) coupling_factor_warp_kernel(int
   for (int q = 0; q < 32; ++q) {
     if (row_ok && q < r) {
       out[(size_t)q * n + r + lane] = -(double)m1[q];
-      out[(size_t)(r + q) * n + r + lane] = (double)sv[q];
+      out[(size_t)(r + q) * n + r + lane] = sv[q];
+    }
+  }
+  // r = 32 and Kf given: the rows of K~^{-1} facing each child in FP32, rows
+  // padded to 2r + 4 (the layout the fused tensor-core update stages): row
+  // `lane` of the second child is [-M1 | S^{-1}], of the first (below)
+  // [I + T_b M1 | -T_b S^{-1}]
+  constexpr int kKfLd = 2 * 32 + 4;
+  if (Kf) {
+    float4* k1 = reinterpret_cast<float4*>(Kf + ((size_t)(2 * j + 1) * 32 + lane) * kKfLd);
+#pragma unroll
+    for (int q4 = 0; q4 < 8; ++q4) {
+      k1[q4] = make_float4((float)-m1[4 * q4], (float)-m1[4 * q4 + 1], (float)-m1[4 * q4 + 2],
+                           (float)-m1[4 * q4 + 3]);
+      k1[8 + q4] = make_float4((float)sv[4 * q4], (float)sv[4 * q4 + 1], (float)sv[4 * q4 + 2],
+                               (float)sv[4 * q4 + 3]);
     }
   }
   // [11] = I + T_b M1, [12] = -T_b S^{-1}
-  float a11[32], a12[32];
+  TPR a11[32], a12[32];
 #pragma unroll
   for (int q = 0; q < 32; ++q) {
-    a11[q] = 0.f;
-    a12[q] = 0.f;
+    a11[q] = TPR(0);
+    a12[q] = TPR(0);
   }
   for (int t = 0; t < r; ++t) {
-    const float tb = Tb[lane * kCwLd + t];
+    const TPR tb = (TPR)Tb[lane * kCwLd + t];
 #pragma unroll
     for (int q = 0; q < 32; ++q) {
-      a11[q] = fmaf(tb, X[t * kCwLd + q], a11[q]);
-      a12[q] = fmaf(tb, Ta[t * kCwLd + q], a12[q]);
+      a11[q] = fma(tb, M1P[t * kCwLd + q], a11[q]);
+      a12[q] = fma(tb, SiP[t * kCwLd + q], a12[q]);
     }
   }
 #pragma unroll
@@ -186,6 +235,18 @@ __global__ void __launch_bounds__(32 * kCwWarps) coupling_factor_warp_kernel(int
       out[(size_t)(r + q) * n + lane] = -(double)a12[q];
     }
   }
+  if (Kf) {
+    float4* k0 = reinterpret_cast<float4*>(Kf + ((size_t)(2 * j) * 32 + lane) * kKfLd);
+#pragma unroll
+    for (int q4 = 0; q4 < 8; ++q4) {
+      float e[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) e[u] = (float)a11[4 * q4 + u] + (4 * q4 + u == lane ? 1.f : 0.f);
+      k0[q4] = make_float4(e[0], e[1], e[2], e[3]);
+      k0[8 + q4] = make_float4((float)-a12[4 * q4], (float)-a12[4 * q4 + 1], (float)-a12[4 * q4 + 2],
+                               (float)-a12[4 * q4 + 3]);
+    }
+  }
   if (lane == 0) {
     node_ld[2 * j] = la;
     node_ld[2 * j + 1] = sing >= 0 ? 0.0 : (neg ? -1.0 : 1.0);
@@ -193,19 +254,31 @@ __global__ void __launch_bounds__(32 * kCwWarps) coupling_factor_warp_kernel(int
   }
 }
 
-bool coupling_warp_supported(const Factor& F) { return F.prec == HODLR_PREC_BF16 && F.d.r <= 32; }
+bool coupling_warp_supported(const Factor& F) { return F.d.r <= 32; }
+
+bool coupling_writes_kf32(const Factor& F, int c) {
+  return F.prec == HODLR_PREC_BF16 && F.d.r == 32 && F.kf32 != nullptr && g_use_tc &&
+         update_tc_supported(F.d.N, F.d.r, c);
+}
 
 cudaError_t launch_coupling_factor_warp(const Factor& F, int c, cudaStream_t s) {
   const int r = F.d.r;
   const int n = 2 * r;
   const int64_t parents = (int64_t)1 << (c - 1);
-  const size_t sm = (size_t)kCwWarps * 3 * 32 * kCwLd * sizeof(float);
-  cudaFuncSetAttribute(coupling_factor_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const size_t sm = (size_t)kCwWarps * 3 * 32 * kCwLd * sizeof(double);
+  // FP64 and FP32 factors: the whole inverse in FP64; BF16 factor: S and its
+  // inverse in FP64, the products of the explicit inverse in FP32
+  const bool full = F.prec != HODLR_PREC_BF16;
+  if (full)
+    cudaFuncSetAttribute(coupling_factor_warp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  else
+    cudaFuncSetAttribute(coupling_factor_warp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   const int64_t grid = (parents + kCwWarps - 1) / kCwWarps;
   {
-    coupling_factor_warp_kernel<<<(unsigned)grid, 32 * kCwWarps, sm, s>>>(
+    auto kern = full ? coupling_factor_warp_kernel<true> : coupling_factor_warp_kernel<false>;
+    kern<<<(unsigned)grid, 32 * kCwWarps, sm, s>>>(
         F.d.N, r, c, F.P, F.P_reduced ? 1 : chunks_per_node(F.d.N, c), F.K + F.Koff[c] * n * n,
-        F.node_ld + 2 * F.Koff[c], F.status, parents);
+        F.node_ld + 2 * F.Koff[c], F.status, parents, coupling_writes_kf32(F, c) ? F.kf32 : nullptr);
     note_launches(1);
   }
   return cudaGetLastError();

@@ -133,6 +133,9 @@ struct Factor {
   // BF16 factor: per-parent right-hand sides [W_beta; W_alpha]^T of one level
   // in the tensor cores' operand layout (rhs_bf16_bytes)
   uint8_t* rhs16;
+  // BF16 factor: K~^{-1}(rows of alpha, :) in FP32 for every child of one
+  // level, rows padded to 2r + 4 (kf32_bytes)
+  float* kf32;
   // BF16 factor with m = 128: the leaf stage runs on the tensor cores; the
   // leaf inverse then also writes D_b^{-1} in operand layout into P (P is
   // free until the level loop starts)
@@ -197,10 +200,16 @@ cudaError_t launch_update(int64_t N, int r, int c, const TB* Bas, int64_t ldb, i
 // LU, log|det|, solve for the ancestor columns; W' written to each child's
 // first chunk slot. Solve modes reuse the stored LU.
 cudaError_t launch_coupling_factor(const Factor& F, int c, cudaStream_t s);
-// FP32 warp-per-parent variant for the BF16 factor (r <= 32)
+// FP64 warp-per-parent variant (r <= 32)
 bool coupling_warp_supported(const Factor& F);
 cudaError_t launch_coupling_factor_warp(const Factor& F, int c, cudaStream_t s);
-cudaError_t launch_coupling_solve(const Factor& F, int c, double* P, int k, int trans, cudaStream_t s);
+// true when the warp coupling kernel of level c also writes the FP32 rows
+// K~^{-1}(rows of alpha, :) the fused tensor-core update stages (F.kf32)
+bool coupling_writes_kf32(const Factor& F, int c);
+// reduced: the chunk partials of every node were already summed into its
+// first slot (launch_reduce_chunks)
+cudaError_t launch_coupling_solve(const Factor& F, int c, double* P, int k, int trans, cudaStream_t s,
+                                  bool reduced = false);
 // Sum the chunk partials of every node into the node's first chunk slot.
 cudaError_t launch_reduce_chunks(int64_t N, int r, int c, double* P, int ncols, cudaStream_t s);
 
@@ -257,6 +266,7 @@ cudaError_t launch_project_tc(int64_t N, int r, int L, int c, const __nv_bfloat1
 // and the BF16 right-hand-side staging area rhs16 (rhs_bf16_bytes).
 bool update_tc_supported(int64_t N, int r, int c);
 size_t rhs_bf16_bytes(const hodlr_desc& d);
+size_t kf32_bytes(const hodlr_desc& d);
 cudaError_t launch_update_coupled_tc(const Factor& F, int c, cudaStream_t s);
 // Tensor-core (kind::tf32) leaf stage Y = D_b^{-1} U of the BF16 factor
 // (m = 128, r L a multiple of 32; U 16-byte aligned with even ldu).

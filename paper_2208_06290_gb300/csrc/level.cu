@@ -705,7 +705,7 @@ cudaError_t launch_coupling_factor_apply(const Factor& F, int c, cudaStream_t s)
 template <int KC>
 __global__ void __launch_bounds__(256) coupling_solve_skinny_kernel(int64_t N, int r, int c, double* P, int k,
                                                                     const double* __restrict__ Kinv,
-                                                                    int first_is_beta, int trans) {
+                                                                    int first_is_beta, int trans, int64_t cpn_read) {
   __shared__ double sRhs[256 * KC];
   const int n = 2 * r;
   const int ppc = 256 / n;  // parents per CTA
@@ -725,7 +725,7 @@ __global__ void __launch_bounds__(256) coupling_solve_skinny_kernel(int64_t N, i
     for (int cc = 0; cc < KC; ++cc) {
       double acc = 0.0;
       if (cc < k)
-        for (int64_t q = 0; q < cpn; ++q) acc += P[(q0 + q) * slot + (size_t)cc * r + row];
+        for (int64_t q = 0; q < cpn_read; ++q) acc += P[(q0 + q) * slot + (size_t)cc * r + row];
       rhs[i * KC + cc] = acc;
     }
   }
@@ -753,28 +753,30 @@ __global__ void __launch_bounds__(256) coupling_solve_skinny_kernel(int64_t N, i
 
 template <int KC>
 static cudaError_t coupling_solve_skinny(int64_t N, int r, int c, double* P, int k, const double* Kinv,
-                                         int first_is_beta, int trans, cudaStream_t s) {
+                                         int first_is_beta, int trans, cudaStream_t s, int64_t cpn_read) {
   const int n = 2 * r;
   const int ppc = 256 / n;
   const int64_t parents = (int64_t)1 << (c - 1);
   const unsigned grid = (unsigned)((parents + ppc - 1) / ppc);
   note_work(8.0 * ((double)num_chunks(N, c) * r * k + parents * n * n + 2.0 * parents * r * k),
             parents * 2.0 * n * n * (double)k);
-  { coupling_solve_skinny_kernel<KC><<<grid, 256, 0, s>>>(N, r, c, P, k, Kinv, first_is_beta, trans); note_launches(1); }
+  { coupling_solve_skinny_kernel<KC><<<grid, 256, 0, s>>>(N, r, c, P, k, Kinv, first_is_beta, trans, cpn_read); note_launches(1); }
   return cudaGetLastError();
 }
 
 // Solve / adjoint: w = Kinv [s_beta; s_alpha] or t = Kinv^T [s_alpha; s_beta], FP64.
-cudaError_t launch_coupling_solve(const Factor& F, int c, double* P, int k, int trans, cudaStream_t s) {
+cudaError_t launch_coupling_solve(const Factor& F, int c, double* P, int k, int trans, cudaStream_t s,
+                                  bool reduced) {
   ProfScope prof_(KC_COUPLING_APPLY, s);
   const int r = F.d.r;
   const double* Kc = F.K + F.Koff[c] * 4 * r * r;
   const int fib = trans ? 0 : 1;
-  if (k == 1) return coupling_solve_skinny<1>(F.d.N, r, c, P, k, Kc, fib, trans, s);
-  if (k <= 2) return coupling_solve_skinny<2>(F.d.N, r, c, P, k, Kc, fib, trans, s);
-  if (k <= 4) return coupling_solve_skinny<4>(F.d.N, r, c, P, k, Kc, fib, trans, s);
-  if (k <= 8) return coupling_solve_skinny<8>(F.d.N, r, c, P, k, Kc, fib, trans, s);
-  return coupling_apply<double>(F.d.N, r, c, P, k, k, Kc, fib, trans, s);
+  const int64_t cr = reduced ? 1 : chunks_per_node(F.d.N, c);
+  if (k == 1) return coupling_solve_skinny<1>(F.d.N, r, c, P, k, Kc, fib, trans, s, cr);
+  if (k <= 2) return coupling_solve_skinny<2>(F.d.N, r, c, P, k, Kc, fib, trans, s, cr);
+  if (k <= 4) return coupling_solve_skinny<4>(F.d.N, r, c, P, k, Kc, fib, trans, s, cr);
+  if (k <= 8) return coupling_solve_skinny<8>(F.d.N, r, c, P, k, Kc, fib, trans, s, cr);
+  return coupling_apply<double>(F.d.N, r, c, P, k, k, Kc, fib, trans, s, cr);
 }
 
 // ---------------------------------------------------------------------------

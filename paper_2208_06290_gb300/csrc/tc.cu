@@ -231,29 +231,17 @@ cudaError_t launch_project_tc(int64_t N, int r, int L, int c, const __nv_bfloat1
 // (8-row x 16-byte cores, LBO = 128 B between cores along K, SBO = 2r/8 * 128 B
 // between 8-row groups), one contiguous block per kFuNC ancestor columns, so
 // that one bulk copy stages it.
-// Step 2 (update_coupled_tc_kernel): per 128-row tile of a node, TMA brings the
-// own block Y_own (128 x r); Z = Y_own K~^{-1}(alpha rows, :) (128 x 2r) is
-// formed on the CUDA cores in FP32 and rounded to BF16 into the A layout; per
-// chunk of kFuNC ancestor columns a bulk copy brings Rhs^T and TMA the old Y
-// tile, one tcgen05.mma kind::f16 chain (K = 2r) accumulates Z Rhs in TMEM,
-// and the epilogue subtracts it from the staged tile, which TMA stores back.
+// Step 2 (update_coupled_tc_kernel): per 128-row tile of a node, the own block
+// Y_own (128 x r) and K~^{-1}(rows of alpha, :) (FP32, staged per child by
+// kf32_kernel) give Z = Y_own K~^{-1}(alpha rows, :) (128 x 2r), formed on the
+// CUDA cores and rounded to BF16 into the A layout; per chunk of kFuNC
+// ancestor columns one tcgen05.mma kind::f16 chain (K = 2r) accumulates
+// Z Rhs in TMEM, and the epilogue subtracts it from the old Y tile, staged and
+// stored by TMA. The roles and their pipeline are described at the kernel.
 namespace {
 
-constexpr int kFuNC = 128;   // ancestor columns per MMA chunk (N of the MMA)
+constexpr int kFuNC = 64;    // ancestor columns per MMA chunk (N of the MMA)
 constexpr int kFuBox = 32;   // columns per TMA box of Y (box = 128 rows x 32 columns)
-
-template <int RK>
-struct FusedSmem {
-  static constexpr int K2 = 2 * RK;
-  static constexpr uint32_t kABytes = 128 * K2 * 2;       // Z, K-major cores
-  static constexpr uint32_t kBBytes = kFuNC * K2 * 2;     // Rhs^T chunk
-  static constexpr int kKLd = K2 + 4;                     // padded row: 4-way instead of 32-way store conflicts
-  static constexpr uint32_t kKBytes = RK * kKLd * 4;      // K~^{-1}(alpha rows, :), FP32
-  static constexpr uint32_t kOwnBytes = 128 * RK * 2;     // Y_own tile [k][m]
-  static constexpr uint32_t kYBytes = 128 * kFuNC * 2;    // old / new Y tile [j][m]
-  static constexpr uint32_t kBarOff = kABytes + kBBytes + kKBytes + kOwnBytes + kYBytes;
-  static constexpr uint32_t kBytes = kBarOff + 64 + 128;  // 3 mbarriers + TMEM slot, + alignment slack
-};
 
 // Rhs^T of every parent of child level c into the B layout above. Thread per
 // 16-byte core row (8 consecutive K entries of one ancestor column); threads
@@ -328,36 +316,172 @@ bool make_map_plain(CUtensorMap* map, const void* base, int64_t rows, int64_t co
 
 }  // namespace
 
+// Pipelined, warp-specialized form of step 2 (320 threads, persistent over
+// 128-row tiles; every CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// and chunks of kFuNC ancestor columns inside each tile in the same order):
+//   warp 4, lane 0 (producer): TMA / bulk copies into double-buffered stages:
+//     per tile the own block Y_own (128 x r) and the FP32 rows
+//     K~^{-1}(rows of alpha, :) (precomputed per node, see kf32_kernel); per
+//     chunk the parent's Rhs^T chunk and the old Y tile;
+//   warps 0-3 (Z warps, thread per row): Z = Y_own K~^{-1}(alpha rows, :) in
+//     FP32, rounded to BF16 into the A operand;
+//   warp 5, lane 0 (MMA issuer): one tcgen05.mma chain (K = 2r) per chunk into
+//     one of two TMEM accumulators;
+//   warps 6-9 (epilogue, TMEM lane quarter = warp % 4): accumulator subtracted
+//     from the staged old Y tile, which one thread stores by TMA; the stage is
+//     handed back to the producer once the store has read it.
+// Hand-offs are mbarriers (full / empty pairs). Every wait is bounded and also
+// gives up when another thread has raised the CTA's abort flag; on the way out
+// thread 0 of each role lets its own copies and MMAs land (bounded) before the
+// TMEM is freed.
+namespace {
+
+// Rhs^T / old-Y stages and A (Z) buffers. Two stages and one A buffer keep
+// r = 32 at two CTAs per SM (99 KB of shared memory each), which measured
+// faster than four stages and a double-buffered A at one CTA per SM.
+template <int RK> constexpr int fu_stages() { return 2; }
+template <int RK> constexpr int fu_abufs() { return 1; }
+constexpr int kFuThreads = 320;  // 10 warps
+
 template <int RK>
-__global__ void __launch_bounds__(256, RK == 32 ? 2 : 1) update_coupled_tc_kernel(const __grid_constant__ CUtensorMap mapY, int64_t N,
-                                                                int c, const uint8_t* __restrict__ rhs,
-                                                                const double* __restrict__ Kinv, int anc,
-                                                                DevStatus* st) {
+struct FusedSmem {
+  static constexpr int K2 = 2 * RK;
+  static constexpr int kKLd = K2 + 4;                     // padded FP32 row of K~^{-1}(alpha rows, :)
+  static constexpr uint32_t kOwnBytes = 128 * RK * 2;     // Y_own tile [k][m]
+  static constexpr uint32_t kKfBytes = RK * kKLd * 4;
+  static constexpr uint32_t kABytes = 128 * K2 * 2;       // Z, K-major cores
+  static constexpr uint32_t kBBytes = kFuNC * K2 * 2;     // Rhs^T chunk
+  static constexpr uint32_t kYBytes = 128 * kFuNC * 2;    // old / new Y tile [j][m]
+  static constexpr int NS = fu_stages<RK>();
+  static constexpr int NA = fu_abufs<RK>();
+  static constexpr uint32_t kOwnOff = 0;
+  static constexpr uint32_t kKfOff = kOwnOff + 2 * kOwnBytes;
+  static constexpr uint32_t kAOff = kKfOff + 2 * kKfBytes;
+  static constexpr uint32_t kBOff = kAOff + NA * kABytes;
+  static constexpr uint32_t kYOff = kBOff + NS * kBBytes;
+  static constexpr uint32_t kBarOff = kYOff + NS * kYBytes;
+  static constexpr uint32_t kBytes = kBarOff + 256 + 128;  // barriers, TMEM slot, flag, + alignment slack
+  static_assert(8 * (12 + 3 * NS) + 16 <= 256, "barrier area");
+  static_assert(kBytes <= 227 * 1024, "shared memory per CTA");
+};
+
+// K~^{-1}(rows of alpha, :) in FP32 for every child alpha of level c,
+// rows padded to 2r + 4 floats (the layout the fused update stages).
+template <int RK>
+__global__ void kf32_kernel(int c, const double* __restrict__ Kinv, float* __restrict__ Kf) {
+  constexpr int K2 = 2 * RK, LD = K2 + 4;
+  const int64_t nodes = (int64_t)1 << c;
+  const int64_t total = nodes * RK * K2;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t node = e / (RK * K2);
+    const int w = (int)(e % (RK * K2));
+    const int q = w / RK, k = w % RK;  // k fastest: coalesced reads of a Kinv column
+    const double* Kj = Kinv + (size_t)(node >> 1) * K2 * K2;
+    const int rowoff = (node & 1) ? RK : 0;
+    Kf[(size_t)node * RK * LD + (size_t)k * LD + q] = (float)Kj[(size_t)q * K2 + rowoff + k];
+  }
+}
+
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  const uint32_t a = tc::smem_u32(bar);
+  const long long t0 = clock64();
+  for (uint32_t it = 0; it < tc::kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 15) == 15) {
+      if (*abort_flag) return false;
+      if (clock64() - t0 > tc::kSpinCycles) {
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+__device__ __forceinline__ void named_bar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// AND of pred over the `count` threads of named barrier `id` (all of them
+// take the same branch afterwards).
+__device__ __forceinline__ bool named_bar_and(int id, int count, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.cta.red.and.pred q, %2, %3, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "r"(count)
+      : "memory");
+  return r != 0;
+}
+
+// Lane 0 waits, the warp learns the outcome (warp-uniform).
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  int r = 1;
+  if ((threadIdx.x & 31) == 0) r = wait_or_abort(bar, parity, abort_flag) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, r, 0) != 0;
+}
+
+}  // namespace
+
+template <int RK>
+__global__ void __launch_bounds__(kFuThreads, RK == 32 ? 2 : 1) update_coupled_tc_kernel(const __grid_constant__ CUtensorMap mapY,
+                                                                          int64_t N, int c,
+                                                                          const uint8_t* __restrict__ rhs,
+                                                                          const float* __restrict__ Kf, int anc,
+                                                                          DevStatus* st) {
   using S = FusedSmem<RK>;
+  constexpr int NA = S::NA;
   constexpr int K2 = 2 * RK;
   constexpr uint32_t kSBO = (K2 / 8) * 128;
-  constexpr uint32_t kTmemCols = kFuNC;
+  constexpr uint32_t kTmemCols = 2 * kFuNC;  // two accumulators
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  uint8_t* sA = smem;
-  uint8_t* sB = sA + S::kABytes;
-  float* sK = reinterpret_cast<float*>(sB + S::kBBytes);
-  __nv_bfloat16* sOwn = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<uint8_t*>(sK) + S::kKBytes);
-  __nv_bfloat16* sY = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<uint8_t*>(sOwn) + S::kOwnBytes);
-  uint64_t* bar_own = reinterpret_cast<uint64_t*>(smem + S::kBarOff);
-  uint64_t* bar_ld = bar_own + 1;
-  uint64_t* bar_mma = bar_own + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_own + 3);
+  __nv_bfloat16* sOwn = reinterpret_cast<__nv_bfloat16*>(smem + S::kOwnOff);  // [2][RK][128]
+  float* sKf = reinterpret_cast<float*>(smem + S::kKfOff);                     // [2][RK][kKLd]
+  uint8_t* sA = smem + S::kAOff;                                               // [NA]
+  uint8_t* sB = smem + S::kBOff;                                               // [stages]
+  __nv_bfloat16* sY = reinterpret_cast<__nv_bfloat16*>(smem + S::kYOff);      // [stages][kFuNC][128]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::kBarOff);
+  uint64_t* own_full = bars;                        // [2]
+  uint64_t* own_empty = bars + 2;                   // [2]   count 128 (Z threads)
+  uint64_t* a_full = bars + 4;                      // [2]   count 128 (Z threads)
+  uint64_t* a_empty = bars + 6;                     // [2]   MMA commit
+  uint64_t* acc_full = bars + 8;                    // [2]   MMA commit
+  uint64_t* acc_empty = bars + 10;                  // [2]   count 128 (epilogue threads)
+  uint64_t* ld_full = bars + 12;                    // [stages]
+  uint64_t* b_empty = bars + 12 + S::NS;        // [stages] MMA commit
+  uint64_t* y_empty = bars + 12 + 2 * S::NS;    // [stages] epilogue storer
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 12 + 3 * S::NS);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 13 + 3 * S::NS);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
-    tc::mbar_init(bar_own, 1);
-    tc::mbar_init(bar_ld, 1);
-    tc::mbar_init(bar_mma, 1);
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&own_full[i], 1);
+      tc::mbar_init(&own_empty[i], 128);
+      tc::mbar_init(&a_full[i], 128);
+      tc::mbar_init(&a_empty[i], 1);
+      tc::mbar_init(&acc_full[i], 1);
+      tc::mbar_init(&acc_empty[i], 128);
+    }
+    for (int i = 0; i < S::NS; ++i) {
+      tc::mbar_init(&ld_full[i], 1);
+      tc::mbar_init(&b_empty[i], 1);
+      tc::mbar_init(&y_empty[i], 1);
+    }
+    *abort_flag = 0;
     tc::fence_mbar_init();
     tc::prefetch_tmap(&mapY);
   }
-  if (warp == 0) tc::tmem_alloc(tmem_slot, kTmemCols);
+  if (warp == 5) tc::tmem_alloc(tmem_slot, kTmemCols);
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
@@ -365,58 +489,127 @@ __global__ void __launch_bounds__(256, RK == 32 ? 2 : 1) update_coupled_tc_kerne
 
   const int64_t n = N >> c;
   const int64_t tiles = N / 128;
-  const int nchunks = (anc + kFuNC - 1) / kFuNC;
-  bool ok = true;
-  uint32_t ph_own = 0, ph_ld = 0, ph_mma = 0;
-  // copies / MMAs issued by thread 0 and not yet waited for (thread 0's view)
-  bool own_pending = false, ld_pending = false, mma_pending = false;
-  for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-    const int64_t row0 = t * 128;
-    const int64_t node = row0 / n;
-    const int64_t parent = node >> 1;
-    const int first = (node & 1) == 0;
-    const uint8_t* rhs_j = rhs + (size_t)parent * anc * K2 * 2;
-    if (tid == 0) {
-      // the previous tile's last store must have left sY before it is refilled
-      bulk_wait_read0();
-      tc::mbar_expect_tx(bar_own, S::kOwnBytes);
+  const int nch = (anc + kFuNC - 1) / kFuNC;
+
+  if (warp == 4) {
+    // ---------------------------------------------------------------- producer
+    // the whole warp walks the schedule and waits; lane 0 issues the copies
+    uint32_t g = 0, it = 0;
+    int pend_own = 0, pend_ld = 0;  // copies issued (the drain below waits for their landing)
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++it) {
+      const int64_t row0 = t * 128;
+      const int64_t node = row0 / n;
+      const int tb = it & 1;
+      if (it >= 2 && !(ok = warp_wait(&own_empty[tb], ((it >> 1) - 1) & 1, abort_flag))) break;
+      if (lane == 0) {
+        tc::mbar_expect_tx(&own_full[tb], S::kOwnBytes + S::kKfBytes);
 #pragma unroll
-      for (int b = 0; b < RK / kFuBox; ++b)
-        tc::tma_load_2d(sOwn + b * 128 * kFuBox, &mapY, (int32_t)row0, (c - 1) * RK + b * kFuBox, bar_own);
-      const int nc = anc < kFuNC ? anc : kFuNC;
-      tc::mbar_expect_tx(bar_ld, (uint32_t)nc * K2 * 2 + (uint32_t)nc * 128 * 2);
-      bulk_load_1d(sB, rhs_j, (uint32_t)nc * K2 * 2, bar_ld);
-      for (int b = 0; b < nc / kFuBox; ++b) tc::tma_load_2d(sY + b * 128 * kFuBox, &mapY, (int32_t)row0, b * kFuBox, bar_ld);
-      own_pending = ld_pending = true;
+        for (int b = 0; b < RK / kFuBox; ++b)
+          tc::tma_load_2d(sOwn + (size_t)tb * 128 * RK + b * 128 * kFuBox, &mapY, (int32_t)row0,
+                          (c - 1) * RK + b * kFuBox, &own_full[tb]);
+        bulk_load_1d(sKf + (size_t)tb * RK * S::kKLd, Kf + (size_t)node * RK * S::kKLd, S::kKfBytes,
+                     &own_full[tb]);
+      }
+      pend_own = it + 1;
+      const uint8_t* rhs_j = rhs + (size_t)(node >> 1) * anc * K2 * 2;
+      for (int ch = 0; ch < nch; ++ch, ++g) {
+        const int col0 = ch * kFuNC;
+        const int nc = (anc - col0) < kFuNC ? (anc - col0) : kFuNC;
+        const int s = g % S::NS;
+        if (g >= (uint32_t)S::NS) {
+          const uint32_t ph = ((g / S::NS) - 1) & 1;
+          if (!(ok = warp_wait(&b_empty[s], ph, abort_flag))) break;
+          if (!(ok = warp_wait(&y_empty[s], ph, abort_flag))) break;
+        }
+        if (lane == 0) {
+          tc::mbar_expect_tx(&ld_full[s], (uint32_t)nc * K2 * 2 + (uint32_t)nc * 128 * 2);
+          bulk_load_1d(sB + (size_t)s * S::kBBytes, rhs_j + (size_t)col0 * K2 * 2, (uint32_t)nc * K2 * 2,
+                       &ld_full[s]);
+          for (int b = 0; b < nc / kFuBox; ++b)
+            tc::tma_load_2d(sY + (size_t)s * 128 * kFuNC + b * 128 * kFuBox, &mapY, (int32_t)row0,
+                            col0 + b * kFuBox, &ld_full[s]);
+        }
+        pend_ld = g + 1;
+        __syncwarp();
+      }
     }
-    // K~^{-1}(alpha rows, :) -> sK[k][q]  (FP64 column-major 2r x 2r)
-    const double* Kj = Kinv + (size_t)parent * K2 * K2;
-    const int rowoff = first ? 0 : RK;
-    for (int e = tid; e < RK * K2; e += blockDim.x) {
-      const int k = e % RK, q = e / RK;
-      sK[k * S::kKLd + q] = (float)Kj[(size_t)q * K2 + rowoff + k];
+    // let the last copies land before the CTA can exit (bounded)
+    if (lane == 0) {
+      if (pend_own > 0) {
+        const uint32_t last = pend_own - 1;
+        tc::mbar_wait(&own_full[last & 1], (last >> 1) & 1);
+        if (last >= 1) tc::mbar_wait(&own_full[(last - 1) & 1], ((last - 1) >> 1) & 1);
+      }
+      for (int q = 0; q < S::NS && q < pend_ld; ++q) {
+        const uint32_t gg = pend_ld - 1 - q;
+        tc::mbar_wait(&ld_full[gg % S::NS], (gg / S::NS) & 1);
+      }
     }
-    __syncthreads();
-    ok = __syncthreads_and(tc::mbar_wait(bar_own, ph_own)) != 0;
-    if (!ok) break;
-    ph_own ^= 1;
-    own_pending = false;
-    // Z = Y_own K~^{-1}(alpha rows, :): thread pair per row, each half of 2r
-    {
-      const int m = tid & 127, half = tid >> 7;
+    __syncwarp();
+  } else if (warp == 5) {
+    // ---------------------------------------------------------------- MMA issuer
+    // the whole warp walks the schedule and waits; lane 0 issues and commits
+    uint32_t g = 0, it = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++it) {
+      const int ab = it % NA;
+      if (!(ok = warp_wait(&a_full[ab], (it / NA) & 1, abort_flag))) break;
+      tc::tc_fence_after();
+      for (int ch = 0; ch < nch; ++ch, ++g) {
+        const int col0 = ch * kFuNC;
+        const int nc = (anc - col0) < kFuNC ? (anc - col0) : kFuNC;
+        const int s = g % S::NS, a = g & 1;
+        if (!(ok = warp_wait(&ld_full[s], (g / S::NS) & 1, abort_flag))) break;
+        if (g >= 2 && !(ok = warp_wait(&acc_empty[a], ((g >> 1) - 1) & 1, abort_flag))) break;
+        tc::tc_fence_after();
+        if (lane == 0) {
+          const uint32_t idesc = tc::idesc_bf16_f32(128, nc);
+          const uint32_t a0 = tc::smem_u32(sA + (size_t)ab * S::kABytes), b0 = tc::smem_u32(sB + (size_t)s * S::kBBytes);
+#pragma unroll
+          for (int ks = 0; ks < K2 / 16; ++ks)
+            tc::mma_bf16(tmem + a * kFuNC, tc::desc_noswz_kmajor(a0 + ks * 256, 128, kSBO),
+                         tc::desc_noswz_kmajor(b0 + ks * 256, 128, kSBO), idesc, ks != 0);
+          tc::mma_commit(&acc_full[a]);
+          tc::mma_commit(&b_empty[s]);
+        }
+        __syncwarp();
+      }
+      if (!ok) break;
+      if (lane == 0) tc::mma_commit(&a_empty[ab]);  // sA[ab] may be refilled once this tile's MMAs are done
+      __syncwarp();
+    }
+    // drain: the last commit covers every MMA issued (bounded)
+    if (lane == 0 && g > 0) tc::mbar_wait(&acc_full[(g - 1) & 1], ((g - 1) >> 1) & 1);
+    __syncwarp();
+  } else if (warp < 4) {
+    // ---------------------------------------------------------------- Z warps
+    const int m = tid;  // 0..127
+    uint32_t it = 0;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++it) {
+      const int64_t row0 = t * 128;
+      const int64_t node = row0 / n;
+      (void)node;
+      const int tb = it & 1;
+      if (!wait_or_abort(&own_full[tb], (it >> 1) & 1, abort_flag)) break;
+      const int ab = it % NA;
+      if (it >= (uint32_t)NA && !wait_or_abort(&a_empty[ab], ((it / NA) - 1) & 1, abort_flag)) break;
+      uint8_t* sAt = sA + (size_t)ab * S::kABytes;
+      const __nv_bfloat16* own = sOwn + (size_t)tb * 128 * RK;
+      const float* kf = sKf + (size_t)tb * RK * S::kKLd;
       float yv[RK];
 #pragma unroll
-      for (int k = 0; k < RK; ++k) yv[k] = __bfloat162float(sOwn[k * 128 + m]);
+      for (int k = 0; k < RK; ++k) yv[k] = __bfloat162float(own[k * 128 + m]);
 #pragma unroll
-      for (int g = 0; g < RK / 8; ++g) {  // 8 output columns -> one 16-byte core row
-        const int q0 = half * RK + g * 8;
+      for (int g8 = 0; g8 < K2 / 8; ++g8) {  // 8 output columns -> one 16-byte core row
+        const int q0 = g8 * 8;
         float z[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) z[u] = 0.f;
 #pragma unroll
         for (int k = 0; k < RK; ++k) {
-          const float4 k0 = *reinterpret_cast<const float4*>(sK + k * S::kKLd + q0);
-          const float4 k1 = *reinterpret_cast<const float4*>(sK + k * S::kKLd + q0 + 4);
+          const float4 k0 = *reinterpret_cast<const float4*>(kf + k * S::kKLd + q0);
+          const float4 k1 = *reinterpret_cast<const float4*>(kf + k * S::kKLd + q0 + 4);
           z[0] = fmaf(yv[k], k0.x, z[0]);
           z[1] = fmaf(yv[k], k0.y, z[1]);
           z[2] = fmaf(yv[k], k0.z, z[2]);
@@ -431,78 +624,60 @@ __global__ void __launch_bounds__(256, RK == 32 ? 2 : 1) update_coupled_tc_kerne
         for (int u = 0; u < 4; ++u)
           pk[u] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(z[2 * u])) |
                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(z[2 * u + 1])) << 16);
-        const int kg = q0 / 8;
-        *reinterpret_cast<uint4*>(sA + kg * 128 + (m >> 3) * kSBO + (m & 7) * 16) =
+        *reinterpret_cast<uint4*>(sAt + g8 * 128 + (m >> 3) * kSBO + (m & 7) * 16) =
             make_uint4(pk[0], pk[1], pk[2], pk[3]);
       }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc::mbar_arrive(&own_empty[tb]);
+      tc::mbar_arrive(&a_full[ab]);
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    for (int ch = 0; ch < nchunks && ok; ++ch) {
-      const int col0 = ch * kFuNC;
-      const int nc = (anc - col0) < kFuNC ? (anc - col0) : kFuNC;  // multiple of 32 (anc = r (c-1))
-      if (ch > 0 && tid == 0) {
-        bulk_wait_read0();
-        tc::mbar_expect_tx(bar_ld, (uint32_t)nc * K2 * 2 + (uint32_t)nc * 128 * 2);
-        bulk_load_1d(sB, rhs_j + (size_t)col0 * K2 * 2, (uint32_t)nc * K2 * 2, bar_ld);
-        for (int b = 0; b < nc / kFuBox; ++b)
-          tc::tma_load_2d(sY + b * 128 * kFuBox, &mapY, (int32_t)row0, col0 + b * kFuBox, bar_ld);
-        ld_pending = true;
-      }
-      tc::tc_fence_before();
-      ok = __syncthreads_and(tc::mbar_wait(bar_ld, ph_ld)) != 0;  // also orders the Z writes before the MMA
-      if (!ok) break;
-      ph_ld ^= 1;
-      ld_pending = false;
-      tc::tc_fence_after();
-      if (tid == 0) {
-        const uint32_t idesc = tc::idesc_bf16_f32(128, nc);
-        const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+  } else if (warp >= 6) {
+    // ---------------------------------------------------------------- epilogue
+    const int q4 = warp & 3;                 // TMEM lane quarter
+    const int row = q4 * 32 + lane;          // tile row
+    const bool storer = warp == 6 && lane == 0;
+    uint32_t g = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+      const int64_t row0 = t * 128;
+      for (int ch = 0; ch < nch; ++ch, ++g) {
+        const int col0 = ch * kFuNC;
+        const int nc = (anc - col0) < kFuNC ? (anc - col0) : kFuNC;
+        const int s = g % S::NS, a = g & 1;
+        bool w = wait_or_abort(&acc_full[a], (g >> 1) & 1, abort_flag);
+        w = w && wait_or_abort(&ld_full[s], (g / S::NS) & 1, abort_flag);
+        if (!(ok = named_bar_and(1, 128, w))) break;  // uniform over the epilogue warps
+        tc::tc_fence_after();
+        __nv_bfloat16* ys = sY + (size_t)s * 128 * kFuNC;
+        for (int cb = 0; cb < nc; cb += 32) {
+          float v[32];
+          tc::tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + a * kFuNC + cb, v);
 #pragma unroll
-        for (int ks = 0; ks < K2 / 16; ++ks)
-          tc::mma_bf16(tmem, tc::desc_noswz_kmajor(a0 + ks * 256, 128, kSBO),
-                       tc::desc_noswz_kmajor(b0 + ks * 256, 128, kSBO), idesc, ks != 0);
-        tc::mma_commit(bar_mma);
-        mma_pending = true;
-      }
-      ok = __syncthreads_and(tc::mbar_wait(bar_mma, ph_mma)) != 0;  // block-uniform before warp-collective loads
-      if (!ok) break;
-      ph_mma ^= 1;
-      mma_pending = false;
-      tc::tc_fence_after();
-      // warps w and w+4 share TMEM lanes 32 (w % 4) .. +31 and split the columns
-      const int m = (warp & 3) * 32 + lane;
-      for (int cb = (warp >> 2) * 32; cb < nc; cb += 64) {
-        float v[32];
-        tc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + cb, v);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          __nv_bfloat16* p = sY + (cb + j) * 128 + m;
-          *p = __float2bfloat16_rn(__bfloat162float(*p) - v[j]);
+          for (int j = 0; j < 32; ++j) {
+            __nv_bfloat16* p = ys + (cb + j) * 128 + row;
+            *p = __float2bfloat16_rn(__bfloat162float(*p) - v[j]);
+          }
+        }
+        tc::tc_fence_before();
+        tc::mbar_arrive(&acc_empty[a]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        named_bar_sync(1, 128);
+        if (storer) {
+          for (int b = 0; b < nc / kFuBox; ++b)
+            tma_store_2d(&mapY, ys + b * 128 * kFuBox, (int32_t)row0, col0 + b * kFuBox);
+          bulk_commit();
+          // hand the stage back as soon as the store has read it
+          bulk_wait_read0();
+          tc::mbar_arrive(&y_empty[s]);
         }
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      tc::tc_fence_before();
-      __syncthreads();
-      tc::tc_fence_after();
-      if (tid == 0) {
-        for (int b = 0; b < nc / kFuBox; ++b)
-          tma_store_2d(&mapY, sY + b * 128 * kFuBox, (int32_t)row0, col0 + b * kFuBox);
-        bulk_commit();
-      }
     }
-  }
-  if (tid == 0) {
-    // a wait that gave up leaves its copies / MMAs in flight: let them land
-    // (bounded) before the shared memory and TMEM are released
-    if (own_pending) tc::mbar_wait(bar_own, ph_own);
-    if (ld_pending) tc::mbar_wait(bar_ld, ph_ld);
-    if (mma_pending) tc::mbar_wait(bar_mma, ph_mma);
-    bulk_wait0();
-    if (!ok) set_status(st, HODLR_ERR_TIMEOUT, c, 2);
+    if (storer) bulk_wait0();
   }
   tc::tc_fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+  if (tid == 0 && *abort_flag) set_status(st, HODLR_ERR_TIMEOUT, c, 2);
+  if (warp == 5) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
 bool update_tc_supported(int64_t N, int r, int c) {
@@ -519,6 +694,11 @@ size_t rhs_bf16_bytes(const hodlr_desc& d) {
   return best;
 }
 
+size_t kf32_bytes(const hodlr_desc& d) {
+  // 2^L children (the deepest level) x r x (2r + 4) FP32
+  return ((size_t)1 << d.L) * (size_t)d.r * (2 * d.r + 4) * 4;
+}
+
 cudaError_t launch_update_coupled_tc(const Factor& F, int c, cudaStream_t s) {
   const int64_t N = F.d.N;
   const int r = F.d.r;
@@ -527,47 +707,59 @@ cudaError_t launch_update_coupled_tc(const Factor& F, int c, cudaStream_t s) {
   const int64_t cpn = chunks_per_node(N, c);
   const int64_t pstride = cpn * (int64_t)r * r * c;  // node -> its first chunk's slot (reduced)
   const int64_t parents = (int64_t)1 << (c - 1);
+  const double* Kc = F.K + F.Koff[c] * 4 * r * r;
   {
     ProfScope prof_(KC_COUPLING_APPLY, s);
-    note_work(8.0 * (double)(1ll << c) * r * anc + 2.0 * (double)parents * anc * 2 * r, 0.0);
+    note_work(8.0 * (double)(1ll << c) * r * anc + 2.0 * (double)parents * anc * 2 * r +
+                  8.0 * parents * 4.0 * r * r + 4.0 * (1ll << c) * r * (2.0 * r + 4),
+              0.0);
     const int64_t total = parents * (int64_t)anc * (2 * r / 8);
     int64_t grid = (total + 255) / 256;
     if (grid > 16 * (int64_t)sm_count()) grid = 16 * (int64_t)sm_count();
+    const int64_t kt = ((int64_t)1 << c) * r * 2 * r;
+    int64_t gk = (kt + 255) / 256;
+    if (gk > 16 * (int64_t)sm_count()) gk = 16 * (int64_t)sm_count();
     if (r == 32) {
       rhs_bf16_kernel<32><<<(unsigned)grid, 256, 0, s>>>(c, F.P, pstride, anc, F.rhs16);
+      note_launches(1);
+      if (!coupling_writes_kf32(F, c)) {
+        kf32_kernel<32><<<(unsigned)gk, 256, 0, s>>>(c, Kc, F.kf32);
+        note_launches(1);
+      }
     } else {
       rhs_bf16_kernel<64><<<(unsigned)grid, 256, 0, s>>>(c, F.P, pstride, anc, F.rhs16);
+      kf32_kernel<64><<<(unsigned)gk, 256, 0, s>>>(c, Kc, F.kf32);
+      note_launches(2);
     }
-    note_launches(1);
   }
   ProfScope prof_(KC_UPDATE_TC, s);
   note_work(2.0 * (double)N * r + 4.0 * (double)N * anc + 4.0 * (double)parents * anc * r +
-                32.0 * (double)parents * r * r,
+                4.0 * (double)(1ll << c) * r * (2.0 * r + 4),
             4.0 * N * r * (double)anc + 4.0 * N * r * (double)r);
   CUtensorMap mY;
   __nv_bfloat16* Y = static_cast<__nv_bfloat16*>(F.Y);
   if (!make_map_plain(&mY, Y, N, (int64_t)r * F.d.L, N)) return cudaErrorInvalidValue;
-  const double* Kc = F.K + F.Koff[c] * 4 * r * r;
   const int64_t tiles = N / 128;
   if (r == 32) {
     using S = FusedSmem<32>;
-    const int per_sm = (int)((227 * 1024) / S::kBytes);
+    const int per_sm = (int)((227 * 1024) / (S::kBytes + 1024));
     int64_t grid = (int64_t)sm_count() * (per_sm < 1 ? 1 : per_sm);
     if (grid > tiles) grid = tiles;
     cudaFuncSetAttribute(update_coupled_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kBytes);
-    { update_coupled_tc_kernel<32><<<(unsigned)grid, 256, S::kBytes, s>>>(mY, N, c, F.rhs16, Kc, anc, F.status); note_launches(1); }
+    { update_coupled_tc_kernel<32><<<(unsigned)grid, kFuThreads, S::kBytes, s>>>(mY, N, c, F.rhs16, F.kf32, anc, F.status); note_launches(1); }
   } else {
     using S = FusedSmem<64>;
-    const int per_sm = (int)((227 * 1024) / S::kBytes);
+    const int per_sm = (int)((227 * 1024) / (S::kBytes + 1024));
     int64_t grid = (int64_t)sm_count() * (per_sm < 1 ? 1 : per_sm);
     if (grid > tiles) grid = tiles;
     cudaFuncSetAttribute(update_coupled_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kBytes);
-    { update_coupled_tc_kernel<64><<<(unsigned)grid, 256, S::kBytes, s>>>(mY, N, c, F.rhs16, Kc, anc, F.status); note_launches(1); }
+    { update_coupled_tc_kernel<64><<<(unsigned)grid, kFuThreads, S::kBytes, s>>>(mY, N, c, F.rhs16, F.kf32, anc, F.status); note_launches(1); }
   }
   return cudaGetLastError();
 }
 
 }  // namespace hodlr
+
 
 namespace hodlr {
 
