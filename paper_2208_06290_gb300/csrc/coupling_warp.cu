@@ -254,6 +254,201 @@ __global__ void __launch_bounds__(32 * kCwWarps) coupling_factor_warp_kernel(int
   }
 }
 
+// Levels with few parents: the same computation by four warps per parent,
+// warp w holding columns 8w .. 8w+7 of every row (lane = row), so that the
+// FP64 work of one parent is spread over the SM's four sub-partitions (one
+// warp alone runs its FP64 instructions on one of them and, at the top
+// levels, is pure latency). Per Gauss-Jordan step the warp owning column k
+// finds the pivot and publishes (p, pivot, column k) through shared memory
+// (double-buffered by step parity); one barrier per step.
+template <bool FULL>
+__global__ void __launch_bounds__(128) coupling_factor_cta4_kernel(int64_t N, int r, int c,
+                                                                   const double* __restrict__ P, int64_t cpn_read,
+                                                                   double* __restrict__ Kinv,
+                                                                   double* __restrict__ node_ld, DevStatus* st,
+                                                                   int64_t heap_first, float* __restrict__ Kf) {
+  using TPR = typename std::conditional<FULL, double, float>::type;
+  __shared__ double Ta[32 * kCwLd], Tb[32 * kCwLd], X[32 * kCwLd];
+  __shared__ double sh_f[2][32];
+  __shared__ double sh_piv[2];
+  __shared__ int sh_p[2];
+  __shared__ TPR M1s[32 * kCwLd], Sis[32 * kCwLd];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t j = blockIdx.x;
+  const int64_t cpn = chunks_per_node(N, c);
+  const size_t slot = (size_t)r * r * c;
+  const int anc = r * (c - 1);
+  const int64_t qa = 2 * j * cpn, qb = (2 * j + 1) * cpn;
+  const int c0 = warp * 8;  // this warp's columns
+
+  // T_a, T_b (warp w gathers columns 8w .. 8w+7)
+#pragma unroll
+  for (int cc = 0; cc < 8; ++cc) {
+    const int col = c0 + cc;
+    double a = 0.0, b = 0.0;
+    if (lane < r && col < r) {
+      const double* pa = P + qa * slot + (size_t)(anc + col) * r + lane;
+      const double* pb = P + qb * slot + (size_t)(anc + col) * r + lane;
+      for (int64_t q = 0; q < cpn_read; ++q) {
+        a += pa[q * slot];
+        b += pb[q * slot];
+      }
+    }
+    Ta[lane * kCwLd + col] = a;
+    Tb[lane * kCwLd + col] = b;
+  }
+  __syncthreads();
+  // row `lane`, columns c0.. of S = I - T_a T_b
+  double s[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s[q] = lane == c0 + q ? 1.0 : 0.0;
+  for (int t = 0; t < r; ++t) {
+    const double a = Ta[lane * kCwLd + t];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s[q] = fma(-a, Tb[t * kCwLd + c0 + q], s[q]);
+  }
+
+  bool used = false;
+  double mypiv = 1.0;
+  int mypos = lane, mystep = lane, ninv = 0;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    const int buf = k & 1;
+    const int ow = k >> 3, kk = k & 7;
+    if (warp == ow) {
+      double v = used ? -1.0 : fabs(s[kk]);
+      if (v != v) v = __longlong_as_double(0x7ff0000000000000ll);
+      int idx = lane;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ov = __shfl_xor_sync(kFull, v, off);
+        const int oi = __shfl_xor_sync(kFull, idx, off);
+        if (ov > v || (ov == v && oi < idx)) {
+          v = ov;
+          idx = oi;
+        }
+      }
+      const double pv = __shfl_sync(kFull, s[kk], idx);
+      sh_f[buf][lane] = s[kk];
+      if (lane == 0) {
+        sh_p[buf] = idx;
+        sh_piv[buf] = pv;
+      }
+    }
+    __syncthreads();
+    const int p = sh_p[buf];
+    const double piv = sh_piv[buf];
+    const double rp = piv != 0.0 ? 1.0 / piv : 0.0;
+    if (lane < k) ninv += p < mypos ? 1 : 0;
+    if (lane == k) {
+      mypiv = piv;
+      mypos = p;
+    }
+    const bool isp = lane == p;
+    if (isp) {
+      used = true;
+      mystep = k;
+    }
+    const double coef = isp ? rp : -sh_f[buf][lane] * rp;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const double pvq = __shfl_sync(kFull, s[q], p);
+      s[q] = (warp == ow && q == kk) ? coef : fma(coef, pvq, isp ? 0.0 : s[q]);
+    }
+  }
+
+  double la = lane < r ? log(fabs(mypiv)) : 0.0;
+  int neg = ((lane < r && mypiv < 0.0) ? 1 : 0) ^ (ninv & 1);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    la += __shfl_xor_sync(kFull, la, off);
+    neg ^= __shfl_xor_sync(kFull, neg, off);
+  }
+  const unsigned zero = __ballot_sync(kFull, lane < r && mypiv == 0.0);
+  const int sing = zero ? __ffs(zero) - 1 : -1;
+
+  // tableau -> X; row k of S^{-1}, columns c0.. : S^{-1}(k, i) = X(p_k, step(i))
+#pragma unroll
+  for (int q = 0; q < 8; ++q) X[lane * kCwLd + c0 + q] = s[q];
+  __syncthreads();
+  double sv[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) sv[i] = X[mypos * kCwLd + __shfl_sync(kFull, mystep, i)];
+  double svc[8];  // this warp's columns of the row (the array above is only indexed statically)
+#pragma unroll
+  for (int q = 0; q < 8; ++q) svc[q] = X[mypos * kCwLd + __shfl_sync(kFull, mystep, c0 + q)];
+  // M1 = S^{-1} T_a, columns c0..
+  TPR m1[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) m1[q] = TPR(0);
+#pragma unroll
+  for (int i = 0; i < 32; ++i)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) m1[q] = fma((TPR)sv[i], (TPR)Ta[i * kCwLd + c0 + q], m1[q]);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    M1s[lane * kCwLd + c0 + q] = m1[q];
+    Sis[lane * kCwLd + c0 + q] = (TPR)svc[q];
+  }
+  __syncthreads();
+  const int n = 2 * r;
+  double* out = Kinv + (size_t)j * n * n;
+  const bool row_ok = lane < r;
+  constexpr int kKfLd = 2 * 32 + 4;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int col = c0 + q;
+    if (row_ok && col < r) {
+      out[(size_t)col * n + r + lane] = -(double)m1[q];  // [21]
+      out[(size_t)(r + col) * n + r + lane] = svc[q];     // [22]
+    }
+  }
+  if (Kf) {
+    float* k1 = Kf + ((size_t)(2 * j + 1) * 32 + lane) * kKfLd;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      k1[c0 + q] = (float)-m1[q];
+      k1[32 + c0 + q] = (float)svc[q];
+    }
+  }
+  // [11] = I + T_b M1, [12] = -T_b S^{-1}, columns c0..
+  TPR a11[8], a12[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    a11[q] = TPR(0);
+    a12[q] = TPR(0);
+  }
+  for (int t = 0; t < r; ++t) {
+    const TPR tb = (TPR)Tb[lane * kCwLd + t];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      a11[q] = fma(tb, M1s[t * kCwLd + c0 + q], a11[q]);
+      a12[q] = fma(tb, Sis[t * kCwLd + c0 + q], a12[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int col = c0 + q;
+    if (row_ok && col < r) {
+      out[(size_t)col * n + lane] = (double)a11[q] + (col == lane ? 1.0 : 0.0);
+      out[(size_t)(r + col) * n + lane] = -(double)a12[q];
+    }
+  }
+  if (Kf) {
+    float* k0 = Kf + ((size_t)(2 * j) * 32 + lane) * kKfLd;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      k0[c0 + q] = (float)a11[q] + (c0 + q == lane ? 1.f : 0.f);
+      k0[32 + c0 + q] = (float)-a12[q];
+    }
+  }
+  if (threadIdx.x == 0) {
+    node_ld[2 * j] = la;
+    node_ld[2 * j + 1] = sing >= 0 ? 0.0 : (neg ? -1.0 : 1.0);
+    if (sing >= 0) set_status(st, HODLR_ERR_SINGULAR_COUPLING, heap_first + j, r + sing);
+  }
+}
+
 bool coupling_warp_supported(const Factor& F) { return F.d.r <= 32; }
 
 bool coupling_writes_kf32(const Factor& F, int c) {
@@ -273,6 +468,16 @@ cudaError_t launch_coupling_factor_warp(const Factor& F, int c, cudaStream_t s) 
     cudaFuncSetAttribute(coupling_factor_warp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   else
     cudaFuncSetAttribute(coupling_factor_warp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const double* Pc = F.P;
+  const int64_t cpn_read = F.P_reduced ? 1 : chunks_per_node(F.d.N, c);
+  float* kf = coupling_writes_kf32(F, c) ? F.kf32 : nullptr;
+  if (parents <= 256) {  // few parents: four warps each (latency)
+    auto k4 = full ? coupling_factor_cta4_kernel<true> : coupling_factor_cta4_kernel<false>;
+    k4<<<(unsigned)parents, 128, 0, s>>>(F.d.N, r, c, Pc, cpn_read, F.K + F.Koff[c] * n * n,
+                                         F.node_ld + 2 * F.Koff[c], F.status, parents, kf);
+    note_launches(1);
+    return cudaGetLastError();
+  }
   const int64_t grid = (parents + kCwWarps - 1) / kCwWarps;
   {
     auto kern = full ? coupling_factor_warp_kernel<true> : coupling_factor_warp_kernel<false>;
