@@ -210,16 +210,22 @@ size_t solve_partials_bytes(const hodlr_desc& d, int k) {
 
 // In-place solve on x (N x k, ld ldx) in type TX with the factor's panels TP.
 template <typename TP, typename TX>
-hodlr_status solve_core(const Factor& F, TX* x, int64_t ldx, int k, double* Ps, int trans, cudaStream_t s) {
+hodlr_status solve_core(const Factor& F, TX* x, int64_t ldx, int k, double* Ps, int trans, cudaStream_t s,
+                        double* slab = nullptr) {
   const hodlr_desc& d = F.d;
   const TP* Y = static_cast<const TP*>(F.Y);
   const TP* Vp = static_cast<const TP*>(F.Vp);
   if (!trans) {
     HODLR_CUDA((launch_leaf_solve<TX, TX>(F, x, ldx, x, ldx, k, 0, s)));
     for (int c = d.L; c >= 1; --c) {
-      HODLR_CUDA((launch_project<TP, TX>(d.N, d.r, c, Vp, F.ldvp, c - 1, x, ldx, k, Ps, 0, s)));
-      const bool red = chunks_per_node(d.N, c) >= 8;  // many partials per node: sum them in parallel first
-      if (red) HODLR_CUDA(launch_reduce_chunks(d.N, d.r, c, Ps, k, s));
+      bool red = false;
+      if (k == 1 && launch_project_k1_slab<TP, TX>(d.N, d.r, c, Vp, F.ldvp, c - 1, x, slab, Ps, s)) {
+        red = true;  // node sums already in the first slots
+      } else {
+        HODLR_CUDA((launch_project<TP, TX>(d.N, d.r, c, Vp, F.ldvp, c - 1, x, ldx, k, Ps, 0, s)));
+        red = chunks_per_node(d.N, c) >= 8;  // many partials per node: sum them in parallel first
+        if (red) HODLR_CUDA(launch_reduce_chunks(d.N, d.r, c, Ps, k, s));
+      }
       HODLR_CUDA(launch_coupling_solve(F, c, Ps, k, 0, s, red));
       const int64_t wstride = chunks_per_node(d.N, c) * (int64_t)d.r * k;
       HODLR_CUDA((launch_update<TP, TX>(d.N, d.r, c, Y, d.N, c - 1, x, ldx, k, Ps, wstride, 0, -1.0, 0, s)));
@@ -243,10 +249,13 @@ hodlr_status solve_any(const Factor& F, double* B, int64_t ldb, int k, void* wor
   double* Ps = static_cast<double*>(work);
   if (F.prec == HODLR_PREC_FP64) return solve_core<double, double>(F, B, ldb, k, Ps, trans, s);
   float* xw = reinterpret_cast<float*>(static_cast<char*>(work) + solve_partials_bytes(d, k));
+  double* slab = k == 1 ? reinterpret_cast<double*>(static_cast<char*>(work) + solve_partials_bytes(d, k) +
+                                                    align_up((size_t)d.N * k * sizeof(float)))
+                        : nullptr;
   HODLR_CUDA((launch_copy_cols<float, double>(d.N, k, B, ldb, xw, d.N, s)));
   hodlr_status st = F.prec == HODLR_PREC_FP32
-                        ? solve_core<float, float>(F, xw, d.N, k, Ps, trans, s)
-                        : solve_core<__nv_bfloat16, float>(F, xw, d.N, k, Ps, trans, s);
+                        ? solve_core<float, float>(F, xw, d.N, k, Ps, trans, s, slab)
+                        : solve_core<__nv_bfloat16, float>(F, xw, d.N, k, Ps, trans, s, slab);
   if (st != HODLR_OK) return st;
   HODLR_CUDA((launch_copy_cols<double, float>(d.N, k, xw, d.N, B, ldb, s)));
   return HODLR_OK;
@@ -255,6 +264,8 @@ hodlr_status solve_any(const Factor& F, double* B, int64_t ldb, int k, void* wor
 size_t solve_ws_bytes(const Factor& F, int k) {
   size_t b = solve_partials_bytes(F.d, k);
   if (F.prec != HODLR_PREC_FP64) b += align_up((size_t)F.d.N * k * sizeof(float));
+  // one right-hand side, low precision: 128-row slab partials of the projections
+  if (F.prec != HODLR_PREC_FP64 && k == 1) b += align_up((size_t)(F.d.N / 128 + 1) * F.d.r * sizeof(double));
   return b;
 }
 

@@ -212,6 +212,12 @@ cudaError_t launch_coupling_solve(const Factor& F, int c, double* P, int k, int 
                                   bool reduced = false);
 // Sum the chunk partials of every node into the node's first chunk slot.
 cudaError_t launch_reduce_chunks(int64_t N, int r, int c, double* P, int ncols, cudaStream_t s);
+// One-column projection of the preconditioner solve in slab form (BF16 panels,
+// FP32 vectors, node sizes a multiple of 128, r <= 32): leaves each node's sum
+// in its first slot of P and returns true; false if it does not apply.
+template <typename TB, typename TR>
+bool launch_project_k1_slab(int64_t N, int r, int c, const TB* Bas, int64_t ldb, int bas_block, const TR* R,
+                            double* slab, double* P, cudaStream_t s);
 
 // Low-precision factors with m <= 128 keep D_b^{-1} (FP32) instead of the LU
 // factors; their leaf solves are GEMMs with it.

@@ -243,6 +243,96 @@ __global__ void __launch_bounds__(256) project_k1v_kernel(int64_t N, int r, int 
   }
 }
 
+// One column, slab form (the preconditioner solve): a warp per 128-row slab
+// (lane l: rows 4l .. 4l+3, one 8- or 16-byte access per rank column), the
+// transposed butterfly leaves the slab's partial of column l in lane l; no
+// CTA-wide reduction. With one slab per node the partial goes straight to the
+// node's slot of P, otherwise to `slab` and project_slab_node_kernel sums the
+// node's slabs (fixed order).
+template <typename TB, typename TR, int RT>
+__global__ void __launch_bounds__(256) project_k1_slab_kernel(int64_t N, int r, const TB* __restrict__ B0,
+                                                              int64_t ldb, const TR* __restrict__ R,
+                                                              double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t sl = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (sl * 128 >= N) return;  // whole warp
+  const int64_t row = sl * 128 + 4 * lane;
+  float x[4];
+  load4(R + row, x);
+  float acc[RT];
+#pragma unroll
+  for (int j = 0; j < RT; ++j) {
+    acc[j] = 0.f;
+    if (j < r) {
+      float b[4];
+      load4(B0 + (int64_t)j * ldb + row, b);
+      acc[j] = b[0] * x[0] + b[1] * x[1] + b[2] * x[2] + b[3] * x[3];
+    }
+  }
+  const float t = warp_transpose_reduce32(acc);
+  if (lane < r) out[(size_t)sl * r + lane] = (double)t;
+}
+
+// Sum of the 128-row slab partials of each node of child level c, in slab
+// order within each warp and warp order across the CTA, into the node's first
+// slot of P (the layout of the chunk partials).
+__global__ void __launch_bounds__(256) project_slab_node_kernel(int64_t N, int r, int c,
+                                                                const double* __restrict__ slab,
+                                                                double* __restrict__ P) {
+  __shared__ double part[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t node = blockIdx.x;
+  const int64_t spn = (N >> c) / 128;  // slabs per node
+  double a = 0.0;
+  if (lane < r)
+    for (int64_t q = warp; q < spn; q += 8) a += slab[(size_t)(node * spn + q) * r + lane];
+  part[warp][lane] = a;
+  __syncthreads();
+  if (warp == 0 && lane < r) {
+    double t = part[0][lane];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) t += part[w][lane];
+    P[(size_t)node * chunks_per_node(N, c) * r + lane] = t;
+  }
+}
+
+// Returns true when it handled level c: the node sums are then in each node's
+// first slot (reduced form).
+template <typename TB, typename TR>
+bool launch_project_k1_slab(int64_t N, int r, int c, const TB* Bas, int64_t ldb, int bas_block, const TR* R,
+                            double* slab, double* P, cudaStream_t s) {
+  if constexpr (!std::is_same<TB, __nv_bfloat16>::value || !std::is_same<TR, float>::value) {
+    return false;
+  } else {
+    const int64_t n = N >> c;
+    if (r > 32 || n % 128 != 0 || ldb % 4 != 0 || reinterpret_cast<uintptr_t>(Bas) % 16 != 0 ||
+        reinterpret_cast<uintptr_t>(R) % 16 != 0)
+      return false;
+    const int64_t spn = n / 128;
+    if (spn > 1 && slab == nullptr) return false;
+    ProfScope prof_(KC_PROJECT, s);
+    note_work(2.0 * (double)N * r + 4.0 * (double)N + 8.0 * (double)(N / 128) * r * (spn > 1 ? 2 : 1),
+              2.0 * N * r);
+    const TB* B0 = Bas + (int64_t)bas_block * r * ldb;
+    const int64_t slabs = N / 128;
+    const unsigned g = (unsigned)((slabs + 7) / 8);
+    if (spn == 1) {
+      // one slab per node, one chunk per node: the slab partial is the node's slot
+      { project_k1_slab_kernel<TB, TR, 32><<<g, 256, 0, s>>>(N, r, B0, ldb, R, P); note_launches(1); }
+    } else {
+      { project_k1_slab_kernel<TB, TR, 32><<<g, 256, 0, s>>>(N, r, B0, ldb, R, slab); note_launches(1); }
+      { project_slab_node_kernel<<<(unsigned)((int64_t)1 << c), 256, 0, s>>>(N, r, c, slab, P); note_launches(1); }
+    }
+    return cudaGetLastError() == cudaSuccess;
+  }
+}
+template bool launch_project_k1_slab<__nv_bfloat16, float>(int64_t, int, int, const __nv_bfloat16*, int64_t, int,
+                                                          const float*, double*, double*, cudaStream_t);
+template bool launch_project_k1_slab<float, float>(int64_t, int, int, const float*, int64_t, int, const float*,
+                                                  double*, double*, cudaStream_t);
+template bool launch_project_k1_slab<double, double>(int64_t, int, int, const double*, int64_t, int, const double*,
+                                                    double*, double*, cudaStream_t);
+
 int project_k1_warps(int64_t ch) {
   int w = 1;
   while (w < 8 && ch >= (int64_t)256 * w && ch % (2 * w) == 0) w *= 2;  // >= 128 rows per warp

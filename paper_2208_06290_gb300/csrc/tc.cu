@@ -232,10 +232,11 @@ cudaError_t launch_project_tc(int64_t N, int r, int L, int c, const __nv_bfloat1
 // between 8-row groups), one contiguous block per kFuNC ancestor columns, so
 // that one bulk copy stages it.
 // Step 2 (update_coupled_tc_kernel): per 128-row tile of a node, the own block
-// Y_own (128 x r) and K~^{-1}(rows of alpha, :) (FP32, staged per child by
-// kf32_kernel) give Z = Y_own K~^{-1}(alpha rows, :) (128 x 2r), formed on the
-// CUDA cores and rounded to BF16 into the A layout; per chunk of kFuNC
-// ancestor columns one tcgen05.mma kind::f16 chain (K = 2r) accumulates
+// Y_own (128 x r) and K~^{-1}(rows of alpha, :) (FP32 rows staged per child by
+// the coupling kernel or kf32_kernel) are rounded to BF16 operands and
+// Z = Y_own K~^{-1}(alpha rows, :) (128 x 2r) is formed by one tcgen05.mma
+// chain (K = r) in TMEM, then rounded to BF16 into the A layout; per chunk of
+// kFuNC ancestor columns one tcgen05.mma kind::f16 chain (K = 2r) accumulates
 // Z Rhs in TMEM, and the epilogue subtracts it from the old Y tile, staged and
 // stored by TMA. The roles and their pipeline are described at the kernel.
 namespace {
@@ -323,10 +324,12 @@ bool make_map_plain(CUtensorMap* map, const void* base, int64_t rows, int64_t co
 //     per tile the own block Y_own (128 x r) and the FP32 rows
 //     K~^{-1}(rows of alpha, :) (precomputed per node, see kf32_kernel); per
 //     chunk the parent's Rhs^T chunk and the old Y tile;
-//   warps 0-3 (Z warps, thread per row): Z = Y_own K~^{-1}(alpha rows, :) in
-//     FP32, rounded to BF16 into the A operand;
-//   warp 5, lane 0 (MMA issuer): one tcgen05.mma chain (K = 2r) per chunk into
-//     one of two TMEM accumulators;
+//   warps 0-3 (Z warps, thread per row): Y_own and K~^{-1}(alpha rows, :)^T
+//     into BF16 K-major operands; after the Z product, Z from TMEM rounded to
+//     BF16 into the A operand;
+//   warp 5, lane 0 (MMA issuer): per tile the Z product (K = r) into TMEM
+//     columns 128.., per chunk one tcgen05.mma chain (K = 2r) into one of two
+//     TMEM accumulators;
 //   warps 6-9 (epilogue, TMEM lane quarter = warp % 4): accumulator subtracted
 //     from the staged old Y tile, which one thread stores by TMA; the stage is
 //     handed back to the producer once the store has read it.
@@ -341,6 +344,7 @@ namespace {
 // faster than four stages and a double-buffered A at one CTA per SM.
 template <int RK> constexpr int fu_stages() { return 2; }
 template <int RK> constexpr int fu_abufs() { return 1; }
+template <int RK> constexpr int fu_obufs() { return RK == 32 ? 2 : 1; }  // own-block / K~ rows buffers
 constexpr int kFuThreads = 320;  // 10 warps
 
 template <int RK>
@@ -354,14 +358,19 @@ struct FusedSmem {
   static constexpr uint32_t kYBytes = 128 * kFuNC * 2;    // old / new Y tile [j][m]
   static constexpr int NS = fu_stages<RK>();
   static constexpr int NA = fu_abufs<RK>();
+  static constexpr int NO = fu_obufs<RK>();
+  static constexpr uint32_t kAoBytes = 128 * RK * 2;      // Y_own, K-major cores (A of the Z product)
+  static constexpr uint32_t kKbBytes = K2 * RK * 2;       // K~^{-1}(alpha rows, :)^T, K-major cores (its B)
   static constexpr uint32_t kOwnOff = 0;
-  static constexpr uint32_t kKfOff = kOwnOff + 2 * kOwnBytes;
-  static constexpr uint32_t kAOff = kKfOff + 2 * kKfBytes;
+  static constexpr uint32_t kKfOff = kOwnOff + NO * kOwnBytes;
+  static constexpr uint32_t kAoOff = kKfOff + NO * kKfBytes;
+  static constexpr uint32_t kKbOff = kAoOff + kAoBytes;
+  static constexpr uint32_t kAOff = kKbOff + kKbBytes;
   static constexpr uint32_t kBOff = kAOff + NA * kABytes;
   static constexpr uint32_t kYOff = kBOff + NS * kBBytes;
   static constexpr uint32_t kBarOff = kYOff + NS * kYBytes;
   static constexpr uint32_t kBytes = kBarOff + 256 + 128;  // barriers, TMEM slot, flag, + alignment slack
-  static_assert(8 * (12 + 3 * NS) + 16 <= 256, "barrier area");
+  static_assert(8 * (14 + 3 * NS) + 16 <= 256, "barrier area");
   static_assert(kBytes <= 227 * 1024, "shared memory per CTA");
 };
 
@@ -441,11 +450,16 @@ __global__ void __launch_bounds__(kFuThreads, RK == 32 ? 2 : 1) update_coupled_t
   constexpr int NA = S::NA;
   constexpr int K2 = 2 * RK;
   constexpr uint32_t kSBO = (K2 / 8) * 128;
-  constexpr uint32_t kTmemCols = 2 * kFuNC;  // two accumulators
+  constexpr uint32_t kTmemCols = 256;          // two chunk accumulators (2 x kFuNC) + the Z product (2r)
+  constexpr uint32_t kZCol = 2 * kFuNC;
+  constexpr uint32_t kSBOr = (RK / 8) * 128;   // 8-row group stride of the K = r operands
+  constexpr int NO = S::NO;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  __nv_bfloat16* sOwn = reinterpret_cast<__nv_bfloat16*>(smem + S::kOwnOff);  // [2][RK][128]
-  float* sKf = reinterpret_cast<float*>(smem + S::kKfOff);                     // [2][RK][kKLd]
+  __nv_bfloat16* sOwn = reinterpret_cast<__nv_bfloat16*>(smem + S::kOwnOff);  // [NO][RK][128]
+  float* sKf = reinterpret_cast<float*>(smem + S::kKfOff);                     // [NO][RK][kKLd]
+  uint8_t* sAo = smem + S::kAoOff;
+  uint8_t* sKb = smem + S::kKbOff;
   uint8_t* sA = smem + S::kAOff;                                               // [NA]
   uint8_t* sB = smem + S::kBOff;                                               // [stages]
   __nv_bfloat16* sY = reinterpret_cast<__nv_bfloat16*>(smem + S::kYOff);      // [stages][kFuNC][128]
@@ -456,11 +470,13 @@ __global__ void __launch_bounds__(kFuThreads, RK == 32 ? 2 : 1) update_coupled_t
   uint64_t* a_empty = bars + 6;                     // [2]   MMA commit
   uint64_t* acc_full = bars + 8;                    // [2]   MMA commit
   uint64_t* acc_empty = bars + 10;                  // [2]   count 128 (epilogue threads)
-  uint64_t* ld_full = bars + 12;                    // [stages]
-  uint64_t* b_empty = bars + 12 + S::NS;        // [stages] MMA commit
-  uint64_t* y_empty = bars + 12 + 2 * S::NS;    // [stages] epilogue storer
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 12 + 3 * S::NS);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 13 + 3 * S::NS);
+  uint64_t* zin_full = bars + 12;                   //       count 128 (Z threads: A_own and B staged)
+  uint64_t* z_done = bars + 13;                     //       MMA commit of the Z product
+  uint64_t* ld_full = bars + 14;                    // [stages]
+  uint64_t* b_empty = bars + 14 + S::NS;        // [stages] MMA commit
+  uint64_t* y_empty = bars + 14 + 2 * S::NS;    // [stages] epilogue storer
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 14 + 3 * S::NS);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 15 + 3 * S::NS);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
@@ -472,6 +488,8 @@ __global__ void __launch_bounds__(kFuThreads, RK == 32 ? 2 : 1) update_coupled_t
       tc::mbar_init(&acc_full[i], 1);
       tc::mbar_init(&acc_empty[i], 128);
     }
+    tc::mbar_init(zin_full, 128);
+    tc::mbar_init(z_done, 1);
     for (int i = 0; i < S::NS; ++i) {
       tc::mbar_init(&ld_full[i], 1);
       tc::mbar_init(&b_empty[i], 1);
@@ -500,8 +518,8 @@ __global__ void __launch_bounds__(kFuThreads, RK == 32 ? 2 : 1) update_coupled_t
     for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++it) {
       const int64_t row0 = t * 128;
       const int64_t node = row0 / n;
-      const int tb = it & 1;
-      if (it >= 2 && !(ok = warp_wait(&own_empty[tb], ((it >> 1) - 1) & 1, abort_flag))) break;
+      const int tb = it % NO;
+      if (it >= (uint32_t)NO && !(ok = warp_wait(&own_empty[tb], ((it / NO) - 1) & 1, abort_flag))) break;
       if (lane == 0) {
         tc::mbar_expect_tx(&own_full[tb], S::kOwnBytes + S::kKfBytes);
 #pragma unroll
@@ -536,10 +554,9 @@ __global__ void __launch_bounds__(kFuThreads, RK == 32 ? 2 : 1) update_coupled_t
     }
     // let the last copies land before the CTA can exit (bounded)
     if (lane == 0) {
-      if (pend_own > 0) {
-        const uint32_t last = pend_own - 1;
-        tc::mbar_wait(&own_full[last & 1], (last >> 1) & 1);
-        if (last >= 1) tc::mbar_wait(&own_full[(last - 1) & 1], ((last - 1) >> 1) & 1);
+      for (int q = 0; q < NO && q < pend_own; ++q) {
+        const uint32_t last = pend_own - 1 - q;
+        tc::mbar_wait(&own_full[last % NO], (last / NO) & 1);
       }
       for (int q = 0; q < S::NS && q < pend_ld; ++q) {
         const uint32_t gg = pend_ld - 1 - q;
@@ -553,6 +570,19 @@ __global__ void __launch_bounds__(kFuThreads, RK == 32 ? 2 : 1) update_coupled_t
     uint32_t g = 0, it = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++it) {
+      // Z = Y_own K~^{-1}(alpha rows, :): M = 128, N = 2r, K = r, into TMEM columns kZCol..
+      if (!(ok = warp_wait(zin_full, it & 1, abort_flag))) break;
+      tc::tc_fence_after();
+      if (lane == 0) {
+        const uint32_t idesc = tc::idesc_bf16_f32(128, K2);
+        const uint32_t a0 = tc::smem_u32(sAo), b0 = tc::smem_u32(sKb);
+#pragma unroll
+        for (int ks = 0; ks < RK / 16; ++ks)
+          tc::mma_bf16(tmem + kZCol, tc::desc_noswz_kmajor(a0 + ks * 256, 128, kSBOr),
+                       tc::desc_noswz_kmajor(b0 + ks * 256, 128, kSBOr), idesc, ks != 0);
+        tc::mma_commit(z_done);
+      }
+      __syncwarp();
       const int ab = it % NA;
       if (!(ok = warp_wait(&a_full[ab], (it / NA) & 1, abort_flag))) break;
       tc::tc_fence_after();
@@ -584,51 +614,63 @@ __global__ void __launch_bounds__(kFuThreads, RK == 32 ? 2 : 1) update_coupled_t
     __syncwarp();
   } else if (warp < 4) {
     // ---------------------------------------------------------------- Z warps
-    const int m = tid;  // 0..127
+    // stage Y_own and K~^{-1}(alpha rows, :)^T as BF16 K-major operands, let
+    // the MMA issuer form Z in TMEM, then round Z to BF16 into the A operand
+    const int m = tid;  // 0..127: tile row, and TMEM lane (warp % 4 = lane quarter)
     uint32_t it = 0;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++it) {
-      const int64_t row0 = t * 128;
-      const int64_t node = row0 / n;
-      (void)node;
-      const int tb = it & 1;
-      if (!wait_or_abort(&own_full[tb], (it >> 1) & 1, abort_flag)) break;
-      const int ab = it % NA;
-      if (it >= (uint32_t)NA && !wait_or_abort(&a_empty[ab], ((it / NA) - 1) & 1, abort_flag)) break;
-      uint8_t* sAt = sA + (size_t)ab * S::kABytes;
+      const int tb = it % NO;
+      if (!wait_or_abort(&own_full[tb], (it / NO) & 1, abort_flag)) break;
+      if (it >= 1 && !wait_or_abort(z_done, (it - 1) & 1, abort_flag)) break;  // previous Z product consumed sAo / sKb
       const __nv_bfloat16* own = sOwn + (size_t)tb * 128 * RK;
       const float* kf = sKf + (size_t)tb * RK * S::kKLd;
-      float yv[RK];
 #pragma unroll
-      for (int k = 0; k < RK; ++k) yv[k] = __bfloat162float(own[k * 128 + m]);
-#pragma unroll
-      for (int g8 = 0; g8 < K2 / 8; ++g8) {  // 8 output columns -> one 16-byte core row
-        const int q0 = g8 * 8;
-        float z[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) z[u] = 0.f;
-#pragma unroll
-        for (int k = 0; k < RK; ++k) {
-          const float4 k0 = *reinterpret_cast<const float4*>(kf + k * S::kKLd + q0);
-          const float4 k1 = *reinterpret_cast<const float4*>(kf + k * S::kKLd + q0 + 4);
-          z[0] = fmaf(yv[k], k0.x, z[0]);
-          z[1] = fmaf(yv[k], k0.y, z[1]);
-          z[2] = fmaf(yv[k], k0.z, z[2]);
-          z[3] = fmaf(yv[k], k0.w, z[3]);
-          z[4] = fmaf(yv[k], k1.x, z[4]);
-          z[5] = fmaf(yv[k], k1.y, z[5]);
-          z[6] = fmaf(yv[k], k1.z, z[6]);
-          z[7] = fmaf(yv[k], k1.w, z[7]);
-        }
+      for (int kg = 0; kg < RK / 8; ++kg) {  // row m of Y_own -> A cores
         uint32_t pk[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          pk[u] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(z[2 * u])) |
-                  ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(z[2 * u + 1])) << 16);
-        *reinterpret_cast<uint4*>(sAt + g8 * 128 + (m >> 3) * kSBO + (m & 7) * 16) =
+          pk[u] = (uint32_t)__bfloat16_as_ushort(own[(kg * 8 + 2 * u) * 128 + m]) |
+                  ((uint32_t)__bfloat16_as_ushort(own[(kg * 8 + 2 * u + 1) * 128 + m]) << 16);
+        *reinterpret_cast<uint4*>(sAo + (m >> 3) * kSBOr + kg * 128 + (m & 7) * 16) =
+            make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      }
+      for (int e = m; e < K2 * (RK / 8); e += 128) {  // (q, k-group) of K~^{-1}(alpha rows, :)^T -> B cores
+        const int q = e % K2, kg = e / K2;
+        uint32_t pk[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          pk[u] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(kf[(kg * 8 + 2 * u) * S::kKLd + q])) |
+                  ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(kf[(kg * 8 + 2 * u + 1) * S::kKLd + q]))
+                   << 16);
+        *reinterpret_cast<uint4*>(sKb + (q >> 3) * kSBOr + kg * 128 + (q & 7) * 16) =
             make_uint4(pk[0], pk[1], pk[2], pk[3]);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tc::mbar_arrive(&own_empty[tb]);
+      tc::mbar_arrive(zin_full);
+      const int ab = it % NA;
+      bool w = wait_or_abort(z_done, it & 1, abort_flag);
+      if (w && it >= (uint32_t)NA) w = wait_or_abort(&a_empty[ab], ((it / NA) - 1) & 1, abort_flag);
+      if (!__all_sync(0xffffffffu, w)) break;  // warp-uniform before the warp-collective TMEM loads
+      tc::tc_fence_after();
+      uint8_t* sAt = sA + (size_t)ab * S::kABytes;
+#pragma unroll
+      for (int cb = 0; cb < K2; cb += 32) {
+        float v[32];
+        tc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + kZCol + cb, v);
+#pragma unroll
+        for (int g8 = 0; g8 < 4; ++g8) {
+          uint32_t pk[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            pk[u] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[g8 * 8 + 2 * u])) |
+                    ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[g8 * 8 + 2 * u + 1])) << 16);
+          *reinterpret_cast<uint4*>(sAt + ((cb >> 3) + g8) * 128 + (m >> 3) * kSBO + (m & 7) * 16) =
+              make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+      }
+      tc::tc_fence_before();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tc::mbar_arrive(&a_full[ab]);
     }
   } else if (warp >= 6) {
