@@ -82,6 +82,19 @@ def fp32_peak_tflops(sm_mhz):
     return 152 * FP32_FLOP_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
 
 
+# DRAM traffic / algorithmic bytes of each kernel class, from one ncu capture
+# of the current kernels on the BIE N=2^17 case (profiles/*_bie-2^17.md; DRAM
+# read + write over the launcher's algorithmic bytes). The bench scales its
+# per-launch algorithmic bytes by this ratio for `roofline.traffic` (the
+# traffic of these kernels grows in proportion to the units processed). A
+# class whose kernel changes loses its entry until it is captured again.
+TRAFFIC_RATIO = {
+    "matvec": (336.6 + 5.1 + 471.4 + 3.2) / (336.5 + 471.9),   # mv1_leaf_project16 + mv1_leaf_apply
+    "project_tc": (75.5 + 2.0) / 74.4,                          # project_tc_kernel, level 7
+    "leaf_solve": (402.7 + 66.7) / 486.5,                       # leaf_apply_tc_kernel
+}
+
+
 def class_bound(cls, prec):
     """Resource that bounds each kernel class of the library's profiler:
     'hbm' (bytes), 'alu64' / 'alu32' (flops on the FP64 / FP32 pipes)."""
@@ -314,8 +327,9 @@ def run_native(args, w, rank, world):
             unit = "TFLOP/s"
             src = f"{'FP64' if bound == 'alu64' else 'FP32'} pipe {per_clk:g} flop/clk/SM x 152 SMs x median " \
                   f"{sm_mhz:.0f} MHz"
+        traffic = TRAFFIC_RATIO[cls] * cbytes / max(cn, 1) if cls in TRAFFIC_RATIO and prec == "bf16" else None
         return {"bound": "hbm" if bound == "hbm" else "alu", "pipe": bound, "kernel": cls, "achieved": ach,
-                "peak": peak, "unit": unit, "frac": ach / peak, "traffic": None, "peak_source": src,
+                "peak": peak, "unit": unit, "frac": ach / peak, "traffic": traffic, "peak_source": src,
                 "launches_in_region": cn, "avg_launch_us": cms * 1e3 / max(cn, 1),
                 "bytes_per_launch": cbytes / max(cn, 1), "flops_per_launch": cflops / max(cn, 1),
                 "ms": cms / args.steps}

@@ -220,7 +220,9 @@ hodlr_status solve_core(const Factor& F, TX* x, int64_t ldx, int k, double* Ps, 
     for (int c = d.L; c >= 1; --c) {
       bool red = false;
       if (k == 1 && launch_project_k1_slab<TP, TX>(d.N, d.r, c, Vp, F.ldvp, c - 1, x, slab, Ps, s)) {
-        red = true;  // node sums already in the first slots
+        // node sums in the first slots: coupling solve and update in one launch
+        if (launch_update_k1_coupled<TP, TX>(F, c, Y, d.N, c - 1, x, Ps, s)) continue;
+        red = true;
       } else {
         HODLR_CUDA((launch_project<TP, TX>(d.N, d.r, c, Vp, F.ldvp, c - 1, x, ldx, k, Ps, 0, s)));
         red = chunks_per_node(d.N, c) >= 8;  // many partials per node: sum them in parallel first

@@ -215,6 +215,12 @@ cudaError_t launch_reduce_chunks(int64_t N, int r, int c, double* P, int ncols, 
 // One-column projection of the preconditioner solve in slab form (BF16 panels,
 // FP32 vectors, node sizes a multiple of 128, r <= 32): leaves each node's sum
 // in its first slot of P and returns true; false if it does not apply.
+// One column, after launch_project_k1_slab: the coupling solve fused into the
+// update x(rows) -= Y_own w (w formed per CTA from K~^{-1} and the node sums);
+// false if it does not apply.
+template <typename TB, typename TR>
+bool launch_update_k1_coupled(const Factor& F, int c, const TB* Bas, int64_t ldb, int bas_block, TR* R,
+                              const double* P, cudaStream_t s);
 template <typename TB, typename TR>
 bool launch_project_k1_slab(int64_t N, int r, int c, const TB* Bas, int64_t ldb, int bas_block, const TR* R,
                             double* slab, double* P, cudaStream_t s);

@@ -530,6 +530,100 @@ __global__ void __launch_bounds__(256) update_k1v_kernel(int64_t N, int r, int c
   store4(R + row, x);
 }
 
+// One column, coupling solve fused in (the preconditioner solve after the
+// slab projection): each CTA first forms its node's w = K~^{-1}(rows of the
+// node, :) [s_second; s_first] in FP64 from the node sums in the children's
+// first slots (rows 0..r-1 of the right-hand side from the second child, as
+// in K~ [w_first; w_second] = [s_second; s_first]), then x(rows) -= Y_own w
+// as update_k1v_kernel.
+template <typename TB, typename TR, typename TA>
+__global__ void __launch_bounds__(256) update_k1v_coupled_kernel(int64_t N, int r, int c,
+                                                                 const TB* __restrict__ Bas, int64_t ldb,
+                                                                 int bas_block, TR* __restrict__ R,
+                                                                 const double* __restrict__ P, int64_t pstride,
+                                                                 const double* __restrict__ Kinv) {
+  __shared__ double sRhs[128];
+  __shared__ double sPart[8][64];
+  __shared__ TA sW[64];
+  const int64_t n = N >> c;
+  const int64_t tpn = (n + 1023) / 1024;
+  const int64_t node = blockIdx.x / tpn;
+  const int64_t t0 = (blockIdx.x % tpn) * 1024;
+  const int n2 = 2 * r;
+  const int64_t parent = node >> 1;
+  const int rowoff = (node & 1) ? r : 0;
+  for (int q = threadIdx.x; q < n2; q += 256)
+    sRhs[q] = q < r ? P[(2 * parent + 1) * pstride + q] : P[(2 * parent) * pstride + q - r];
+  __syncthreads();
+  {
+    const int j = threadIdx.x % r, part = threadIdx.x / r;  // r <= 32: 8 parts
+    const int parts = 256 / r;
+    const double* Kj = Kinv + (size_t)parent * n2 * n2;
+    double a = 0.0;
+    if (part < parts && part < 8)
+      for (int q = part; q < n2; q += (parts < 8 ? parts : 8)) a += Kj[(size_t)q * n2 + rowoff + j] * sRhs[q];
+    if (part < 8) sPart[part][j] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < r) {
+    const int parts = 256 / r < 8 ? 256 / r : 8;
+    double w = 0.0;
+    for (int pp = 0; pp < parts; ++pp) w += sPart[pp][threadIdx.x];
+    sW[threadIdx.x] = conv<TA>(-w);
+  }
+  __syncthreads();
+  const int64_t i = t0 + 4 * threadIdx.x;
+  if (i >= n) return;
+  const int64_t row = node * n + i;
+  const TB* B0 = Bas + (int64_t)bas_block * r * ldb + row;
+  TA acc[4] = {TA(0), TA(0), TA(0), TA(0)};
+#pragma unroll 8
+  for (int j = 0; j < r; ++j) {
+    TA b[4];
+    load4(B0 + (int64_t)j * ldb, b);
+    const TA w = sW[j];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] += b[q] * w;
+  }
+  TA x[4];
+  load4(R + row, x);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) x[q] += acc[q];
+  store4(R + row, x);
+}
+
+template <typename TB, typename TR>
+bool launch_update_k1_coupled(const Factor& F, int c, const TB* Bas, int64_t ldb, int bas_block, TR* R,
+                              const double* P, cudaStream_t s) {
+  const int64_t N = F.d.N;
+  const int r = F.d.r;
+  const int64_t n = N >> c;
+  if (r > 32 || n % 4 != 0 || ldb % 4 != 0 || reinterpret_cast<uintptr_t>(Bas) % 16 != 0 ||
+      reinterpret_cast<uintptr_t>(R) % 16 != 0)
+    return false;
+  ProfScope prof_(KC_UPDATE, s);
+  const int64_t parents = (int64_t)1 << (c - 1);
+  note_work(sizeof(TB) * (double)N * r + 2.0 * sizeof(TR) * (double)N + 8.0 * parents * 4.0 * r * r +
+                8.0 * (double)(1ll << c) * r,
+            2.0 * N * r + parents * 2.0 * (2.0 * r) * (2.0 * r));
+  const int64_t tpn = (n + 1023) / 1024;
+  const unsigned g = (unsigned)(((int64_t)1 << c) * tpn);
+  const int64_t pstride = chunks_per_node(N, c) * (int64_t)r;
+  using TA = typename AccOf<TR>::type;
+  {
+    update_k1v_coupled_kernel<TB, TR, TA><<<g, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, P, pstride,
+                                                            F.K + F.Koff[c] * 4 * r * r);
+    note_launches(1);
+  }
+  return cudaGetLastError() == cudaSuccess;
+}
+template bool launch_update_k1_coupled<__nv_bfloat16, float>(const Factor&, int, const __nv_bfloat16*, int64_t, int,
+                                                            float*, const double*, cudaStream_t);
+template bool launch_update_k1_coupled<float, float>(const Factor&, int, const float*, int64_t, int, float*,
+                                                    const double*, cudaStream_t);
+template bool launch_update_k1_coupled<double, double>(const Factor&, int, const double*, int64_t, int, double*,
+                                                      const double*, cudaStream_t);
+
 template <typename TB, typename TR>
 cudaError_t launch_update(int64_t N, int r, int c, const TB* Bas, int64_t ldb, int bas_block, TR* R, int64_t ldr,
                           int ncols, const double* Wbase, int64_t wstride, int swap_sibling, double alpha,
