@@ -217,17 +217,17 @@ hodlr_status solve_core(const Factor& F, TX* x, int64_t ldx, int k, double* Ps, 
   const TP* Vp = static_cast<const TP*>(F.Vp);
   if (!trans) {
     HODLR_CUDA((launch_leaf_solve<TX, TX>(F, x, ldx, x, ldx, k, 0, s)));
-    for (int c = d.L; c >= 1; --c) {
-      bool red = false;
-      if (k == 1 && launch_project_k1_slab<TP, TX>(d.N, d.r, c, Vp, F.ldvp, c - 1, x, slab, Ps, s)) {
-        // node sums in the first slots: coupling solve and update in one launch
-        if (launch_update_k1_coupled<TP, TX>(F, c, Y, d.N, c - 1, x, Ps, s)) continue;
-        red = true;
-      } else {
-        HODLR_CUDA((launch_project<TP, TX>(d.N, d.r, c, Vp, F.ldvp, c - 1, x, ldx, k, Ps, 0, s)));
-        red = chunks_per_node(d.N, c) >= 8;  // many partials per node: sum them in parallel first
-        if (red) HODLR_CUDA(launch_reduce_chunks(d.N, d.r, c, Ps, k, s));
+    if constexpr (std::is_same<TX, float>::value && !std::is_same<TP, double>::value) {
+      // one column: two launches per level (parts in the slab region, W in Ps)
+      if (k == 1 && slab && solve_k1_supported<TP>(F, Y, Vp, F.ldvp, x)) {
+        HODLR_CUDA(launch_solve_k1_chain<TP>(F, Y, Vp, F.ldvp, x, slab, reinterpret_cast<float*>(Ps), s));
+        return HODLR_OK;
       }
+    }
+    for (int c = d.L; c >= 1; --c) {
+      HODLR_CUDA((launch_project<TP, TX>(d.N, d.r, c, Vp, F.ldvp, c - 1, x, ldx, k, Ps, 0, s)));
+      const bool red = chunks_per_node(d.N, c) >= 8;  // many partials per node: sum them in parallel first
+      if (red) HODLR_CUDA(launch_reduce_chunks(d.N, d.r, c, Ps, k, s));
       HODLR_CUDA(launch_coupling_solve(F, c, Ps, k, 0, s, red));
       const int64_t wstride = chunks_per_node(d.N, c) * (int64_t)d.r * k;
       HODLR_CUDA((launch_update<TP, TX>(d.N, d.r, c, Y, d.N, c - 1, x, ldx, k, Ps, wstride, 0, -1.0, 0, s)));
@@ -266,8 +266,8 @@ hodlr_status solve_any(const Factor& F, double* B, int64_t ldb, int k, void* wor
 size_t solve_ws_bytes(const Factor& F, int k) {
   size_t b = solve_partials_bytes(F.d, k);
   if (F.prec != HODLR_PREC_FP64) b += align_up((size_t)F.d.N * k * sizeof(float));
-  // one right-hand side, low precision: 128-row slab partials of the projections
-  if (F.prec != HODLR_PREC_FP64 && k == 1) b += align_up((size_t)(F.d.N / 128 + 1) * F.d.r * sizeof(double));
+  // one right-hand side, low precision: the parts of the projections
+  if (F.prec != HODLR_PREC_FP64 && k == 1) b += align_up(solve_k1_parts_elems(F.d) * sizeof(double));
   return b;
 }
 

@@ -33,6 +33,21 @@ constexpr int kCwLd = 33;    // padded row stride of the per-warp 32 x 32 tiles
 constexpr unsigned kFull = 0xffffffffu;
 }  // namespace
 
+// Pivot lane of a Gauss-Jordan step: the unused lane with the largest |x|,
+// the lowest lane on ties (LAPACK's first maximum), NaN above every number
+// (a total order keeps the choice warp-uniform). |x| is compared as the
+// integer bits of the FP64 magnitude (the same order for non-NaN values),
+// high word then low word, by two warp reductions on the integer pipe:
+// the FP64 pipe, the bottleneck of these kernels, is left to the elimination.
+__device__ __forceinline__ int pivot_lane(double x, bool used) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  const unsigned hi = used ? 0u : (unsigned)(bits >> 32) + 1u;  // 0 only for used lanes
+  const unsigned lo = used ? 0u : (unsigned)bits;
+  const unsigned H = __reduce_max_sync(kFull, hi);
+  const unsigned Lo = __reduce_max_sync(kFull, hi == H ? lo : 0u);
+  return __ffs(__ballot_sync(kFull, hi == H && lo == Lo)) - 1;  // an unused lane: H >= 1
+}
+
 template <bool FULL>
 __global__ void __launch_bounds__(32 * kCwWarps) coupling_factor_warp_kernel(int64_t N, int r, int c,
                                                                               const double* __restrict__ P,
@@ -71,14 +86,38 @@ __global__ void __launch_bounds__(32 * kCwWarps) coupling_factor_warp_kernel(int
   }
   __syncwarp();
 
-  // row `lane` of S = I - T_a T_b
+  // row `lane` of S = I - T_a T_b: FP64 products for the FP64 and FP32
+  // factors; FP32 products of FP32 copies (in X, free until the tableau is
+  // gathered) for the BF16 factor, whose T_a, T_b come from BF16 panels
   double s[32];
+  if constexpr (FULL) {
 #pragma unroll
-  for (int q = 0; q < 32; ++q) s[q] = lane == q ? 1.0 : 0.0;
-  for (int t = 0; t < r; ++t) {
-    const double a = Ta[lane * kCwLd + t];
+    for (int q = 0; q < 32; ++q) s[q] = lane == q ? 1.0 : 0.0;
+    for (int t = 0; t < r; ++t) {
+      const double a = Ta[lane * kCwLd + t];
 #pragma unroll
-    for (int q = 0; q < 32; ++q) s[q] = fma(-a, Tb[t * kCwLd + q], s[q]);
+      for (int q = 0; q < 32; ++q) s[q] = fma(-a, Tb[t * kCwLd + q], s[q]);
+    }
+  } else {
+    float* TaF = reinterpret_cast<float*>(X);
+    float* TbF = TaF + 32 * kCwLd;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      TaF[lane * kCwLd + q] = (float)Ta[lane * kCwLd + q];
+      TbF[lane * kCwLd + q] = (float)Tb[lane * kCwLd + q];
+    }
+    __syncwarp();
+    float sf[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) sf[q] = lane == q ? 1.f : 0.f;
+    for (int t = 0; t < r; ++t) {
+      const float a = TaF[lane * kCwLd + t];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) sf[q] = fmaf(-a, TbF[t * kCwLd + q], sf[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 32; ++q) s[q] = (double)sf[q];
+    __syncwarp();  // X is the tableau's area below
   }
 
   bool used = false;
@@ -88,19 +127,7 @@ __global__ void __launch_bounds__(32 * kCwWarps) coupling_factor_warp_kernel(int
   int ninv = 0;       // lane k: #{k' > k : p_k' < p_k}
 #pragma unroll
   for (int k = 0; k < 32; ++k) {
-    double v = used ? -1.0 : fabs(s[k]);
-    if (v != v) v = __longlong_as_double(0x7ff0000000000000ll);  // NaN ranks first: a total order keeps the choice warp-uniform
-    int idx = lane;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const double ov = __shfl_xor_sync(kFull, v, off);
-      const int oi = __shfl_xor_sync(kFull, idx, off);
-      if (ov > v || (ov == v && oi < idx)) {
-        v = ov;
-        idx = oi;
-      }
-    }
-    const int p = idx;  // an unused lane: at least one has v >= 0 > -1
+    const int p = pivot_lane(s[k], used);
     const double piv = __shfl_sync(kFull, s[k], p);
     const double rp = piv != 0.0 ? 1.0 / piv : 0.0;
     if (lane < k) ninv += p < mypos ? 1 : 0;
@@ -296,16 +323,34 @@ __global__ void __launch_bounds__(128) coupling_factor_cta4_kernel(int64_t N, in
     }
     Ta[lane * kCwLd + col] = a;
     Tb[lane * kCwLd + col] = b;
+    if constexpr (!FULL) {  // FP32 copies for the BF16 factor's S, in M1s / Sis until the products
+      M1s[lane * kCwLd + col] = (float)a;
+      Sis[lane * kCwLd + col] = (float)b;
+    }
   }
   __syncthreads();
-  // row `lane`, columns c0.. of S = I - T_a T_b
+  // row `lane`, columns c0.. of S = I - T_a T_b (FP32 products for the BF16
+  // factor, as in the one-warp kernel)
   double s[8];
+  if constexpr (FULL) {
 #pragma unroll
-  for (int q = 0; q < 8; ++q) s[q] = lane == c0 + q ? 1.0 : 0.0;
-  for (int t = 0; t < r; ++t) {
-    const double a = Ta[lane * kCwLd + t];
+    for (int q = 0; q < 8; ++q) s[q] = lane == c0 + q ? 1.0 : 0.0;
+    for (int t = 0; t < r; ++t) {
+      const double a = Ta[lane * kCwLd + t];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) s[q] = fma(-a, Tb[t * kCwLd + c0 + q], s[q]);
+      for (int q = 0; q < 8; ++q) s[q] = fma(-a, Tb[t * kCwLd + c0 + q], s[q]);
+    }
+  } else {
+    float sf[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) sf[q] = lane == c0 + q ? 1.f : 0.f;
+    for (int t = 0; t < r; ++t) {
+      const float a = M1s[lane * kCwLd + t];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) sf[q] = fmaf(-a, Sis[t * kCwLd + c0 + q], sf[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s[q] = (double)sf[q];
   }
 
   bool used = false;
@@ -316,18 +361,7 @@ __global__ void __launch_bounds__(128) coupling_factor_cta4_kernel(int64_t N, in
     const int buf = k & 1;
     const int ow = k >> 3, kk = k & 7;
     if (warp == ow) {
-      double v = used ? -1.0 : fabs(s[kk]);
-      if (v != v) v = __longlong_as_double(0x7ff0000000000000ll);
-      int idx = lane;
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const double ov = __shfl_xor_sync(kFull, v, off);
-        const int oi = __shfl_xor_sync(kFull, idx, off);
-        if (ov > v || (ov == v && oi < idx)) {
-          v = ov;
-          idx = oi;
-        }
-      }
+      const int idx = pivot_lane(s[kk], used);
       const double pv = __shfl_sync(kFull, s[kk], idx);
       sh_f[buf][lane] = s[kk];
       if (lane == 0) {

@@ -43,6 +43,26 @@ __device__ __forceinline__ TD conv(TS s) {
   return d;
 }
 
+// FP64 -> FP32 on the integer pipe (this GPU's FP64 pipe, which also runs
+// the F2F conversion, is narrow): the sign and exponent rebiased and the top
+// 23 significand bits kept, i.e. rounding toward zero; magnitudes below
+// 2^-126 become a signed zero, finite magnitudes of 2^128 and above become
+// infinity, NaN stays NaN.
+__device__ __forceinline__ uint32_t f64_to_f32_trunc_bits(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const uint32_t sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  const uint32_t mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  uint32_t bits = sign | ((uint32_t)(e - 896) << 23) | mant;
+  if (e <= 896) bits = sign;
+  if (e >= 1151) bits = sign | 0x7F800000u | ((e == 2047 && ((hi & 0xFFFFFu) | lo)) ? 0x400000u : 0u);
+  return bits;
+}
+// isfinite of an FP64 value from its exponent bits (integer pipe).
+__device__ __forceinline__ bool f64_finite_bits(double x) {
+  return (((uint32_t)__double2hiint(x) >> 20) & 0x7FFu) != 0x7FFu;
+}
+
 // Four consecutive elements (16-byte aligned for float / double, 8-byte for
 // BF16) loaded in one or two vector accesses and converted; store4 likewise.
 template <typename TA>
@@ -212,18 +232,16 @@ cudaError_t launch_coupling_solve(const Factor& F, int c, double* P, int k, int 
                                   bool reduced = false);
 // Sum the chunk partials of every node into the node's first chunk slot.
 cudaError_t launch_reduce_chunks(int64_t N, int r, int c, double* P, int ncols, cudaStream_t s);
-// One-column projection of the preconditioner solve in slab form (BF16 panels,
-// FP32 vectors, node sizes a multiple of 128, r <= 32): leaves each node's sum
-// in its first slot of P and returns true; false if it does not apply.
-// One column, after launch_project_k1_slab: the coupling solve fused into the
-// update x(rows) -= Y_own w (w formed per CTA from K~^{-1} and the node sums);
-// false if it does not apply.
-template <typename TB, typename TR>
-bool launch_update_k1_coupled(const Factor& F, int c, const TB* Bas, int64_t ldb, int bas_block, TR* R,
-                              const double* P, cudaStream_t s);
-template <typename TB, typename TR>
-bool launch_project_k1_slab(int64_t N, int r, int c, const TB* Bas, int64_t ldb, int bas_block, const TR* R,
-                            double* slab, double* P, cudaStream_t s);
+// One right-hand side, low-precision panels TB, FP32 vector: the level loop
+// of the forward solve in two launches per level (parent sums + coupling
+// solve; update of level c fused with the projection of level c - 1).
+// parts: solve_k1_parts_elems doubles; W: 2^L * r floats.
+size_t solve_k1_parts_elems(const hodlr_desc& d);
+template <typename TB>
+bool solve_k1_supported(const Factor& F, const TB* Y, const TB* Vp, int64_t ldvp, const float* x);
+template <typename TB>
+cudaError_t launch_solve_k1_chain(const Factor& F, const TB* Y, const TB* Vp, int64_t ldvp, float* x,
+                                  double* parts, float* W, cudaStream_t s);
 
 // Low-precision factors with m <= 128 keep D_b^{-1} (FP32) instead of the LU
 // factors; their leaf solves are GEMMs with it.

@@ -8,7 +8,8 @@
 
 namespace hodlr {
 
-// One CTA (256 threads, 16 x 16) per leaf: D_b (FP64) -> FP32, padded to an
+// One CTA (256 threads, 16 x 16) per leaf: D_b (FP64) -> FP32 (rounded toward
+// zero on the integer pipe), padded to an
 // MB x MB matrix with the identity (MB = 64 or 128), inverted in registers by
 // Gauss-Jordan elimination with partial pivoting over all MB rows; thread
 // (ty, tx) holds the TT x TT block (TT = MB / 16) of rows ty*TT.. and columns
@@ -17,55 +18,41 @@ namespace hodlr {
 // pivot row p_k is the unused row with the largest |a_ik| (lowest row on
 // ties, as getrf's first maximum) and the exchange step turns row p_k into
 // unknown k and column k into equation p_k, so that at the end entry (r, c) of
-// the tableau is D^{-1}(step(r), p_c) and is written there. Per step, two
-// barriers: (1) the half-warp owning column k publishes it (the multipliers)
-// and the pivot it found with shuffles, (2) the owners of row p_k publish it
-// scaled by 1/pivot; every thread then applies the rank-1 update to its block.
-// The pivots are getrf's pivots with rows in the order p_0, p_1, ..., so
-// log|det D_b| = sum log|pivot| and the sign is the parity of the negative
-// pivots and of the inversions of (p_k). Writes D_b^{-1} (FP32, column-major)
-// to the factor's leaf buffer, the log-determinant pieces, and the status on a
-// zero pivot or a non-finite entry.
+// the tableau is D^{-1}(step(r), p_c) and is written there.
+// Rows are kept unscaled: the tableau row r is the stored row times
+// 1 / pivot(step(r)) once row r has been a pivot row (the rank-1 update is
+// linear in each row, so the scale commutes with later steps), and every
+// stored row is scaled once after the last step. Per step, two barriers:
+// (1) the half-warp owning column k finds the pivot with shuffles and
+// publishes the multipliers f_i / pivot (0 for the pivot row, whose entry k
+// becomes 1), (2) the owners of row p_k stage their blocks in shared memory;
+// every thread then applies the rank-1 update a_ij -= (f_i / pivot) a_pj to
+// its block. The pivots are getrf's pivots with rows in the order p_0, p_1,
+// ..., so log|det D_b| = sum log|pivot| and the sign is the parity of the
+// negative pivots and of the inversions of (p_k). Writes D_b^{-1} (FP32,
+// column-major) to the factor's leaf buffer, the log-determinant pieces, and
+// the status on a zero pivot or a non-finite entry.
 // If Dtc is given (m = MB = 128), D_b^{-1} is also written in the K-major
 // core-matrix layout of a tcgen05 operand (8-row x 16-byte cores: element
 // (i, k) at float (i/8)*1024 + (k/4)*32 + (i%8)*4 + k%4), the A operand of
 // the tensor-core leaf apply.
-template <int TT, int II = 0>
-__device__ __forceinline__ void get_row(const float (&a)[TT][TT], int pi, float (&q)[TT]) {
-  if constexpr (II < TT) {
-    if (pi == II) {
-#pragma unroll
-      for (int jj = 0; jj < TT; ++jj) q[jj] = a[II][jj];
-    } else {
-      get_row<TT, II + 1>(a, pi, q);
-    }
-  }
-}
-
-template <int TT, int II = 0>
-__device__ __forceinline__ void set_row(float (&a)[TT][TT], int pi, const float (&q)[TT]) {
-  if constexpr (II < TT) {
-    if (pi == II) {
-#pragma unroll
-      for (int jj = 0; jj < TT; ++jj) a[II][jj] = q[jj];
-    } else {
-      set_row<TT, II + 1>(a, pi, q);
-    }
-  }
-}
-
 template <int MB>
 __global__ void __launch_bounds__(256, 2) leaf_inv_kernel(int m, const double* __restrict__ D,
                                                           float* __restrict__ Dinv, float* __restrict__ Dtc,
                                                           double* __restrict__ leaf_ld, DevStatus* st) {
   constexpr int TT = MB / 16;
+  constexpr int TG = TT / 4;            // float4 groups of a thread's rows / columns
   constexpr int LD = MB + 1;
-  extern __shared__ float s_stage[];  // MB x LD: input, then output staging
-  __shared__ float s_f[2][MB];        // column k (multipliers), double-buffered by step parity
-  __shared__ float s_q[2][MB];        // pivot row scaled by 1/pivot
-  __shared__ float2 s_pv[2];          // (pivot value, pivot row as int bits)
-  __shared__ int s_prow[MB];          // p_k
-  __shared__ int s_step[MB];          // step that took row r
+  constexpr int BLK = TT * TT + 4;      // staged block stride (floats): the two half-warps hit different banks
+  extern __shared__ float s_stage[];    // MB x LD: input, then output staging
+  // multipliers of step k (double-buffered by step parity); rows ty*TT + 4g + e
+  // at float ((g * 16 + ty) * 4 + e), so that a quarter-warp reads 128
+  // contiguous bytes
+  __shared__ __align__(16) float s_f[2][MB];
+  __shared__ __align__(16) float s_blk[16 * BLK];  // blocks of the owners of the pivot row
+  __shared__ float2 s_pv[2];                        // (pivot value, pivot row as int bits)
+  __shared__ int s_prow[MB];                        // p_k
+  __shared__ int s_step[MB];                        // step that took row r
   __shared__ float s_piv[MB];
   __shared__ int s_bad;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -74,17 +61,23 @@ __global__ void __launch_bounds__(256, 2) leaf_inv_kernel(int m, const double* _
   if (tid == 0) s_bad = 0;
   const double* Db = D + (size_t)b * m * m;
   bool bad = false;
-  for (int e = tid; e < MB * MB; e += 256) {
-    const int c = e / MB, r = e % MB;
-    float v;
-    if (r < m && c < m) {
-      const double x = Db[(size_t)c * m + r];
-      bad |= !isfinite(x);
-      v = (float)x;
-    } else {
-      v = r == c ? 1.f : 0.f;
+  // eight loads in flight per thread before any is used (the leaf is read
+  // once, from HBM)
+  for (int e0 = 0; e0 < MB * MB; e0 += 8 * 256) {
+    double xv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * 256 + tid;
+      const int c = e / MB, r = e % MB;
+      xv[u] = (r < m && c < m) ? Db[(size_t)c * m + r] : (r == c ? 1.0 : 0.0);
     }
-    s_stage[c * LD + r] = v;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * 256 + tid;
+      const int c = e / MB, r = e % MB;
+      bad |= !f64_finite_bits(xv[u]);
+      s_stage[c * LD + r] = __uint_as_float(f64_to_f32_trunc_bits(xv[u]));
+    }
   }
   __syncthreads();
   if (bad) atomicOr(&s_bad, 1);
@@ -101,75 +94,86 @@ __global__ void __launch_bounds__(256, 2) leaf_inv_kernel(int m, const double* _
     for (int kk = 0; kk < TT; ++kk) {
       const int k = kb * TT + kk;
       const int buf = k & 1;
-      // (1) the half-warp owning column k: multipliers and the pivot; column k
-      // is zeroed so that the update below writes -f_i / pivot there
+      // (1) the half-warp owning column k: the pivot (largest |a_ik| over the
+      // unused rows, lowest row on ties; NaN ranks as +inf so that the order
+      // stays total), then the scaled multipliers and column k of the
+      // tableau (1 in the pivot row, 0 elsewhere; the update below writes
+      // -f_i / pivot there)
       if (warp == (kb >> 1)) {
-        float bv = -1.f, bval = 0.f;
-        int brow = MB;
+        unsigned long long bkey = 0;  // (|a| bits, 255 - row): larger |a|, then the lower row; 0 = used
+        float bval = 0.f;
         if (col_owner) {
 #pragma unroll
           for (int ii = 0; ii < TT; ++ii) {
             const float x = a[ii][kk];
-            s_f[buf][ty * TT + ii] = x;
-            a[ii][kk] = 0.f;
-            float v = ((used >> ii) & 1u) ? -1.f : fabsf(x);
-            if (v != v) v = __int_as_float(0x7f800000);  // NaN ranks first: a total order keeps p uniform
-            if (v > bv) {
-              bv = v;
+            uint32_t ab = __float_as_uint(x) & 0x7fffffffu;
+            if (ab > 0x7f800000u) ab = 0x7f800000u;
+            const unsigned long long key =
+                ((used >> ii) & 1u) ? 0ull : ((unsigned long long)ab << 8) | (unsigned long long)(255 - (ty * TT + ii));
+            if (key > bkey) {
+              bkey = key;
               bval = x;
-              brow = ty * TT + ii;
             }
           }
         }
+        unsigned long long wkey = bkey;
 #pragma unroll
-        for (int off = 8; off > 0; off >>= 1) {  // within each half-warp
-          const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
-          const float oval = __shfl_xor_sync(0xffffffffu, bval, off);
-          const int orow = __shfl_xor_sync(0xffffffffu, brow, off);
-          if (ov > bv || (ov == bv && orow < brow)) {
-            bv = ov;
-            bval = oval;
-            brow = orow;
+        for (int off = 8; off > 0; off >>= 1) wkey = max(wkey, __shfl_xor_sync(0xffffffffu, wkey, off));
+        const int p = 255 - (int)(wkey & 255ull);
+        const float piv = __shfl_sync(0xffffffffu, bval, (lane & 16) | (p / TT));
+        if (col_owner) {
+          const float rp = piv != 0.f ? 1.f / piv : 0.f;
+#pragma unroll
+          for (int ii = 0; ii < TT; ++ii) {
+            const int row = ty * TT + ii;
+            const float x = a[ii][kk];
+            s_f[buf][((ii >> 2) * 16 + ty) * 4 + (ii & 3)] = row == p ? 0.f : x * rp;
+            a[ii][kk] = row == p ? 1.f : 0.f;
           }
-        }
-        if (col_owner && ty == 0) {
-          s_pv[buf] = make_float2(bval, __int_as_float(brow));
-          s_prow[k] = brow;
-          s_step[brow] = k;
-          s_piv[k] = bval;
+          if (ty == 0) {
+            s_pv[buf] = make_float2(piv, __int_as_float(p));
+            s_prow[k] = p;
+            s_step[p] = k;
+            s_piv[k] = piv;
+          }
         }
       }
       __syncthreads();
-      const float2 pvv = s_pv[buf];
-      const float piv = pvv.x;
-      const int p = __float_as_int(pvv.y);
-      const float rp = piv != 0.f ? 1.f / piv : 0.f;
+      const int p = __float_as_int(s_pv[buf].y);
       const int pg = p / TT, pi = p % TT;
-      // (2) owners of row p: the pivot row scaled by 1/pivot (entry k: 1/pivot)
-      float q[TT];
-      const bool row_owner = ty == pg;
-      if (row_owner) {
-        get_row<TT>(a, pi, q);
+      // (2) owners of row p stage their whole blocks (static register indices)
+      if (ty == pg) {
+        float4* o = reinterpret_cast<float4*>(s_blk + tx * BLK);
 #pragma unroll
-        for (int jj = 0; jj < TT; ++jj) {
-          q[jj] = (tx * TT + jj == k) ? rp : q[jj] * rp;
-          s_q[buf][tx * TT + jj] = q[jj];
-        }
+        for (int ii = 0; ii < TT; ++ii)
+#pragma unroll
+          for (int g = 0; g < TG; ++g)
+            o[ii * TG + g] = make_float4(a[ii][4 * g], a[ii][4 * g + 1], a[ii][4 * g + 2], a[ii][4 * g + 3]);
         used |= 1u << pi;
       }
       __syncthreads();
-      // rank-1 update of every block; row p is then overwritten with q
-      float f[TT], qq[TT];
+      // rank-1 update of every block (the pivot row has multiplier 0)
+      float f[TT], q[TT];
 #pragma unroll
-      for (int ii = 0; ii < TT; ++ii) f[ii] = s_f[buf][ty * TT + ii];
-#pragma unroll
-      for (int jj = 0; jj < TT; ++jj) qq[jj] = s_q[buf][tx * TT + jj];
+      for (int g = 0; g < TG; ++g) {
+        const float4 fv = reinterpret_cast<const float4*>(s_f[buf])[g * 16 + ty];
+        const float4 qv = reinterpret_cast<const float4*>(s_blk + tx * BLK)[pi * TG + g];
+        f[4 * g] = fv.x; f[4 * g + 1] = fv.y; f[4 * g + 2] = fv.z; f[4 * g + 3] = fv.w;
+        q[4 * g] = qv.x; q[4 * g + 1] = qv.y; q[4 * g + 2] = qv.z; q[4 * g + 3] = qv.w;
+      }
 #pragma unroll
       for (int ii = 0; ii < TT; ++ii)
 #pragma unroll
-        for (int jj = 0; jj < TT; ++jj) a[ii][jj] = fmaf(-f[ii], qq[jj], a[ii][jj]);
-      if (row_owner) set_row<TT>(a, pi, q);
+        for (int jj = 0; jj < TT; ++jj) a[ii][jj] = fmaf(-f[ii], q[jj], a[ii][jj]);
     }
+  }
+  // every row has been a pivot row once: scale it by 1 / its pivot
+#pragma unroll
+  for (int ii = 0; ii < TT; ++ii) {
+    const float pv = s_piv[s_step[ty * TT + ii]];
+    const float sc = pv != 0.f ? 1.f / pv : 0.f;
+#pragma unroll
+    for (int jj = 0; jj < TT; ++jj) a[ii][jj] *= sc;
   }
   // D^{-1}(step(r), p_c) = tableau(r, c): staged, then written column-major
 #pragma unroll

@@ -143,6 +143,24 @@ __device__ __forceinline__ TA warp_transpose_reduce32(TA (&v)[32]) {
   return v[0];
 }
 
+// The same on 16 values: lane l ends with value l % 16 summed over the 16
+// lanes of its half-warp.
+template <typename TA>
+__device__ __forceinline__ TA warp_transpose_reduce16(TA (&v)[16]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 8; s >= 1; s >>= 1) {
+    const bool upper = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const TA send = upper ? v[i] : v[i + s];
+      const TA keep = upper ? v[i + s] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  return v[0];
+}
+
 // One right-hand side: wpc warps (1, 2, 4 or 8) per row chunk, 8 / wpc chunks
 // per CTA; warp w of a chunk sums rows [w ch/wpc, (w+1) ch/wpc) (lane l rows
 // l, l+32, ...), the transposed butterfly leaves column j's sum in lane j, and
@@ -243,95 +261,223 @@ __global__ void __launch_bounds__(256) project_k1v_kernel(int64_t N, int r, int 
   }
 }
 
-// One column, slab form (the preconditioner solve): a warp per 128-row slab
-// (lane l: rows 4l .. 4l+3, one 8- or 16-byte access per rank column), the
-// transposed butterfly leaves the slab's partial of column l in lane l; no
-// CTA-wide reduction. With one slab per node the partial goes straight to the
-// node's slot of P, otherwise to `slab` and project_slab_node_kernel sums the
-// node's slabs (fixed order).
-template <typename TB, typename TR, int RT>
-__global__ void __launch_bounds__(256) project_k1_slab_kernel(int64_t N, int r, const TB* __restrict__ B0,
-                                                              int64_t ldb, const TR* __restrict__ R,
-                                                              double* __restrict__ out) {
-  const int lane = threadIdx.x & 31;
-  const int64_t sl = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (sl * 128 >= N) return;  // whole warp
-  const int64_t row = sl * 128 + 4 * lane;
-  float x[4];
-  load4(R + row, x);
-  float acc[RT];
-#pragma unroll
-  for (int j = 0; j < RT; ++j) {
-    acc[j] = 0.f;
-    if (j < r) {
-      float b[4];
-      load4(B0 + (int64_t)j * ldb + row, b);
-      acc[j] = b[0] * x[0] + b[1] * x[1] + b[2] * x[2] + b[3] * x[3];
-    }
-  }
-  const float t = warp_transpose_reduce32(acc);
-  if (lane < r) out[(size_t)sl * r + lane] = (double)t;
-}
-
-// Sum of the 128-row slab partials of each node of child level c, in slab
-// order within each warp and warp order across the CTA, into the node's first
-// slot of P (the layout of the chunk partials).
-__global__ void __launch_bounds__(256) project_slab_node_kernel(int64_t N, int r, int c,
-                                                                const double* __restrict__ slab,
-                                                                double* __restrict__ P) {
-  __shared__ double part[8][32];
+// ---------------------------------------------------------------------------
+// One right-hand side, low-precision panels (the preconditioner solve of the
+// iterative solvers): the level loop of Alg. 2 in two launches per level.
+// Rows are handled in 1024-row CTAs, a warp per 128-row slab, lane l rows
+// 4l .. 4l+3 (one 8- or 16-byte access per basis column).
+//
+// solve_k1_level_kernel<UPD, PROJ>: with UPD, x(rows) += Y_own W(node) for the
+// update of level cu (W = -K~^{-1}(rows of the node, :) [s_second; s_first],
+// from solve_k1_parent_kernel); with PROJ, the projection of level cp on the
+// updated x (still in registers): per warp the transposed butterfly leaves the
+// slab's partial of basis column j in lane j, and the warps of one part
+// (min(n_p, 1024) rows, n_p = N >> cp) add their partials in FP64 in warp
+// order, so that each node of level cp has max(n_p / 1024, 1) parts.
+// A level kernel reads the own-basis block of level cu and the basis block
+// of level cp once: the update of level c and the projection of level c - 1
+// share one pass over x. Registers are held to 32 for BF16 panels (eight CTAs
+// per SM: the 1024-row CTAs of N = 2^20 then run in one wave).
+template <typename TB, bool UPD, bool PROJ>
+__global__ void __launch_bounds__(256, sizeof(TB) == 2 ? 8 : 6) solve_k1_level_kernel(int64_t N, int r, int cu, const TB* __restrict__ Yu,
+                                                             int64_t ldy, const float* __restrict__ W, int cp,
+                                                             const TB* __restrict__ Vp, int64_t ldv,
+                                                             float* __restrict__ x, double* __restrict__ parts) {
+  __shared__ double sPart[8][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t node = blockIdx.x;
-  const int64_t spn = (N >> c) / 128;  // slabs per node
-  double a = 0.0;
-  if (lane < r)
-    for (int64_t q = warp; q < spn; q += 8) a += slab[(size_t)(node * spn + q) * r + lane];
-  part[warp][lane] = a;
-  __syncthreads();
-  if (warp == 0 && lane < r) {
-    double t = part[0][lane];
+  const int64_t row = (int64_t)blockIdx.x * 1024 + 4 * threadIdx.x;
+  const bool valid = row < N;  // whole warps (N is a multiple of 128)
+  float xv[4] = {0.f, 0.f, 0.f, 0.f};
+  if (valid) load4(x + row, xv);
+  if constexpr (UPD) {
+    const int64_t node = row / (N >> cu);  // one node per warp (nodes of >= 128 rows)
+    const float wl = (valid && lane < r) ? W[node * r + lane] : 0.f;
+    if (valid) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+      for (int j = 0; j < 32; ++j) {
+        if (j < r) {
+          float b[4];
+          load4(Yu + (int64_t)j * ldy + row, b);
+          const float w = __shfl_sync(0xffffffffu, wl, j);
 #pragma unroll
-    for (int w = 1; w < 8; ++w) t += part[w][lane];
-    P[(size_t)node * chunks_per_node(N, c) * r + lane] = t;
+          for (int q = 0; q < 4; ++q) acc[q] = fmaf(b[q], w, acc[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) xv[q] += acc[q];
+      store4(x + row, xv);
+    }
+  }
+  if constexpr (PROJ) {
+    // basis columns in two halves of 16 (16 accumulators live at a time):
+    // a 16-wide transposed butterfly leaves column h*16 + (l % 16) summed over
+    // each half-warp in lane l, and one more exchange adds the two halves
+    float t = 0.f;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float acc[16];
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj) {
+        const int j = h * 16 + jj;
+        acc[jj] = 0.f;
+        if (valid && j < r) {
+          float b[4];
+          load4(Vp + (int64_t)j * ldv + row, b);
+          acc[jj] = b[0] * xv[0] + b[1] * xv[1] + b[2] * xv[2] + b[3] * xv[3];
+        }
+      }
+      float th = warp_transpose_reduce16(acc);
+      th += __shfl_xor_sync(0xffffffffu, th, 16);
+      if ((lane >> 4) == h) t = th;
+    }
+    const int64_t np = N >> cp;
+    const int gw = (int)((np < 1024 ? np : 1024) / 128);  // warps per part
+    if (gw == 1) {
+      if (valid && lane < r) parts[(size_t)(blockIdx.x * 8 + warp) * r + lane] = (double)t;
+    } else {
+      sPart[warp][lane] = (double)t;
+      __syncthreads();
+      if (valid && warp % gw == 0 && lane < r) {
+        double a = sPart[warp][lane];
+        for (int w2 = 1; w2 < gw; ++w2) a += sPart[warp + w2][lane];
+        parts[(size_t)((blockIdx.x * 8 + warp) / gw) * r + lane] = a;
+      }
+    }
   }
 }
 
-// Returns true when it handled level c: the node sums are then in each node's
-// first slot (reduced form).
-template <typename TB, typename TR>
-bool launch_project_k1_slab(int64_t N, int r, int c, const TB* Bas, int64_t ldb, int bas_block, const TR* R,
-                            double* slab, double* P, cudaStream_t s) {
-  if constexpr (!std::is_same<TB, __nv_bfloat16>::value || !std::is_same<TR, float>::value) {
-    return false;
-  } else {
-    const int64_t n = N >> c;
-    if (r > 32 || n % 128 != 0 || ldb % 4 != 0 || reinterpret_cast<uintptr_t>(Bas) % 16 != 0 ||
-        reinterpret_cast<uintptr_t>(R) % 16 != 0)
-      return false;
-    const int64_t spn = n / 128;
-    if (spn > 1 && slab == nullptr) return false;
-    ProfScope prof_(KC_PROJECT, s);
-    note_work(2.0 * (double)N * r + 4.0 * (double)N + 8.0 * (double)(N / 128) * r * (spn > 1 ? 2 : 1),
-              2.0 * N * r);
-    const TB* B0 = Bas + (int64_t)bas_block * r * ldb;
-    const int64_t slabs = N / 128;
-    const unsigned g = (unsigned)((slabs + 7) / 8);
-    if (spn == 1) {
-      // one slab per node, one chunk per node: the slab partial is the node's slot
-      { project_k1_slab_kernel<TB, TR, 32><<<g, 256, 0, s>>>(N, r, B0, ldb, R, P); note_launches(1); }
-    } else {
-      { project_k1_slab_kernel<TB, TR, 32><<<g, 256, 0, s>>>(N, r, B0, ldb, R, slab); note_launches(1); }
-      { project_slab_node_kernel<<<(unsigned)((int64_t)1 << c), 256, 0, s>>>(N, r, c, slab, P); note_launches(1); }
+// One CTA per parent at level c: the children's projections (sums of their
+// ppn parts, fixed order: part q by group q % G of the NT / 32 = G groups,
+// then the groups in order), then W = -K~^{-1} [s_second; s_first]
+// (Eq. e:k; rows 0..r-1 of the right-hand side from the second child) in
+// FP64, rows 0..r-1 for the first child and r..2r-1 for the second, rounded to
+// FP32 for the update. NT = 1024 at the top levels (many parts, few parents),
+// else 256.
+template <int NT>
+__global__ void __launch_bounds__(NT) solve_k1_parent_kernel(int r, int64_t ppn, const double* __restrict__ parts,
+                                                             const double* __restrict__ Kinv,
+                                                             float* __restrict__ W) {
+  constexpr int G = NT / 32;   // part groups
+  constexpr int KP = NT / 64;  // term groups of the K~^{-1} product
+  __shared__ double sSum[G][2][32];
+  __shared__ double sRhs[64];
+  __shared__ double sW[KP][64];
+  const int t = threadIdx.x, lane = t & 31, g = t >> 5;
+  const int64_t p = blockIdx.x;
+  const int n2 = 2 * r;
+  double a0 = 0.0, a1 = 0.0;
+  if (lane < r) {
+    const double* c0 = parts + (size_t)(2 * p) * ppn * r + lane;
+    const double* c1 = parts + (size_t)(2 * p + 1) * ppn * r + lane;
+#pragma unroll 4
+    for (int64_t q = g; q < ppn; q += G) {
+      a0 += c0[(size_t)q * r];
+      a1 += c1[(size_t)q * r];
     }
-    return cudaGetLastError() == cudaSuccess;
+  }
+  sSum[g][0][lane] = a0;
+  sSum[g][1][lane] = a1;
+  __syncthreads();
+  if (t < 64) {
+    const int ch = t >> 5;  // 0: first child, 1: second
+    double s = sSum[0][ch][lane];
+#pragma unroll
+    for (int gg = 1; gg < G; ++gg) s += sSum[gg][ch][lane];
+    if (lane < r) sRhs[ch ? lane : r + lane] = s;  // [s_second; s_first]
+  }
+  __syncthreads();
+  {
+    const int o = t & 63, part = t >> 6;  // output row o of K~^{-1}, terms q = part, part + KP, ...
+    const double* Kj = Kinv + (size_t)p * n2 * n2;
+    double a = 0.0;
+    if (o < n2)
+      for (int q = part; q < n2; q += KP) a += Kj[(size_t)q * n2 + o] * sRhs[q];
+    sW[part][o] = a;
+  }
+  __syncthreads();
+  if (t < n2) {
+    double w = sW[0][t];
+#pragma unroll
+    for (int pp = 1; pp < KP; ++pp) w += sW[pp][t];
+    const int ch = t >= r ? 1 : 0;
+    W[(size_t)(2 * p + ch) * r + (t - ch * r)] = (float)-w;
   }
 }
-template bool launch_project_k1_slab<__nv_bfloat16, float>(int64_t, int, int, const __nv_bfloat16*, int64_t, int,
-                                                          const float*, double*, double*, cudaStream_t);
-template bool launch_project_k1_slab<float, float>(int64_t, int, int, const float*, int64_t, int, const float*,
-                                                  double*, double*, cudaStream_t);
-template bool launch_project_k1_slab<double, double>(int64_t, int, int, const double*, int64_t, int, const double*,
-                                                    double*, double*, cudaStream_t);
+
+size_t solve_k1_parts_elems(const hodlr_desc& d) { return (size_t)(d.N / 128) * d.r; }
+
+template <typename TB>
+bool solve_k1_supported(const Factor& F, const TB* Y, const TB* Vp, int64_t ldvp, const float* x) {
+  const hodlr_desc& d = F.d;
+  return d.r <= 32 && d.m % 128 == 0 && d.N % 4 == 0 && ldvp % 4 == 0 && reinterpret_cast<uintptr_t>(Y) % 16 == 0 &&
+         reinterpret_cast<uintptr_t>(Vp) % 16 == 0 && reinterpret_cast<uintptr_t>(x) % 16 == 0;
+}
+
+template <typename TB>
+cudaError_t launch_solve_k1_level(const hodlr_desc& d, bool upd, bool proj, int cu, const TB* Yu, const float* W,
+                                  int cp, const TB* Vp, int64_t ldv, float* x, double* parts, cudaStream_t s) {
+  const int64_t N = d.N;
+  const int r = d.r;
+  ProfScope prof_(upd ? KC_UPDATE : KC_PROJECT, s);
+  const double pb = proj ? (double)(N / std::min<int64_t>(N >> cp, 1024)) * 8.0 * r : 0.0;
+  note_work((upd ? sizeof(TB) * (double)N * r + 4.0 * N + 4.0 * (double)(1ll << cu) * r : 0.0) +
+                (proj ? sizeof(TB) * (double)N * r : 0.0) + 4.0 * N + pb,
+            (upd ? 2.0 * N * r : 0.0) + (proj ? 2.0 * N * r : 0.0));
+  const unsigned g = (unsigned)((N + 1023) / 1024);
+  if (upd && proj)
+    solve_k1_level_kernel<TB, true, true><<<g, 256, 0, s>>>(N, r, cu, Yu, N, W, cp, Vp, ldv, x, parts);
+  else if (upd)
+    solve_k1_level_kernel<TB, true, false><<<g, 256, 0, s>>>(N, r, cu, Yu, N, W, cp, Vp, ldv, x, parts);
+  else
+    solve_k1_level_kernel<TB, false, true><<<g, 256, 0, s>>>(N, r, cu, Yu, N, W, cp, Vp, ldv, x, parts);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+// Forward solve (Alg. 2 after the leaf stage), one column in FP32 with
+// panels TB: the projection of level L, then per level c = L .. 1 the parent
+// kernel and the level kernel (update of c with the projection of c - 1).
+template <typename TB>
+cudaError_t launch_solve_k1_chain(const Factor& F, const TB* Y, const TB* Vp, int64_t ldvp, float* x,
+                                  double* parts, float* W, cudaStream_t s) {
+  const hodlr_desc& d = F.d;
+  const int64_t N = d.N;
+  const int r = d.r, L = d.L;
+  cudaError_t e;
+  if ((e = launch_solve_k1_level<TB>(d, false, true, 0, nullptr, nullptr, L, Vp + (int64_t)(L - 1) * r * ldvp, ldvp,
+                                     x, parts, s)) != cudaSuccess)
+    return e;
+  for (int c = L; c >= 1; --c) {
+    const int64_t nc = N >> c;
+    const int64_t ppn = nc >= 1024 ? nc / 1024 : 1;
+    {
+      ProfScope prof_(KC_COUPLING_APPLY, s);
+      const int64_t parents = (int64_t)1 << (c - 1);
+      note_work(8.0 * (double)(1ll << c) * ppn * r + 8.0 * parents * 4.0 * r * r + 4.0 * (double)(1ll << c) * r,
+                parents * 2.0 * (2.0 * r) * (2.0 * r));
+      const double* Kc = F.K + F.Koff[c] * 4 * r * r;
+      if (ppn >= 64)
+        solve_k1_parent_kernel<1024><<<(unsigned)parents, 1024, 0, s>>>(r, ppn, parts, Kc, W);
+      else
+        solve_k1_parent_kernel<256><<<(unsigned)parents, 256, 0, s>>>(r, ppn, parts, Kc, W);
+      note_launches(1);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const TB* Yu = Y + (int64_t)(c - 1) * r * N;
+    const TB* Vn = c > 1 ? Vp + (int64_t)(c - 2) * r * ldvp : nullptr;
+    if ((e = launch_solve_k1_level<TB>(d, true, c > 1, c, Yu, W, c - 1, Vn, ldvp, x, parts, s)) != cudaSuccess)
+      return e;
+  }
+  return cudaSuccess;
+}
+template bool solve_k1_supported<__nv_bfloat16>(const Factor&, const __nv_bfloat16*, const __nv_bfloat16*, int64_t,
+                                                const float*);
+template bool solve_k1_supported<float>(const Factor&, const float*, const float*, int64_t, const float*);
+template cudaError_t launch_solve_k1_chain<__nv_bfloat16>(const Factor&, const __nv_bfloat16*, const __nv_bfloat16*,
+                                                         int64_t, float*, double*, float*, cudaStream_t);
+template cudaError_t launch_solve_k1_chain<float>(const Factor&, const float*, const float*, int64_t, float*, double*,
+                                                 float*, cudaStream_t);
 
 int project_k1_warps(int64_t ch) {
   int w = 1;
@@ -529,100 +675,6 @@ __global__ void __launch_bounds__(256) update_k1v_kernel(int64_t N, int r, int c
   for (int q = 0; q < 4; ++q) x[q] += acc[q];
   store4(R + row, x);
 }
-
-// One column, coupling solve fused in (the preconditioner solve after the
-// slab projection): each CTA first forms its node's w = K~^{-1}(rows of the
-// node, :) [s_second; s_first] in FP64 from the node sums in the children's
-// first slots (rows 0..r-1 of the right-hand side from the second child, as
-// in K~ [w_first; w_second] = [s_second; s_first]), then x(rows) -= Y_own w
-// as update_k1v_kernel.
-template <typename TB, typename TR, typename TA>
-__global__ void __launch_bounds__(256) update_k1v_coupled_kernel(int64_t N, int r, int c,
-                                                                 const TB* __restrict__ Bas, int64_t ldb,
-                                                                 int bas_block, TR* __restrict__ R,
-                                                                 const double* __restrict__ P, int64_t pstride,
-                                                                 const double* __restrict__ Kinv) {
-  __shared__ double sRhs[128];
-  __shared__ double sPart[8][64];
-  __shared__ TA sW[64];
-  const int64_t n = N >> c;
-  const int64_t tpn = (n + 1023) / 1024;
-  const int64_t node = blockIdx.x / tpn;
-  const int64_t t0 = (blockIdx.x % tpn) * 1024;
-  const int n2 = 2 * r;
-  const int64_t parent = node >> 1;
-  const int rowoff = (node & 1) ? r : 0;
-  for (int q = threadIdx.x; q < n2; q += 256)
-    sRhs[q] = q < r ? P[(2 * parent + 1) * pstride + q] : P[(2 * parent) * pstride + q - r];
-  __syncthreads();
-  {
-    const int j = threadIdx.x % r, part = threadIdx.x / r;  // r <= 32: 8 parts
-    const int parts = 256 / r;
-    const double* Kj = Kinv + (size_t)parent * n2 * n2;
-    double a = 0.0;
-    if (part < parts && part < 8)
-      for (int q = part; q < n2; q += (parts < 8 ? parts : 8)) a += Kj[(size_t)q * n2 + rowoff + j] * sRhs[q];
-    if (part < 8) sPart[part][j] = a;
-  }
-  __syncthreads();
-  if (threadIdx.x < r) {
-    const int parts = 256 / r < 8 ? 256 / r : 8;
-    double w = 0.0;
-    for (int pp = 0; pp < parts; ++pp) w += sPart[pp][threadIdx.x];
-    sW[threadIdx.x] = conv<TA>(-w);
-  }
-  __syncthreads();
-  const int64_t i = t0 + 4 * threadIdx.x;
-  if (i >= n) return;
-  const int64_t row = node * n + i;
-  const TB* B0 = Bas + (int64_t)bas_block * r * ldb + row;
-  TA acc[4] = {TA(0), TA(0), TA(0), TA(0)};
-#pragma unroll 8
-  for (int j = 0; j < r; ++j) {
-    TA b[4];
-    load4(B0 + (int64_t)j * ldb, b);
-    const TA w = sW[j];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] += b[q] * w;
-  }
-  TA x[4];
-  load4(R + row, x);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) x[q] += acc[q];
-  store4(R + row, x);
-}
-
-template <typename TB, typename TR>
-bool launch_update_k1_coupled(const Factor& F, int c, const TB* Bas, int64_t ldb, int bas_block, TR* R,
-                              const double* P, cudaStream_t s) {
-  const int64_t N = F.d.N;
-  const int r = F.d.r;
-  const int64_t n = N >> c;
-  if (r > 32 || n % 4 != 0 || ldb % 4 != 0 || reinterpret_cast<uintptr_t>(Bas) % 16 != 0 ||
-      reinterpret_cast<uintptr_t>(R) % 16 != 0)
-    return false;
-  ProfScope prof_(KC_UPDATE, s);
-  const int64_t parents = (int64_t)1 << (c - 1);
-  note_work(sizeof(TB) * (double)N * r + 2.0 * sizeof(TR) * (double)N + 8.0 * parents * 4.0 * r * r +
-                8.0 * (double)(1ll << c) * r,
-            2.0 * N * r + parents * 2.0 * (2.0 * r) * (2.0 * r));
-  const int64_t tpn = (n + 1023) / 1024;
-  const unsigned g = (unsigned)(((int64_t)1 << c) * tpn);
-  const int64_t pstride = chunks_per_node(N, c) * (int64_t)r;
-  using TA = typename AccOf<TR>::type;
-  {
-    update_k1v_coupled_kernel<TB, TR, TA><<<g, 256, 0, s>>>(N, r, c, Bas, ldb, bas_block, R, P, pstride,
-                                                            F.K + F.Koff[c] * 4 * r * r);
-    note_launches(1);
-  }
-  return cudaGetLastError() == cudaSuccess;
-}
-template bool launch_update_k1_coupled<__nv_bfloat16, float>(const Factor&, int, const __nv_bfloat16*, int64_t, int,
-                                                            float*, const double*, cudaStream_t);
-template bool launch_update_k1_coupled<float, float>(const Factor&, int, const float*, int64_t, int, float*,
-                                                    const double*, cudaStream_t);
-template bool launch_update_k1_coupled<double, double>(const Factor&, int, const double*, int64_t, int, double*,
-                                                      const double*, cudaStream_t);
 
 template <typename TB, typename TR>
 cudaError_t launch_update(int64_t N, int r, int c, const TB* Bas, int64_t ldb, int bas_block, TR* R, int64_t ldr,

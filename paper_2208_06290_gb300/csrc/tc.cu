@@ -832,17 +832,6 @@ struct LeafTcSmem {
   static constexpr uint32_t kBytes = kBarOff + 64 + 128;
 };
 
-__device__ __forceinline__ uint32_t f64_to_f32_trunc_bits(double x) {
-  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
-  const uint32_t sign = hi & 0x80000000u;
-  const int e = (int)((hi >> 20) & 0x7FFu);
-  const uint32_t mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-  uint32_t bits = sign | ((uint32_t)(e - 896) << 23) | mant;
-  if (e <= 896) bits = sign;                                                 // tiny -> signed zero
-  if (e >= 1151) bits = sign | 0x7F800000u | ((hi & 0xFFFFFu) | lo ? 0x400000u : 0u);  // inf / NaN
-  return bits;
-}
-
 __host__ __device__ constexpr uint32_t idesc_tf32_f32(int M, int N) {
   return (1u << 4)                     // D format: F32
          | (2u << 7)                   // A format: TF32

@@ -124,6 +124,28 @@ def test_gmres_reaches_1e10(cuda_lib, prec):
     assert relres_oracle(Dm, Um, Vm, L, Bm, X.cpu().numpy()) <= 2e-10
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("N,L,r", [(256, 1, 3), (1 << 12, 5, 7), (1 << 14, 7, 32), (1 << 15, 8, 16),
+                                   (1 << 16, 9, 32)])
+def test_one_column_solve_matches_multi_column(cuda_lib, prec, N, L, r):
+    """The one-column preconditioner solve (two launches per level: parent
+    sums + coupling solve, update fused with the next projection; leaves of
+    128 rows, node sizes 128 .. N/2 so parts of one warp up to many CTAs per
+    node) against the general k-column path on the same factor (column 0 of
+    a two-column solve of [b, b]) -- the same FP32 arithmetic in another
+    summation order -- and against the oracle's exact solve at the factor's
+    precision."""
+    hb = cuda_lib
+    (Dm, Um, Vm, Bm), (D, U, V, B) = make_case(N, L, r, seed=13 * N + r, k=1)
+    F = hb.hodlr_factor(D, U, V, L, r, prec)
+    x1 = hb.hodlr_solve(F, B.clone()).cpu().numpy()
+    x2 = hb.hodlr_solve(F, torch.stack([B[:, 0], B[:, 0]]).T).cpu().numpy()  # column-major N x 2
+    assert relerr(x1[:, 0], x2[:, 0]) < 1e-5
+    assert relerr(x1[:, 0], x2[:, 1]) < 1e-5
+    tol = 1e-4 if prec == "fp32" else 5e-2
+    assert relerr(x1, RecursiveHODLR(Dm, Um, Vm, L).solve(Bm)) < tol
+
+
 def test_mixed_solve_adjoint_close_to_oracle(cuda_lib):
     hb = cuda_lib
     N, L, r = 2048, 4, 8
