@@ -211,16 +211,16 @@ size_t solve_partials_bytes(const hodlr_desc& d, int k) {
 // In-place solve on x (N x k, ld ldx) in type TX with the factor's panels TP.
 template <typename TP, typename TX>
 hodlr_status solve_core(const Factor& F, TX* x, int64_t ldx, int k, double* Ps, int trans, cudaStream_t s,
-                        double* slab = nullptr) {
+                        double* parts = nullptr) {
   const hodlr_desc& d = F.d;
   const TP* Y = static_cast<const TP*>(F.Y);
   const TP* Vp = static_cast<const TP*>(F.Vp);
   if (!trans) {
     HODLR_CUDA((launch_leaf_solve<TX, TX>(F, x, ldx, x, ldx, k, 0, s)));
     if constexpr (std::is_same<TX, float>::value && !std::is_same<TP, double>::value) {
-      // one column: two launches per level (parts in the slab region, W in Ps)
-      if (k == 1 && slab && solve_k1_supported<TP>(F, Y, Vp, F.ldvp, x)) {
-        HODLR_CUDA(launch_solve_k1_chain<TP>(F, Y, Vp, F.ldvp, x, slab, reinterpret_cast<float*>(Ps), s));
+      // one column: two launches per level (projection parts in `parts`, W in Ps)
+      if (k == 1 && parts && solve_k1_supported<TP>(F, Y, Vp, F.ldvp, x)) {
+        HODLR_CUDA(launch_solve_k1_chain<TP>(F, Y, Vp, F.ldvp, x, parts, reinterpret_cast<float*>(Ps), s));
         return HODLR_OK;
       }
     }
@@ -251,13 +251,13 @@ hodlr_status solve_any(const Factor& F, double* B, int64_t ldb, int k, void* wor
   double* Ps = static_cast<double*>(work);
   if (F.prec == HODLR_PREC_FP64) return solve_core<double, double>(F, B, ldb, k, Ps, trans, s);
   float* xw = reinterpret_cast<float*>(static_cast<char*>(work) + solve_partials_bytes(d, k));
-  double* slab = k == 1 ? reinterpret_cast<double*>(static_cast<char*>(work) + solve_partials_bytes(d, k) +
+  double* parts = k == 1 ? reinterpret_cast<double*>(static_cast<char*>(work) + solve_partials_bytes(d, k) +
                                                     align_up((size_t)d.N * k * sizeof(float)))
                         : nullptr;
   HODLR_CUDA((launch_copy_cols<float, double>(d.N, k, B, ldb, xw, d.N, s)));
   hodlr_status st = F.prec == HODLR_PREC_FP32
-                        ? solve_core<float, float>(F, xw, d.N, k, Ps, trans, s, slab)
-                        : solve_core<__nv_bfloat16, float>(F, xw, d.N, k, Ps, trans, s, slab);
+                        ? solve_core<float, float>(F, xw, d.N, k, Ps, trans, s, parts)
+                        : solve_core<__nv_bfloat16, float>(F, xw, d.N, k, Ps, trans, s, parts);
   if (st != HODLR_OK) return st;
   HODLR_CUDA((launch_copy_cols<double, float>(d.N, k, xw, d.N, B, ldb, s)));
   return HODLR_OK;
