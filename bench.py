@@ -135,7 +135,44 @@ def make_inputs(w, device, rank=0):
 
 
 # ----------------------------------------------------------------- clocks
+CLOCK_FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+THROTTLE_NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+
+def parse_clock_samples(lines, t0=None, t1=None):
+    """Summarise nvidia-smi CSV lines (CLOCK_FIELDS, noheader, nounits): the
+    median SM clock, the max clock and the active throttle reasons of the
+    samples whose timestamp lies in [t0, t1] (epoch seconds, local time as
+    nvidia-smi prints it); all samples if none does or no window is given."""
+    import datetime
+    rows = []
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 10:
+            continue
+        try:
+            sm, smax = float(parts[2]), float(parts[3])
+        except ValueError:
+            continue
+        try:
+            ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            ts = None  # kept, but cannot be placed in the region
+        rows.append((ts, sm, smax, parts[6:10]))
+    inside = [x for x in rows if t0 is not None and t1 is not None and x[0] is not None and t0 <= x[0] <= t1]
+    use = inside if inside else rows
+    reasons = sorted({n for x in use for n, v in zip(THROTTLE_NAMES, x[3]) if v.lower().startswith("active")})
+    return {"sm_mhz": statistics.median(x[1] for x in use) if use else None,
+            "sm_max_mhz": max(x[2] for x in use) if use else None,
+            "reasons": reasons, "samples": len(use), "samples_in_timed_region": len(inside)}
+
+
 class ClockSampler:
+    """nvidia-smi sampling every 50 ms in the background; start() returns once
+    the first sample is written, so that the timed region is covered."""
+
     def __init__(self, index):
         self.index = index
         self.proc = None
@@ -144,42 +181,30 @@ class ClockSampler:
     def start(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={CLOCK_FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        deadline = time.time() + 5.0
+        while time.time() < deadline and self.proc.poll() is None and os.path.getsize(self.path) == 0:
+            time.sleep(0.02)
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)  # one more sample after the region
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
-            for line in f:
-                parts = [x.strip() for x in line.split(",")]
-                if len(parts) < 9:
-                    continue
-                try:
-                    sm.append(float(parts[1]))
-                    smax.append(float(parts[2]))
-                except ValueError:
-                    continue
-                for n, v in zip(names, parts[5:9]):
-                    if v.lower().startswith("active"):
-                        reasons.add(n)
+            out = parse_clock_samples(f.readlines(), t0, t1)
         os.unlink(self.path)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return out
 
 
 # ----------------------------------------------------------------- native arm
@@ -230,13 +255,15 @@ def run_native(args, w, rank, world):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     barrier()
+    wall0 = time.time()
     e0.record(stream)
     info = [step() for _ in range(args.steps)]
     e1.record(stream)
     barrier()
+    wall1 = time.time()
     hb.hodlr_profile_enable(False)
     launches = hb.hodlr_launch_count() - launches0
-    clocks = sampler.stop()
+    clocks = sampler.stop(wall0, wall1)
     ms = e0.elapsed_time(e1)
     prof = hb.hodlr_profile_read()
     work = hb.hodlr_profile_work()
@@ -430,7 +457,7 @@ def run_reference(args, w, rank, world):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
