@@ -410,7 +410,10 @@ size_t solve_k1_parts_elems(const hodlr_desc& d) { return (size_t)(d.N / 128) * 
 template <typename TB>
 bool solve_k1_supported(const Factor& F, const TB* Y, const TB* Vp, int64_t ldvp, const float* x) {
   const hodlr_desc& d = F.d;
-  return d.r <= 32 && d.m % 128 == 0 && d.N % 4 == 0 && ldvp % 4 == 0 && reinterpret_cast<uintptr_t>(Y) % 16 == 0 &&
+  // leaves of 128 * 2^j rows: every node of every level is a whole number of
+  // 128-row warps, and nodes of 1024 rows or more a whole number of parts
+  return d.r <= 32 && d.m % 128 == 0 && (d.m & (d.m - 1)) == 0 && d.N % 4 == 0 && ldvp % 4 == 0 &&
+         reinterpret_cast<uintptr_t>(Y) % 16 == 0 &&
          reinterpret_cast<uintptr_t>(Vp) % 16 == 0 && reinterpret_cast<uintptr_t>(x) % 16 == 0;
 }
 
