@@ -396,60 +396,72 @@ def run_native(args, w, rank, world):
 
 
 # ----------------------------------------------------------------- oracle (CPU) arm
-def cpu_sample(w):
+def cpu_sample(w, log2_cap=16):
     """Bounded sample of the workload for the CPU oracle: the same leaf size and
-    rank at N = 2^16 (or the full N if smaller)."""
-    N = min(w["N"], 1 << 16)
+    rank at N = 2^log2_cap (or the full N if smaller)."""
+    N = min(w["N"], 1 << log2_cap)
     m = w["N"] >> w["L"]
     L = max(1, int(round(math.log2(N // m))))
     return N, L, w["r"], w["k"]
 
 
-def cpu_baseline(w, steps=1):
-    import numpy as np
-    from oracle import costs as oc
-    from oracle.hodlr import RecursiveHODLR
+def _oracle_inputs(w, log2_cap):
     from synth import HodlrShape, gaussian_rhs, synthetic_hodlr, to_math
-    N, L, r, k = cpu_sample(w)
-    m = N >> L
+    N, L, r, k = cpu_sample(w, log2_cap)
     D, U, V, g = synthetic_hodlr(HodlrShape(N, L, r), w["shift"], w["seed"])
     B = gaussian_rhs(N, k, g)
-    Dm, Um, Vm, Bm = to_math(D, U, V, B)
-    times = []
-    for _ in range(steps):
-        t0 = time.perf_counter()
-        rec = RecursiveHODLR(Dm, Um, Vm, L)
-        rec.solve(Bm)
-        rec.slogdet()
-        times.append(time.perf_counter() - t0)
-    sec = statistics.mean(times)
-    flops = oc.loop_factor_flops(N, m, r, L) + oc.loop_solve_flops(N, m, r, L, k)
-    return {"value": flops / sec / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
-            "seconds": sec,
-            "sample": f"FP64 recursive oracle (numpy/LAPACK) factor+solve+slogdet at N={N}, leaf {m}, rank {r}, "
-                      f"{k} RHS (same leaf and rank as the workload, N reduced to bound CPU time)"}
+    return (N, L, r, k), to_math(D, U, V, B)
+
+
+def _oracle_step(shape, mats):
+    """One pass of the oracle (factor + solve + slogdet); returns seconds."""
+    from oracle.hodlr import RecursiveHODLR
+    N, L, r, k = shape
+    Dm, Um, Vm, Bm = mats
+    t0 = time.perf_counter()
+    rec = RecursiveHODLR(Dm, Um, Vm, L)
+    rec.solve(Bm)
+    rec.slogdet()
+    return time.perf_counter() - t0
+
+
+def _oracle_flops(shape):
+    from oracle import costs as oc
+    N, L, r, k = shape
+    m = N >> L
+    return oc.loop_factor_flops(N, m, r, L) + oc.loop_solve_flops(N, m, r, L, k)
+
+
+def _sample_text(shape):
+    N, L, r, k = shape
+    return (f"FP64 recursive oracle (numpy/LAPACK) factor+solve+slogdet at N={N}, leaf {N >> L}, rank {r}, "
+            f"{k} RHS (same leaf and rank as the workload, N reduced to bound CPU time)")
+
+
+def cpu_baseline(w, steps=1):
+    shape, mats = _oracle_inputs(w, 16)
+    sec = statistics.mean(_oracle_step(shape, mats) for _ in range(steps))
+    return {"value": _oracle_flops(shape) / sec / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
+            "kind": "oracle", "seconds": sec, "sample": _sample_text(shape)}
 
 
 def run_reference(args, w, rank, world):
+    """The oracle as it stands on the host cores, on the same workload's
+    bounded sample (N = 2^15 per step, inputs generated once), so that the
+    default warm-up + timed steps end within a few minutes."""
     if rank != 0:
         return
-    times = []
-    for i in range(args.warmup + args.steps):
-        b = cpu_baseline(w, steps=1)
-        if i >= args.warmup:
-            times.append(b["seconds"])
-    sec = statistics.mean(times)
-    N, L, r, k = cpu_sample(w)
-    m = N >> L
-    from oracle import costs as oc
-    flops = oc.loop_factor_flops(N, m, r, L) + oc.loop_solve_flops(N, m, r, L, k)
-    val = flops / sec / 1e12
+    shape, mats = _oracle_inputs(w, 15)
+    for _ in range(args.warmup):
+        _oracle_step(shape, mats)
+    sec = statistics.mean(_oracle_step(shape, mats) for _ in range(args.steps))
+    val = _oracle_flops(shape) / sec / 1e12
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "description": w["desc"], "cpu_sample_N": N},
+            "config": {"workload": args.workload, "description": w["desc"], "cpu_sample_N": shape[0]},
             "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": b["sample"]},
+                             "sample": _sample_text(shape)},
             "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
