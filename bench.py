@@ -134,6 +134,24 @@ def make_inputs(w, device, rank=0):
     return D, U, V, B
 
 
+# ------------------------------------------------------- replicas (N > 1)
+def max_over_ranks(x, world, device):
+    """The largest per-rank value over the job (the rank's own when alone):
+    the slowest replica sets the job's time."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_tflops(flops_per_rank, world, seconds):
+    """Whole-job throughput of `world` independent replicas, each doing
+    flops_per_rank in the slowest rank's `seconds`."""
+    return world * flops_per_rank / seconds / 1e12
+
+
 # ----------------------------------------------------------------- clocks
 CLOCK_FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -267,10 +285,7 @@ def run_native(args, w, rank, world):
     ms = e0.elapsed_time(e1)
     prof = hb.hodlr_profile_read()
     work = hb.hodlr_profile_work()
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, dev)
     sec_step = ms_max / 1e3 / args.steps
     iters = [i[0] for i in info]
     relres = [i[1] for i in info]
@@ -329,10 +344,8 @@ def run_native(args, w, rank, world):
         c1.record(stream)
         barrier()
         s_e2e = c0.elapsed_time(c1) / 1e3 / n_e2e
-        te = torch.tensor([s_e2e], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * flops / float(te.item()) / 1e12, "unit": "TFLOP/s", "seconds": float(te.item()),
+        s_e2e_max = max_over_ranks(s_e2e, world, dev)
+        e2e = {"value": job_tflops(flops, world, s_e2e_max), "unit": "TFLOP/s", "seconds": s_e2e_max,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # roofline of every kernel class, from the live CUDA-event brackets; the
@@ -369,7 +382,7 @@ def run_native(args, w, rank, world):
     share = {c: round(prof[c][0] / max(sum(v[0] for v in prof.values()), 1e-9), 4) for c in prof if prof[c][1]}
 
     line = {
-        "metric": METRIC, "value": world * flops / sec_step / 1e12, "unit": "TFLOP/s", "n_gpus": world,
+        "metric": METRIC, "value": job_tflops(flops, world, sec_step), "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_step * 1e3, "seconds_per_step": sec_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16" if prec == "bf16" else ("f32" if prec == "fp32" else "f64"),
