@@ -44,12 +44,15 @@ WORKLOADS = {
                                       "case of the same structure, for profiler captures)"),
     "synthetic-4096": dict(N=4096, L=6, r=16, k=1, prec="fp64", solver="direct", shift=4.0, seed=0,
                            data="synthetic", desc="synthetic HODLR N=4096, leaf 64, rank 16, FP64"),
-    "gaussian-2^18": dict(N=1 << 18, L=10, r=64, k=16, prec="fp32", solver="refine", shift=0.0, seed=1,
+    "gaussian-2^18": dict(N=1 << 18, L=10, r=64, k=16, prec="fp32", solver="refine", restart=30, shift=0.0, seed=1,
                           data="gaussian", desc="Gaussian kernel (sigma 0.1, nugget 1e-2) on 2^18 kd-ordered points "
-                                                "in [0,1]^2, leaf 256, rank 64, 16 RHS; FP32 factor + refinement"),
-    "matern-2^20": dict(N=1 << 20, L=12, r=64, k=32, prec="fp32", solver="refine", shift=0.0, seed=3,
+                                                "in [0,1]^2, leaf 256, rank 64, 16 RHS; FP32 factor + refinement, "
+                                                "FGMRES(30) when refinement stalls"),
+    "matern-2^20": dict(N=1 << 20, L=12, r=64, k=32, prec="fp32", solver="refine", restart=30, shift=0.0, seed=3,
+                        grad=True,
                         data="matern", desc="Matern-3/2 kernel (lengthscale 0.2, nugget 1e-3) on 2^20 kd-ordered "
-                                            "points in [0,1]^3, leaf 256, rank 64, 32 RHS; FP32 factor + refinement"),
+                                            "points in [0,1]^3, leaf 256, rank 64, 32 RHS; FP32 factor + refinement, "
+                                            "FGMRES(30) when refinement stalls"),
     "synthetic-2^23": dict(N=1 << 23, L=15, r=32, k=64, prec="bf16", solver="refine", shift=8.0, seed=4,
                            data="synthetic", desc="synthetic HODLR N=2^23, leaf 256, rank 32, 64 RHS; BF16 "
                                                   "factor + refinement to 1e-10"),
@@ -83,11 +86,11 @@ def fp32_peak_tflops(sm_mhz):
 
 
 # DRAM traffic / algorithmic bytes of each kernel class, from one ncu capture
-# of the current kernels on the BIE N=2^17 case (profiles/*_bie-2^17.md; DRAM
-# read + write over the launcher's algorithmic bytes). The bench scales its
-# per-launch algorithmic bytes by this ratio for `roofline.traffic` (the
-# traffic of these kernels grows in proportion to the units processed). A
-# class whose kernel changes loses its entry until it is captured again.
+# of the current kernels (DRAM read + write over the launcher's algorithmic
+# bytes). The bench scales its per-launch algorithmic bytes by this ratio for
+# `roofline.traffic` (the traffic of these kernels grows in proportion to the
+# units processed). A class whose kernel changes loses its entry until it is
+# captured again.
 TRAFFIC_RATIO = {
     "matvec": (336.6 + 5.1 + 471.4 + 3.2) / (336.5 + 471.9),   # mv1_leaf_project16 + mv1_leaf_apply
     "project_tc": (75.5 + 2.0) / 74.4,                          # project_tc_kernel, level 7
@@ -95,7 +98,7 @@ TRAFFIC_RATIO = {
 }
 
 
-def class_bound(cls, prec):
+def class_bound(cls, prec, m=128):
     """Resource that bounds each kernel class of the library's profiler:
     'hbm' (bytes), 'alu64' / 'alu32' (flops on the FP64 / FP32 pipes)."""
     if cls in ("vector", "reduce_chunks", "logdet"):
@@ -107,31 +110,65 @@ def class_bound(cls, prec):
     if cls == "coupling":
         return "alu64"
     if cls == "leaf_lu":
-        return "alu32"
+        # leaves of 65..128 rows: blocked Gauss-Jordan with tensor-core updates
+        return "hbm" if 64 < m <= 128 else "alu32"
     if prec == "fp32" and cls in ("leaf_solve", "project", "update", "coupling_apply"):
         return "alu32"
     return "hbm"
 
 
 # ----------------------------------------------------------------- inputs
-def make_inputs(w, device, rank=0):
+def reduced(w, log2_cap):
+    """The workload with N reduced to at most 2^log2_cap (same leaf, rank,
+    right-hand sides, operator family and seed): the bounded sample the CPU
+    oracle is timed on."""
+    N = min(w["N"], 1 << log2_cap)
+    m = w["N"] >> w["L"]
+    out = dict(w)
+    out["N"], out["L"] = N, max(1, int(round(math.log2(N // m))))
+    return out
+
+
+def make_inputs(w, device, rank=0, stats=None):
     import torch
     from synth import HodlrShape, gaussian_rhs, synthetic_hodlr
     shape = HodlrShape(w["N"], w["L"], w["r"])
     if w["data"] in ("bie", "gaussian", "matern"):
         from synth.kernels import bie_hodlr, kernel_hodlr
         if w["data"] == "bie":
-            D, U, V = bie_hodlr(shape, device=device, seed=w["seed"])
+            D, U, V = bie_hodlr(shape, device=device, seed=w["seed"], stats=stats)
         elif w["data"] == "gaussian":
-            D, U, V, _ = kernel_hodlr(shape, 2, "gaussian", 0.1, 1e-2, device=device, seed=w["seed"])
+            D, U, V, _ = kernel_hodlr(shape, 2, "gaussian", 0.1, 1e-2, device=device, seed=w["seed"], stats=stats)
         else:
-            D, U, V, _ = kernel_hodlr(shape, 3, "matern32", 0.2, 1e-3, device=device, seed=w["seed"])
+            D, U, V, _ = kernel_hodlr(shape, 3, "matern32", 0.2, 1e-3, device=device, seed=w["seed"], stats=stats)
         g = torch.Generator(device=device)
         g.manual_seed(w["seed"] + 1000 * rank)
     else:
         D, U, V, g = synthetic_hodlr(shape, w["shift"], w["seed"] + 1000 * rank, device=device)
     B = gaussian_rhs(w["N"], w["k"], g, device=device)
     return D, U, V, B
+
+
+def cpu_model():
+    """Host CPU model as the kernel reports it (x86 'model name'; on Arm the
+    implementer/part pair when lscpu is absent)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+        for key in ("model name", "CPU part"):
+            for line in info.splitlines():
+                if line.startswith(key):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 # ------------------------------------------------------- replicas (N > 1)
@@ -234,9 +271,11 @@ def run_native(args, w, rank, world):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
+    hb.hodlr_coupling_fp64_enable(args.coupling_fp64)
     N, L, r, k = w["N"], w["L"], w["r"], w["k"]
     m = N >> L
-    D, U, V, B = make_inputs(w, dev, rank)
+    gen_stats = {}
+    D, U, V, B = make_inputs(w, dev, rank, stats=gen_stats)
     X = torch.empty(k, N, dtype=torch.float64, device=dev).T
     flops = costs.factor_flops(N, m, r, L) + costs.solve_flops(N, m, r, L, k)
     prec = w["prec"]
@@ -249,13 +288,14 @@ def run_native(args, w, rank, world):
                                              raise_on_fail=False)
         elif w["solver"] == "refine":
             _, it, rr, code = hb.hodlr_solve_refined(F, D, U, V, B, tol=1e-10, max_iter=50, X=X,
-                                                     raise_on_fail=False)
+                                                     raise_on_fail=False, restart=w.get("restart", 0),
+                                                     gmres_max_iter=300)
         else:
             X.copy_(B)
             hb.hodlr_solve(F, X)
             it, rr, code = 0, None, 0
         sign, ld = hb.hodlr_logdet(F)
-        return it, rr, code, ld
+        return it, rr, code, sign, ld
 
     def barrier():
         if world > 1:
@@ -265,10 +305,9 @@ def run_native(args, w, rank, world):
     for _ in range(args.warmup):
         step()
     barrier()
+    # timed region: library profiler off (no per-launch events inside)
     sampler = ClockSampler(dev.index)
     sampler.start()
-    hb.hodlr_profile_reset()
-    hb.hodlr_profile_enable(True)
     launches0 = hb.hodlr_launch_count()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -279,31 +318,43 @@ def run_native(args, w, rank, world):
     e1.record(stream)
     barrier()
     wall1 = time.time()
-    hb.hodlr_profile_enable(False)
     launches = hb.hodlr_launch_count() - launches0
     clocks = sampler.stop(wall0, wall1)
     ms = e0.elapsed_time(e1)
-    prof = hb.hodlr_profile_read()
-    work = hb.hodlr_profile_work()
     ms_max = max_over_ranks(ms, world, dev)
     sec_step = ms_max / 1e3 / args.steps
     iters = [i[0] for i in info]
     relres = [i[1] for i in info]
+    sign_mixed, ld_mixed = info[-1][3], info[-1][4]
+    x_mixed = X.clone()
     # relres measured independently of the solver's own report
     res = hb.hodlr_matvec(D, U, V, L, r, X)
     res.sub_(B).neg_()
     rel_true = float((res.norm(dim=0) / B.norm(dim=0)).max().item())
 
+    # per-kernel-class times: a separate pass of the same steps with the
+    # library's per-launch CUDA-event brackets on (launching stream)
+    nprof = max(1, min(args.steps, 5))
+    hb.hodlr_profile_reset()
+    hb.hodlr_profile_enable(True)
+    for _ in range(nprof):
+        step()
+    hb.hodlr_profile_enable(False)
+    prof = hb.hodlr_profile_read()
+    work = hb.hodlr_profile_work()
+
     # plain FP64 factor + solve on the same inputs
     fp64 = None
+    err_vs_fp64 = {}
     if not args.no_fp64:
         Xf = torch.empty_like(X)
+        ld64 = [None, None]
 
         def step64():
             F64 = hb.hodlr_factor(D, U, V, L, r, "fp64")
             Xf.copy_(B)
             hb.hodlr_solve(F64, Xf)
-            hb.hodlr_logdet(F64)
+            ld64[0], ld64[1] = hb.hodlr_logdet(F64)
 
         step64()
         barrier()
@@ -320,7 +371,16 @@ def run_native(args, w, rank, world):
         r64.sub_(B).neg_()
         fp64 = {"seconds": s64, "tflops": flops / s64 / 1e12,
                 "relres": float((r64.norm(dim=0) / B.norm(dim=0)).max().item()),
+                "logdet": ld64[1], "sign": ld64[0],
                 "speedup_of_mixed": s64 / sec_step}
+        dx = (x_mixed - Xf)
+        err_vs_fp64 = {
+            "x_rel_err_vs_fp64": float((dx.norm(dim=0) / Xf.norm(dim=0)).max().item()),
+            "x_max_abs_err_vs_fp64_over_max_abs": float((dx.abs().max() / Xf.abs().max()).item()),
+            "logdet_mixed": ld_mixed, "logdet_fp64": ld64[1],
+            "logdet_rel_err_vs_fp64": abs(ld_mixed - ld64[1]) / max(abs(ld64[1]), 1e-300),
+            "sign_matches_fp64": sign_mixed == ld64[0],
+        }
 
     # end to end through the C ABI from pinned host buffers
     e2e = None
@@ -348,37 +408,90 @@ def run_native(args, w, rank, world):
         e2e = {"value": job_tflops(flops, world, s_e2e_max), "unit": "TFLOP/s", "seconds": s_e2e_max,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
-    # roofline of every kernel class, from the live CUDA-event brackets; the
-    # line's roofline is the dominant (longest) class
+    # adjoint solve B <- A^{-T} B with a factor of the step's precision, timed alone
+    def timed(fn, n):
+        fn()
+        barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(n):
+            fn()
+        t1.record(stream)
+        barrier()
+        return t0.elapsed_time(t1) / 1e3 / n
+
+    Fa = hb.hodlr_factor(D, U, V, L, r, prec)
+    Xa = torch.empty_like(X)
+
+    def adj():
+        Xa.copy_(B)
+        hb.hodlr_solve_adjoint(Fa, Xa)
+
+    adjoint = {"seconds": timed(adj, 3), "rhs": k, "factor_precision": prec,
+               "bytes_per_solve_min": costs.solve_bytes(N, m, r, L, k, prec)}
+    adjoint["achieved_gbs"] = adjoint["bytes_per_solve_min"] / adjoint["seconds"] / 1e9
+    del Fa, Xa
+    grad = None
+    if w.get("grad") and not args.no_fp64:
+        # backward of loss = sum b^T A^{-1} b + log|det A| (hodlr_grad) on an FP32
+        # factor, and its error against the FP64 factor's gradient (untimed)
+        F32 = hb.hodlr_factor(D, U, V, L, r, "fp32")
+        g32 = [None]
+
+        def back32():
+            g32[0] = hb.hodlr_grad(F32, U, V, B, want_loss=False)
+
+        t_grad = timed(back32, 2)
+        del F32
+        F64 = hb.hodlr_factor(D, U, V, L, r, "fp64")
+        g64 = hb.hodlr_grad(F64, U, V, B, want_loss=False)
+        del F64
+        names = ("dD", "dU", "dV", "dB")
+        grad = {"seconds": t_grad, "factor_precision": "fp32", "rhs": k,
+                "rel_err_vs_fp64": {n: float(((a - b).norm() / b.norm()).item())
+                                    for n, a, b in zip(names, g32[0][1:], g64[1:])}}
+        del g32, g64
+        torch.cuda.empty_cache()
+
+    # FP64 pipe rate of this GPU, measured by the library's register-only
+    # FMA probe (CUDA events on the launching stream, best of three)
     pk = peaks()
     sm_mhz = clocks.get("sm_mhz") or 1920.0
+    fp64_meas = measure_fp64_tflops(hb, dev, stream)
 
+    # roofline of every kernel class, from the profiled pass's CUDA-event
+    # brackets; the line's roofline is the dominant (longest) class
     def roof_of(cls):
         cms, cn = prof[cls]
         cbytes, cflops = work[cls]
-        bound = class_bound(cls, prec)
+        bound = class_bound(cls, prec, m)
         if bound == "hbm":
             ach, peak, unit = cbytes / (cms / 1e3) / 1e9, pk["hbm_gbs"], "GB/s"
             src = f"MEASURED_PEAKS.json hbm_gbs ({pk['source']})"
+        elif bound == "alu64":
+            ach, unit = cflops / (cms / 1e3) / 1e12, "TFLOP/s"
+            peak = fp64_meas["tflops"]
+            src = (f"measured FP64 FMA probe: {fp64_meas['fmas']:.3e} FMA in {fp64_meas['ms']:.3f} ms "
+                   f"(nominal {FP64_FLOP_PER_CLK_PER_SM:g} flop/clk/SM x 152 SMs x {sm_mhz:.0f} MHz = "
+                   f"{fp64_peak_tflops(sm_mhz):.4f} TFLOP/s)")
         else:
-            per_clk = FP64_FLOP_PER_CLK_PER_SM if bound == "alu64" else FP32_FLOP_PER_CLK_PER_SM
-            ach = cflops / (cms / 1e3) / 1e12
-            peak = fp64_peak_tflops(sm_mhz) if bound == "alu64" else fp32_peak_tflops(sm_mhz)
-            unit = "TFLOP/s"
-            src = f"{'FP64' if bound == 'alu64' else 'FP32'} pipe {per_clk:g} flop/clk/SM x 152 SMs x median " \
-                  f"{sm_mhz:.0f} MHz"
+            ach, unit = cflops / (cms / 1e3) / 1e12, "TFLOP/s"
+            peak = fp32_peak_tflops(sm_mhz)
+            src = f"FP32 pipe {FP32_FLOP_PER_CLK_PER_SM:g} flop/clk/SM x 152 SMs x median {sm_mhz:.0f} MHz"
         traffic = TRAFFIC_RATIO[cls] * cbytes / max(cn, 1) if cls in TRAFFIC_RATIO and prec == "bf16" else None
         return {"bound": "hbm" if bound == "hbm" else "alu", "pipe": bound, "kernel": cls, "achieved": ach,
                 "peak": peak, "unit": unit, "frac": ach / peak, "traffic": traffic, "peak_source": src,
-                "launches_in_region": cn, "avg_launch_us": cms * 1e3 / max(cn, 1),
+                "launches_in_profiled_pass": cn, "avg_launch_us": cms * 1e3 / max(cn, 1),
                 "bytes_per_launch": cbytes / max(cn, 1), "flops_per_launch": cflops / max(cn, 1),
-                "ms": cms / args.steps}
+                "ms": cms / nprof, "hbm_frac": (cbytes / (cms / 1e3) / 1e9) / pk["hbm_gbs"]}
 
     active = [c for c in prof if prof[c][1] and prof[c][0] > 0]
     dom = max(active, key=lambda c: prof[c][0])
     roof = roof_of(dom)
     classes = {c: {k2: (round(v, 4) if isinstance(v, float) else v) for k2, v in roof_of(c).items()
-                   if k2 in ("pipe", "ms", "launches_in_region", "achieved", "unit", "frac")} for c in active}
+                   if k2 in ("pipe", "ms", "launches_in_profiled_pass", "achieved", "unit", "frac", "hbm_frac")}
+               for c in active}
     share = {c: round(prof[c][0] / max(sum(v[0] for v in prof.values()), 1e-9), 4) for c in prof if prof[c][1]}
 
     line = {
@@ -389,14 +502,23 @@ def run_native(args, w, rank, world):
         "data": "synthetic",
         "config": {"workload": args.workload, "description": w["desc"], "N": N, "leaf": m, "levels": L, "rank": r,
                    "rhs": k, "factor_precision": prec,
-                   "coupling_precision": "fp64",
+                   "coupling_precision": "fp64 elimination; "
+                                         + ("fp64" if (args.coupling_fp64 or prec != "bf16") else "fp32")
+                                         + " products of S and of the explicit inverse",
                    "residual_precision": "fp64", "solver": w["solver"], "tol": 1e-10,
                    "flops_per_step": flops, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (D, U, V = %.1f GB FP64)" % (8.0 * (m * N + 2 * r * N * L) / 1e9)},
-        "mixed": {"iterations": iters, "relres_reported": relres, "relres_fp64_matvec": rel_true},
+                   "l2": "inputs larger than L2 (D, U, V = %.1f GB FP64)" % (8.0 * (m * N + 2 * r * N * L) / 1e9),
+                   "kernel_classes_from": f"separate profiled pass of {nprof} steps after the timed region",
+                   "restart": w.get("restart", 30 if w["solver"] == "gmres" else 0),
+                   "compression_rel_err_by_level": {str(c): float(f"{e:.3g}") for c, e in
+                                                    gen_stats.get("compression_rel_err", {}).items()}},
+        "mixed": {"iterations": iters, "relres_reported": relres, "relres_fp64_matvec": rel_true, **err_vs_fp64},
         "fp64": fp64,
         "e2e": e2e,
+        "adjoint": adjoint,
+        "grad": grad,
         "roofline": roof,
+        "fp64_pipe_measured": fp64_meas,
         "kernel_time_share": share,
         "kernel_classes": classes,
         "gpu_launches": launches,
@@ -408,22 +530,34 @@ def run_native(args, w, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def measure_fp64_tflops(hb, dev, stream, iters=8192, blocks_per_sm=4):
+    """FP64 FMA rate of this GPU from the library's register-only probe: best
+    of three launches after one warm-up, timed with CUDA events on `stream`."""
+    import torch
+    out = torch.zeros(1, dtype=torch.float64, device=dev)
+    best = None
+    for rep in range(4):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fmas = hb.hodlr_probe_fp64_fma(iters, blocks_per_sm, out)
+        b.record(stream)
+        b.synchronize()
+        t = a.elapsed_time(b)
+        if rep and (best is None or t < best):
+            best = t
+    return {"tflops": 2.0 * fmas / (best / 1e3) / 1e12, "fmas": float(fmas), "ms": best,
+            "blocks_per_sm": blocks_per_sm, "chains_per_thread": 8}
+
+
 # ----------------------------------------------------------------- oracle (CPU) arm
-def cpu_sample(w, log2_cap=16):
-    """Bounded sample of the workload for the CPU oracle: the same leaf size and
-    rank at N = 2^log2_cap (or the full N if smaller)."""
-    N = min(w["N"], 1 << log2_cap)
-    m = w["N"] >> w["L"]
-    L = max(1, int(round(math.log2(N // m))))
-    return N, L, w["r"], w["k"]
-
-
 def _oracle_inputs(w, log2_cap):
-    from synth import HodlrShape, gaussian_rhs, synthetic_hodlr, to_math
-    N, L, r, k = cpu_sample(w, log2_cap)
-    D, U, V, g = synthetic_hodlr(HodlrShape(N, L, r), w["shift"], w["seed"])
-    B = gaussian_rhs(N, k, g)
-    return (N, L, r, k), to_math(D, U, V, B)
+    """The workload's operator family at N = 2^log2_cap (same leaf, rank and
+    right-hand sides), generated on the host, as the oracle's numpy arrays."""
+    from synth import to_math
+    ws = reduced(w, log2_cap)
+    D, U, V, B = make_inputs(ws, "cpu", 0)
+    return (ws["N"], ws["L"], ws["r"], ws["k"]), to_math(D, U, V, B), ws["data"]
 
 
 def _oracle_step(shape, mats):
@@ -445,17 +579,27 @@ def _oracle_flops(shape):
     return oc.loop_factor_flops(N, m, r, L) + oc.loop_solve_flops(N, m, r, L, k)
 
 
-def _sample_text(shape):
+def _sample_text(shape, data):
     N, L, r, k = shape
-    return (f"FP64 recursive oracle (numpy/LAPACK) factor+solve+slogdet at N={N}, leaf {N >> L}, rank {r}, "
-            f"{k} RHS (same leaf and rank as the workload, N reduced to bound CPU time)")
+    return (f"FP64 recursive oracle (numpy/LAPACK) factor+solve+slogdet of the {data} operator at N={N}, "
+            f"leaf {N >> L}, rank {r}, {k} RHS (same operator family, leaf and rank as the workload, N reduced "
+            f"to bound CPU time)")
+
+
+def _oracle_threads():
+    """Threads the oracle's BLAS / LAPACK calls may use (numpy's thread pool
+    follows the process's CPU affinity)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
 
 
 def cpu_baseline(w, steps=1):
-    shape, mats = _oracle_inputs(w, 16)
+    shape, mats, data = _oracle_inputs(w, 16)
     sec = statistics.mean(_oracle_step(shape, mats) for _ in range(steps))
-    return {"value": _oracle_flops(shape) / sec / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
-            "kind": "oracle", "seconds": sec, "sample": _sample_text(shape)}
+    return {"value": _oracle_flops(shape) / sec / 1e12, "unit": "TFLOP/s", "cores": _oracle_threads(),
+            "cpu_model": cpu_model(), "kind": "oracle", "seconds": sec, "sample": _sample_text(shape, data)}
 
 
 def run_reference(args, w, rank, world):
@@ -464,7 +608,7 @@ def run_reference(args, w, rank, world):
     default warm-up + timed steps end within a few minutes."""
     if rank != 0:
         return
-    shape, mats = _oracle_inputs(w, 15)
+    shape, mats, data = _oracle_inputs(w, 15)
     for _ in range(args.warmup):
         _oracle_step(shape, mats)
     sec = statistics.mean(_oracle_step(shape, mats) for _ in range(args.steps))
@@ -473,8 +617,8 @@ def run_reference(args, w, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "description": w["desc"], "cpu_sample_N": shape[0]},
-            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": _sample_text(shape)},
+            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": _oracle_threads(), "cpu_model": cpu_model(),
+                             "kind": "oracle", "sample": _sample_text(shape, data)},
             "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -489,6 +633,8 @@ def main(argv=None):
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--coupling-fp64", action="store_true",
+                    help="BF16 factor: form the coupling products in FP64 (precision experiment)")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "native":
         ap.error("--warmup must be >= 3")

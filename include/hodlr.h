@@ -173,10 +173,16 @@ HODLR_API hodlr_status hodlr_matvec(const hodlr_desc* desc, const double* D, con
  * same FP64 Y = A X with the same kernels, but takes its scratch from one
  * fixed 32 MiB array of device memory defined by the library itself (every
  * GPU that loads the library holds it until the process exits) instead of a
- * caller workspace; it calls no allocator. The scratch needed is
- * hodlr_matvec_workspace_size(desc, k); larger problems are rejected with
- * HODLR_ERR_SCRATCH_LIMIT before anything is enqueued. The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) with
+ * caller workspace; it calls no allocator. The limit it enforces is on the
+ * per-level projection partials: max over child levels c of
+ * chunks(c) * r * k doubles must fit in 32 MiB, where chunks(c) = N / ch(c)
+ * and ch(c) is the node size N / 2^c halved until it is at most 1024 rows;
+ * larger problems are rejected with HODLR_ERR_SCRATCH_LIMIT before anything
+ * is enqueued. That bound is the minimum of hodlr_matvec_workspace_size; with
+ * k = 1 the four-launch one-column path runs only when its larger scratch
+ * (the size hodlr_matvec_workspace_size(desc, 1) reports) also fits, else the
+ * general per-level path runs (same result). The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with
  * that device current; make that first call before any stream capture. All
  * calls share the array: calls that overlap on the GPU race and must be
  * serialized by the caller. Nothing in the scratch needs to start at zero. */
@@ -187,24 +193,38 @@ HODLR_API hodlr_status hodlr_matvec_noalloc(const hodlr_desc* desc, const double
 /* ------------------------------------------------------- refined solvers --
  * Mixed-precision solves recovered to FP64 accuracy. The factor f (any
  * precision) of the HODLR matrix (desc, D, U, V) is the preconditioner; the
- * residual uses the FP64 hodlr_matvec on the unfactored D, U, V.
+ * residual uses the FP64 hodlr_matvec on the unfactored D, U, V. The k
+ * right-hand sides advance together: every correction or inner iteration
+ * applies the factor to all k columns in one k-column solve and the FP64
+ * operator in one k-column matvec.
  *
  * hodlr_solve_refined: iterative refinement, X <- X + f^{-1}(B - A X),
  *   starting from X = f^{-1} B, until max_j |b_j - A x_j| / |b_j| <= tol or
- *   max_iter corrections. Stops early when the residual grows twice in a row.
+ *   max_iter corrections; it stops early when the residual grows twice in a
+ *   row. If tol is not reached then and restart > 0, flexible GMRES(restart)
+ *   continues from the refined X for at most gmres_max_iter inner iterations
+ *   (restart = 0: no continuation; the workspace then holds no Krylov basis).
  * hodlr_gmres: flexible GMRES (restart length `restart`, at most max_iter
- *   inner iterations in total, per column) right-preconditioned by f, started
- *   from X = f^{-1} B, stopping on the true FP64 residual <= tol.
+ *   inner iterations in total) right-preconditioned by f, started from
+ *   X = f^{-1} B, stopping on the FP64 residual <= tol. Per cycle the residual
+ *   is b - A x of the first iterate (one FP64 matvec) and then r - (A Z) y
+ *   from the stored FP64 products A z_i. Classical Gram-Schmidt twice, per
+ *   column; a column whose residual estimate has converged stops extending
+ *   its basis while the others continue.
  * Both write the solution to X (N x k, ldx), leave B unchanged, return
  * HODLR_ERR_NOT_CONVERGED if tol was not reached, report the iteration count
- * (refinement corrections or total GMRES inner iterations) in *iters and the
+ * (refinement corrections plus FGMRES inner iterations) in *iters and the
  * final max relative residual in *relres. They synchronize the stream once per
  * iteration to read residual norms.
+ * Workspace: hodlr_refine_workspace_size(f, k, restart) (restart 0 for
+ * refinement without FGMRES continuation; 1 <= restart <= 200 otherwise);
+ * FGMRES holds 3 * restart + 2 vectors of N x k doubles.
  */
 HODLR_API hodlr_status hodlr_refine_workspace_size(hodlr_factor_t f, int32_t k, int32_t restart, size_t* bytes);
 HODLR_API hodlr_status hodlr_solve_refined(hodlr_factor_t f, const double* D, const double* U, const double* V,
                                  const double* B, int64_t ldb, double* X, int64_t ldx, int32_t k,
-                                 double tol, int32_t max_iter, void* workspace, size_t workspace_bytes,
+                                 double tol, int32_t max_iter, int32_t restart, int32_t gmres_max_iter,
+                                 void* workspace, size_t workspace_bytes,
                                  hodlr_stream_t stream, int32_t* iters, double* relres);
 HODLR_API hodlr_status hodlr_gmres(hodlr_factor_t f, const double* D, const double* U, const double* V,
                          const double* B, int64_t ldb, double* X, int64_t ldx, int32_t k,
@@ -229,8 +249,11 @@ HODLR_API hodlr_status hodlr_gmres(hodlr_factor_t f, const double* D, const doub
  * and leaf below alpha; dD_b also gets D_b^{-T}.
  * dD has D's layout, dU and dV are N x rL with leading dimension N, dB is
  * N x k (lddb). Results overwrite the outputs. If loss is not NULL the call
- * synchronizes and stores the loss value. Only FP64 factors
- * (HODLR_ERR_ARG otherwise). */
+ * synchronizes and stores the loss value. FP64 and FP32 factors
+ * (HODLR_ERR_ARG otherwise). With an FP32 factor the solves, Y_big and the
+ * leaf inverses / LUs carry FP32 rounding (coupling inverses, log-dets and
+ * accumulations stay FP64): its gradient approximates the FP64 one to about
+ * the FP32 factor's solve accuracy. */
 HODLR_API hodlr_status hodlr_grad_workspace_size(hodlr_factor_t f, int32_t k, size_t* bytes);
 HODLR_API hodlr_status hodlr_grad(hodlr_factor_t f, const double* U, const double* V, const double* B, int64_t ldb,
                                   int32_t k, double* dD, double* dU, double* dV, double* dB, int64_t lddb,
@@ -255,11 +278,27 @@ HODLR_API int64_t hodlr_launch_count(void);
  * on by default; off selects the CUDA-core kernels (same results up to FP32
  * summation order). Process-wide; for tests and benchmarks. */
 HODLR_API void hodlr_tc_enable(int32_t on);
+/* BF16 factor, r <= 32: on forms S = I - T_alpha T_beta and the products of
+ * the explicit coupling inverse in FP64 (as the FP64 and FP32 factors do);
+ * off (default) forms them with FP32 products, the elimination of S staying
+ * FP64. Process-wide; for the precision experiment of benchmarks and tests. */
+HODLR_API void hodlr_coupling_fp64_enable(int32_t on);
 HODLR_API void hodlr_profile_enable(int32_t on);
 HODLR_API void hodlr_profile_reset(void);
 HODLR_API int32_t hodlr_profile_read(double* ms, int64_t* launches, int32_t n);
 HODLR_API int32_t hodlr_profile_work(double* bytes, double* flops, int32_t n);
 HODLR_API const char* hodlr_profile_name(int32_t cls);
+
+/* FP64 pipe probe (a diagnostic, not part of the method): enqueues one kernel
+ * of blocks_per_sm (1..64) blocks of 256 threads per SM of the current
+ * device, each thread running 8 independent chains of `iters` dependent FP64
+ * FMAs on registers only; *fmas receives the total FMA count. `out` is a
+ * device pointer to one double that the kernel never writes in practice (it
+ * only keeps the chains from being optimized away). Timing the launch with
+ * events on `stream` gives the FP64 FMA rate that bounds FP64-pipe-bound
+ * kernels on this GPU at its current clock. */
+HODLR_API hodlr_status hodlr_probe_fp64_fma(int64_t iters, int32_t blocks_per_sm, double* out,
+                                            hodlr_stream_t stream, int64_t* fmas);
 
 #ifdef __cplusplus
 }

@@ -40,7 +40,7 @@ EXPORTED = (
     "hodlr_matvec_workspace_size", "hodlr_matvec", "hodlr_refine_workspace_size", "hodlr_solve_refined",
     "hodlr_gmres", "hodlr_launch_count", "hodlr_profile_enable", "hodlr_profile_reset", "hodlr_profile_read",
     "hodlr_profile_name", "hodlr_profile_work", "hodlr_tc_enable", "hodlr_grad_workspace_size", "hodlr_grad",
-    "hodlr_matvec_noalloc",
+    "hodlr_matvec_noalloc", "hodlr_probe_fp64_fma", "hodlr_coupling_fp64_enable",
 )
 
 
@@ -70,8 +70,8 @@ _SIGS = {
     "hodlr_matvec_workspace_size": ([_vp, _i32, _c.POINTER(_sz)], _c.c_int),
     "hodlr_matvec": ([_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64, _i32, _vp, _sz, _vp], _c.c_int),
     "hodlr_refine_workspace_size": ([_vp, _i32, _i32, _c.POINTER(_sz)], _c.c_int),
-    "hodlr_solve_refined": ([_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64, _i32, _dbl, _i32, _vp, _sz, _vp,
-                             _c.POINTER(_i32), _c.POINTER(_dbl)], _c.c_int),
+    "hodlr_solve_refined": ([_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64, _i32, _dbl, _i32, _i32, _i32, _vp, _sz,
+                             _vp, _c.POINTER(_i32), _c.POINTER(_dbl)], _c.c_int),
     "hodlr_gmres": ([_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64, _i32, _dbl, _i32, _i32, _vp, _sz, _vp,
                      _c.POINTER(_i32), _c.POINTER(_dbl)], _c.c_int),
     "hodlr_launch_count": ([], _i64),
@@ -81,7 +81,9 @@ _SIGS = {
     "hodlr_profile_name": ([_i32], _c.c_char_p),
     "hodlr_profile_work": ([_c.POINTER(_dbl), _c.POINTER(_dbl), _i32], _i32),
     "hodlr_tc_enable": ([_i32], None),
+    "hodlr_coupling_fp64_enable": ([_i32], None),
     "hodlr_matvec_noalloc": ([_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64, _i32, _vp], _c.c_int),
+    "hodlr_probe_fp64_fma": ([_i64, _i32, _vp, _vp, _c.POINTER(_i64)], _c.c_int),
     "hodlr_grad_workspace_size": ([_vp, _i32, _c.POINTER(_sz)], _c.c_int),
     "hodlr_grad": ([_vp, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp, _i64, _vp, _sz, _vp, _c.POINTER(_dbl)],
                    _c.c_int),
@@ -125,6 +127,23 @@ def _ld(t: torch.Tensor, N: int) -> int:
     if t.stride(0) != 1:
         raise ValueError("expected a column-major matrix (stride (1, ld))")
     return t.stride(1) if t.shape[1] > 1 else max(N, t.stride(1))
+
+
+def _on_current_device(*ts: torch.Tensor) -> None:
+    """Every operand must live on the current CUDA device: the library
+    launches on that device's current stream (and the allocation-free matvec
+    takes that device's scratch)."""
+    for t in ts:
+        if t is None:
+            continue
+        if not t.is_cuda or t.device.index != torch.cuda.current_device():
+            raise ValueError(f"operand on {t.device}, expected the current CUDA device "
+                             "(use torch.cuda.device(...) around the call)")
+
+
+def _same_width(X: torch.Tensor, Y: torch.Tensor) -> None:
+    if X.dim() != 2 or Y.dim() != 2 or Y.shape[1] != X.shape[1]:
+        raise ValueError(f"X and Y must have the same number of columns, got {tuple(X.shape)} and {tuple(Y.shape)}")
 
 
 def make_desc(N: int, L: int, r: int, U: torch.Tensor | None = None, V: torch.Tensor | None = None) -> hodlr_desc:
@@ -177,6 +196,7 @@ def hodlr_factor_workspace_size(desc: hodlr_desc, prec: str = "fp64") -> int:
 def hodlr_factor(D, U, V, L: int, r: int, prec: str = "fp64") -> FactorHandle:
     N = U.shape[0]
     _check_D(D, N, L)
+    _on_current_device(D, U, V)
     desc = make_desc(N, L, r, U, V)
     if U.shape[1] != r * L or V.shape[1] != r * L:
         raise ValueError("U, V must have r*L columns")
@@ -201,6 +221,7 @@ def hodlr_solve_workspace_size(F: FactorHandle, k: int) -> int:
 
 def _solve(fn, F: FactorHandle, B: torch.Tensor):
     ldb = _ld(B, F.N)
+    _on_current_device(B, F.workspace)
     k = B.shape[1]
     ws = _workspace(hodlr_solve_workspace_size(F, k), B.device)
     _check(fn(F.handle, _ptr(B), ldb, k, _ptr(ws), ws.numel(), _stream()))
@@ -236,6 +257,8 @@ def hodlr_matvec_workspace_size(desc: hodlr_desc, k: int) -> int:
 def hodlr_matvec(D, U, V, L: int, r: int, X: torch.Tensor, Y: torch.Tensor | None = None) -> torch.Tensor:
     """Y = A X in FP64."""
     N = U.shape[0]
+    if Y is not None:
+        _same_width(X, Y)
     _check_D(D, N, L)
     desc = make_desc(N, L, r, U, V)
     ldx = _ld(X, N)
@@ -243,6 +266,7 @@ def hodlr_matvec(D, U, V, L: int, r: int, X: torch.Tensor, Y: torch.Tensor | Non
     if Y is None:
         Y = torch.empty(k, N, dtype=torch.float64, device=X.device).T
     ldy = _ld(Y, N)
+    _on_current_device(D, U, V, X, Y)
     ws = _workspace(hodlr_matvec_workspace_size(desc, k), X.device)
     _check(_LIB.hodlr_matvec(ctypes.byref(desc), _ptr(D), _ptr(U), _ptr(V), _ptr(X), ldx, _ptr(Y), ldy, k,
                              _ptr(ws), ws.numel(), _stream()), "hodlr_matvec: ")
@@ -255,18 +279,25 @@ def hodlr_refine_workspace_size(F: FactorHandle, k: int, restart: int = 0) -> in
     return out.value
 
 
-def hodlr_solve_refined(F: FactorHandle, D, U, V, B, tol=1e-10, max_iter=50, X=None, raise_on_fail=True):
-    """Iterative refinement with FP64 residuals; returns (X, iters, relres, status)."""
+def hodlr_solve_refined(F: FactorHandle, D, U, V, B, tol=1e-10, max_iter=50, X=None, raise_on_fail=True,
+                        restart=0, gmres_max_iter=300):
+    """Iterative refinement with FP64 residuals, continued by FGMRES(restart)
+    when it stalls (restart > 0); returns (X, iters, relres, status)."""
     N = F.N
     ldb = _ld(B, N)
     k = B.shape[1]
+    if X is not None:
+        _same_width(B, X)
     if X is None:
         X = torch.empty(k, N, dtype=torch.float64, device=B.device).T
     ldx = _ld(X, N)
-    ws = _workspace(hodlr_refine_workspace_size(F, k, 0), B.device)
+    _check_D(D, N, F.desc.L)
+    _on_current_device(D, U, V, B, X, F.workspace)
+    ws = _workspace(hodlr_refine_workspace_size(F, k, restart), B.device)
     it, rr = ctypes.c_int32(), ctypes.c_double()
     code = _LIB.hodlr_solve_refined(F.handle, _ptr(D), _ptr(U), _ptr(V), _ptr(B), ldb, _ptr(X), ldx, k, tol,
-                                    max_iter, _ptr(ws), ws.numel(), _stream(), ctypes.byref(it), ctypes.byref(rr))
+                                    max_iter, restart, gmres_max_iter if restart > 0 else 0, _ptr(ws), ws.numel(),
+                                    _stream(), ctypes.byref(it), ctypes.byref(rr))
     if raise_on_fail and code != HODLR_OK:
         raise HodlrError(code, msg=f"hodlr_solve_refined (iters={it.value}, relres={rr.value:.3e}): ")
     return X, it.value, rr.value, code
@@ -277,9 +308,13 @@ def hodlr_gmres(F: FactorHandle, D, U, V, B, tol=1e-10, restart=30, max_iter=300
     N = F.N
     ldb = _ld(B, N)
     k = B.shape[1]
+    if X is not None:
+        _same_width(B, X)
     if X is None:
         X = torch.empty(k, N, dtype=torch.float64, device=B.device).T
     ldx = _ld(X, N)
+    _check_D(D, N, F.desc.L)
+    _on_current_device(D, U, V, B, X, F.workspace)
     ws = _workspace(hodlr_refine_workspace_size(F, k, restart), B.device)
     it, rr = ctypes.c_int32(), ctypes.c_double()
     code = _LIB.hodlr_gmres(F.handle, _ptr(D), _ptr(U), _ptr(V), _ptr(B), ldb, _ptr(X), ldx, k, tol, restart,
@@ -324,6 +359,20 @@ def hodlr_profile_name(i: int) -> str:
     return _LIB.hodlr_profile_name(i).decode()
 
 
+def hodlr_probe_fp64_fma(iters: int, blocks_per_sm: int, out: torch.Tensor) -> int:
+    """Enqueue the FP64 FMA probe on the current stream; returns its FMA count
+    (time it with CUDA events on that stream)."""
+    _on_current_device(out)
+    n = ctypes.c_int64()
+    _check(_LIB.hodlr_probe_fp64_fma(int(iters), int(blocks_per_sm), _ptr(out), _stream(), ctypes.byref(n)))
+    return n.value
+
+
+def hodlr_coupling_fp64_enable(on: bool = True) -> None:
+    """BF16 factor: coupling products in FP64 (on) or FP32 (off, default)."""
+    _LIB.hodlr_coupling_fp64_enable(1 if on else 0)
+
+
 def hodlr_tc_enable(on: bool = True) -> None:
     """Select tensor-core (on, default) or CUDA-core kernels for the BF16 factor."""
     _LIB.hodlr_tc_enable(1 if on else 0)
@@ -345,6 +394,7 @@ def hodlr_grad(F: FactorHandle, U, V, B, want_loss: bool = True):
     m, L = F.desc.m, F.desc.L
     rL = F.desc.r * L
     dev = B.device
+    _on_current_device(U, V, B, F.workspace)
     dD = torch.empty(1 << L, m, m, dtype=torch.float64, device=dev).transpose(1, 2)
     dU = torch.empty(rL, N, dtype=torch.float64, device=dev).T
     dV = torch.empty(rL, N, dtype=torch.float64, device=dev).T
@@ -362,9 +412,11 @@ def hodlr_matvec_noalloc(D, U, V, L: int, r: int, X: torch.Tensor, Y: torch.Tens
     the library's fixed device scratch replaces the workspace. Y must be
     preallocated (column-major)."""
     N = U.shape[0]
+    _same_width(X, Y)
     _check_D(D, N, L)
     desc = make_desc(N, L, r, U, V)
     ldx, ldy = _ld(X, N), _ld(Y, N)
+    _on_current_device(D, U, V, X, Y)
     _check(_LIB.hodlr_matvec_noalloc(ctypes.byref(desc), _ptr(D), _ptr(U), _ptr(V), _ptr(X), ldx, _ptr(Y), ldy,
                                      X.shape[1], _stream()), "hodlr_matvec_noalloc: ")
     return Y

@@ -46,3 +46,16 @@ def project_bytes(N: int, r: int, ncols: int, elem: int) -> float:
     """Algorithmic bytes of one level's projection V^T R(:, 0:ncols): R and the
     level's V block read once."""
     return float(elem) * N * (ncols + r)
+
+
+def solve_bytes(N: int, m: int, r: int, L: int, k: int, prec: str) -> float:
+    """Compulsory bytes of one k-column solve (or adjoint solve) with a factor
+    of precision `prec`: the factor read once (leaf inverses or LUs, Y_big and
+    the level's V blocks, the 2r x 2r coupling inverses in FP64) and the k
+    right-hand sides read and written once per level (in FP32 for a
+    low-precision factor, FP64 otherwise)."""
+    e_leaf = 8 if prec == "fp64" else 4
+    e_panel = {"fp64": 8, "fp32": 4}.get(prec, 2)
+    e_x = 8 if prec == "fp64" else 4
+    factor = e_leaf * N * m + 2.0 * e_panel * N * r * L + 8.0 * 4 * r * r * ((1 << L) - 1)
+    return factor + 2.0 * e_x * N * k * L

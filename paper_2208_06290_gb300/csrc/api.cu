@@ -17,6 +17,7 @@ namespace hodlr {
 cudaError_t launch_coupling_factor_apply(const Factor& F, int c, cudaStream_t s);
 
 bool g_use_tc = true;
+bool g_coupling_fp64 = false;
 
 // ---------------------------------------------------------------- launch accounting
 namespace {
@@ -311,6 +312,7 @@ hodlr_status matvec_core_ext(const hodlr_desc& d, const double* D, const double*
   return matvec_core(d, D, U, V, X, ldx, Y, ldy, k, work, s, work_bytes);
 }
 size_t matvec_scratch_bytes(const hodlr_desc& d, int k) { return matvec_min_bytes(d, k); }
+hodlr_status check_desc_ext(const hodlr_desc* d) { return check_desc(d); }
 
 }  // namespace hodlr
 
@@ -489,6 +491,11 @@ hodlr_status hodlr_matvec(const hodlr_desc* desc, const double* D, const double*
 // ------------------------------------------------------------ refined solvers
 namespace {
 
+// Workspace of the refined solvers. FGMRES (restart > 0) keeps, for the k
+// right-hand sides in lockstep, the Arnoldi basis V (restart + 1 vectors per
+// column), the preconditioned vectors Z and their FP64 products W = A Z
+// (restart each), stored so that the q-th vectors of all columns form one
+// N x k block (column q * k + j, ld N).
 struct RefineLayout {
   size_t R, solve, mv, dots, scal, V, Z, W, w, total;
 };
@@ -498,17 +505,18 @@ RefineLayout refine_layout(const Factor& F, int k, int restart) {
   const size_t N = (size_t)F.d.N;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes); return o; };
-  const int kk = k > 1 ? k : 1;
+  const size_t kk = (size_t)k;
+  const size_t m = (size_t)restart;
   l.R = take(N * kk * sizeof(double));
-  l.solve = take(solve_ws_bytes(F, kk));
-  l.mv = take(matvec_ws_bytes(F.d, kk));
-  l.dots = take(dot_scratch_elems(F.d.N, (kk > restart + 1 ? kk : restart + 1)) * sizeof(double));
-  l.scal = take((size_t)(kk > restart + 2 ? kk : restart + 2) * 2 * sizeof(double));
+  l.solve = take(solve_ws_bytes(F, k));
+  l.mv = take(matvec_ws_bytes(F.d, k));
+  l.dots = take(dot_scratch_elems(F.d.N, (int)((m + 1) * kk)) * sizeof(double));
+  l.scal = take(((2 * (m + 1) + 3 + m) * kk + 8) * sizeof(double));
   if (restart > 0) {
-    l.V = take(N * (restart + 1) * sizeof(double));
-    l.Z = take(N * restart * sizeof(double));
-    l.W = take(N * restart * sizeof(double));  // A z_i before orthogonalisation
-    l.w = take(N * sizeof(double));
+    l.V = take(N * (m + 1) * kk * sizeof(double));
+    l.Z = take(N * m * kk * sizeof(double));
+    l.W = take(N * m * kk * sizeof(double));
+    l.w = take(N * kk * sizeof(double));
   }
   l.total = off;
   return l;
@@ -522,22 +530,161 @@ hodlr_status col_norms2(int64_t N, int k, const double* x, int64_t ldx, double* 
   return HODLR_OK;
 }
 
+// Flexible GMRES(restart), right-preconditioned by the factor, on k columns in
+// lockstep: every inner iteration applies the preconditioner to the k new
+// basis vectors in one k-column solve and the FP64 operator in one k-column
+// matvec; classical Gram-Schmidt twice, per column, with batched dot products;
+// one host synchronization per iteration reads the k columns' Hessenberg
+// entries (Givens rotations on the host). A column whose residual estimate
+// reaches 0.5 tol stops extending its basis (its later vectors are computed
+// but never used). After each cycle x += Z y and r -= (A Z) y from the stored
+// FP64 products (no further matvec); a column that has converged takes y = 0.
+// X holds the initial guess on entry (start_from_x) or is set to f^{-1} B.
+hodlr_status gmres_core(const Factor& F, const double* D, const double* U, const double* V, const double* B,
+                        int64_t ldb, double* X, int64_t ldx, int k, double tol, int restart, int max_iter,
+                        bool start_from_x, char* w, const RefineLayout& lay, cudaStream_t s, int* iters_out,
+                        double* relres_out) {
+  const hodlr_desc& d = F.d;
+  const int64_t N = d.N;
+  const int m = restart;
+  double* R = reinterpret_cast<double*>(w + lay.R);
+  void* sw = w + lay.solve;
+  void* mw = w + lay.mv;
+  double* scratch = reinterpret_cast<double*>(w + lay.dots);
+  double* scal = reinterpret_cast<double*>(w + lay.scal);
+  double* dev_h1 = scal;                          // (m + 1) k
+  double* dev_h2 = dev_h1 + (size_t)(m + 1) * k;  // (m + 1) k
+  double* dev_hn = dev_h2 + (size_t)(m + 1) * k;  // k
+  double* dev_nr = dev_hn + k;                    // k
+  double* dev_nb = dev_nr + k;                    // k
+  double* dev_coef = dev_nb + k;                  // m k
+  double* Vb = reinterpret_cast<double*>(w + lay.V);
+  double* Zb = reinterpret_cast<double*>(w + lay.Z);
+  double* Wb = reinterpret_cast<double*>(w + lay.W);
+  double* wv = reinterpret_cast<double*>(w + lay.w);
+  hodlr_status st;
+  if (!start_from_x) {
+    HODLR_CUDA(launch_copy_cols<double, double>(N, k, B, ldb, X, ldx, s));
+    if ((st = solve_any(F, X, ldx, k, sw, 0, s)) != HODLR_OK) return st;
+  }
+  std::vector<double> nb(k), nr(k), hh((size_t)(2 * (m + 1) + 1) * k), coef((size_t)m * k);
+  std::vector<double> H((size_t)k * (m + 1) * m), g((size_t)k * (m + 1)), cs((size_t)k * m), sn((size_t)k * m),
+      y(m);
+  std::vector<int> nsteps(k), done(k);
+  if ((st = col_norms2(N, k, B, ldb, dev_nb, scratch, nb.data(), s)) != HODLR_OK) return st;
+  for (int j = 0; j < k; ++j) nb[j] = std::sqrt(nb[j]) > 0.0 ? std::sqrt(nb[j]) : 1.0;
+  // r = B - A X (FP64 matvec) once; later cycles update it from W
+  if ((st = matvec_core(d, D, U, V, X, ldx, R, N, k, mw, s, matvec_ws_bytes(d, k))) != HODLR_OK) return st;
+  HODLR_CUDA(launch_axpby_cols(N, k, 1.0, B, ldb, -1.0, R, N, s));
+  int total_it = 0;
+  double worst = INFINITY;
+  for (;;) {
+    if ((st = col_norms2(N, k, R, N, dev_nr, scratch, nr.data(), s)) != HODLR_OK) return st;
+    worst = 0.0;
+    bool any = false;
+    for (int j = 0; j < k; ++j) {
+      const double rel = std::sqrt(nr[j]) / nb[j];
+      worst = std::isnan(rel) ? INFINITY : std::max(worst, rel);
+      done[j] = rel > tol ? 0 : 1;
+      any |= !done[j];
+      nsteps[j] = 0;
+      std::fill(g.begin() + (size_t)j * (m + 1), g.begin() + (size_t)(j + 1) * (m + 1), 0.0);
+      g[(size_t)j * (m + 1)] = std::sqrt(nr[j]);
+    }
+    if (!any || total_it >= max_iter) break;
+    HODLR_CUDA(launch_scale_inv_norm(N, k, R, dev_nr, Vb, s));  // v_0 = r / |r|
+    int nq = 0;
+    for (int i = 0; i < m && total_it < max_iter; ++i) {
+      double* Vi = Vb + (size_t)i * k * N;
+      double* Zi = Zb + (size_t)i * k * N;
+      double* Wi = Wb + (size_t)i * k * N;
+      HODLR_CUDA(launch_copy_cols<double, double>(N, k, Vi, N, Zi, N, s));
+      if ((st = solve_any(F, Zi, N, k, sw, 0, s)) != HODLR_OK) return st;  // z = M^{-1} v
+      if ((st = matvec_core(d, D, U, V, Zi, N, Wi, N, k, mw, s, matvec_ws_bytes(d, k))) != HODLR_OK) return st;
+      HODLR_CUDA(launch_copy_cols<double, double>(N, k, Wi, N, wv, N, s));
+      // classical Gram-Schmidt, twice
+      HODLR_CUDA(launch_bdots(N, k, i + 1, Vb, wv, dev_h1, scratch, s));
+      HODLR_CUDA(launch_bgemv(N, k, i + 1, Vb, dev_h1, -1.0, wv, N, s));
+      HODLR_CUDA(launch_bdots(N, k, i + 1, Vb, wv, dev_h2, scratch, s));
+      HODLR_CUDA(launch_bgemv(N, k, i + 1, Vb, dev_h2, -1.0, wv, N, s));
+      HODLR_CUDA(launch_dots(N, k, wv, N, wv, N, dev_hn, scratch, s));
+      HODLR_CUDA(launch_scale_inv_norm(N, k, wv, dev_hn, Vb + (size_t)(i + 1) * k * N, s));
+      HODLR_CUDA(cudaMemcpyAsync(hh.data(), dev_h1, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+      HODLR_CUDA(cudaStreamSynchronize(s));
+      ++total_it;
+      nq = i + 1;
+      bool all = true;
+      for (int j = 0; j < k; ++j) {
+        if (done[j]) continue;
+        double* Hi = H.data() + ((size_t)j * m + i) * (m + 1);
+        double* gj = g.data() + (size_t)j * (m + 1);
+        double* csj = cs.data() + (size_t)j * m;
+        double* snj = sn.data() + (size_t)j * m;
+        for (int q = 0; q <= i; ++q) Hi[q] = hh[(size_t)q * k + j] + hh[(size_t)(m + 1) * k + (size_t)q * k + j];
+        Hi[i + 1] = std::sqrt(hh[(size_t)2 * (m + 1) * k + j]);
+        for (int q = 0; q < i; ++q) {  // earlier Givens rotations on column i
+          const double t = csj[q] * Hi[q] + snj[q] * Hi[q + 1];
+          Hi[q + 1] = -snj[q] * Hi[q] + csj[q] * Hi[q + 1];
+          Hi[q] = t;
+        }
+        const double den = std::hypot(Hi[i], Hi[i + 1]);
+        csj[i] = den > 0.0 ? Hi[i] / den : 1.0;
+        snj[i] = den > 0.0 ? Hi[i + 1] / den : 0.0;
+        Hi[i] = den;
+        Hi[i + 1] = 0.0;
+        gj[i + 1] = -snj[i] * gj[i];
+        gj[i] = csj[i] * gj[i];
+        nsteps[j] = i + 1;
+        if (std::fabs(gj[i + 1]) / nb[j] <= 0.5 * tol) done[j] = 1;
+        all &= done[j] != 0;
+      }
+      if (all) break;
+    }
+    // y = H(0:n, 0:n)^{-1} g(0:n) per column; x += Z y, r -= (A Z) y
+    std::fill(coef.begin(), coef.end(), 0.0);
+    for (int j = 0; j < k; ++j) {
+      const int ns = nsteps[j];
+      const double* Hj = H.data() + (size_t)j * m * (m + 1);
+      const double* gj = g.data() + (size_t)j * (m + 1);
+      for (int q = ns - 1; q >= 0; --q) {
+        double acc = gj[q];
+        for (int p = q + 1; p < ns; ++p) acc -= Hj[(size_t)p * (m + 1) + q] * y[p];
+        const double hq = Hj[(size_t)q * (m + 1) + q];
+        y[q] = hq != 0.0 ? acc / hq : 0.0;
+      }
+      for (int q = 0; q < ns; ++q) coef[(size_t)q * k + j] = y[q];
+    }
+    HODLR_CUDA(cudaMemcpyAsync(dev_coef, coef.data(), (size_t)nq * k * sizeof(double), cudaMemcpyHostToDevice, s));
+    HODLR_CUDA(launch_bgemv(N, k, nq, Zb, dev_coef, 1.0, X, ldx, s));
+    HODLR_CUDA(launch_bgemv(N, k, nq, Wb, dev_coef, -1.0, R, N, s));
+  }
+  if (iters_out) *iters_out = total_it;
+  if (relres_out) *relres_out = worst;
+  return worst <= tol ? HODLR_OK : HODLR_ERR_NOT_CONVERGED;
+}
+
+hodlr_status device_status(const Factor& F) {
+  DevStatus ds{};
+  if (cudaMemcpy(&ds, F.status, sizeof(ds), cudaMemcpyDeviceToHost) != cudaSuccess) return HODLR_ERR_CUDA;
+  return static_cast<hodlr_status>(ds.code);
+}
+
 }  // namespace
 
 hodlr_status hodlr_refine_workspace_size(hodlr_factor_t f, int32_t k, int32_t restart, size_t* bytes) {
-  if (!valid_factor(f) || k < 1 || restart < 0 || !bytes) return HODLR_ERR_ARG;
+  if (!valid_factor(f) || k < 1 || restart < 0 || restart > 200 || !bytes) return HODLR_ERR_ARG;
   *bytes = refine_layout(*f, k, restart).total;
   return HODLR_OK;
 }
 
 hodlr_status hodlr_solve_refined(hodlr_factor_t f, const double* D, const double* U, const double* V,
                                  const double* B, int64_t ldb, double* X, int64_t ldx, int32_t k, double tol,
-                                 int32_t max_iter, void* workspace, size_t workspace_bytes, hodlr_stream_t stream,
-                                 int32_t* iters, double* relres) {
+                                 int32_t max_iter, int32_t restart, int32_t gmres_max_iter, void* workspace,
+                                 size_t workspace_bytes, hodlr_stream_t stream, int32_t* iters, double* relres) {
   if (!valid_factor(f) || !D || !U || !V || !B || !X || k < 1 || ldb < f->d.N || ldx < f->d.N || max_iter < 0 ||
-      !(tol > 0.0))
+      restart < 0 || restart > 200 || gmres_max_iter < 0 || !(tol > 0.0))
     return HODLR_ERR_ARG;
-  const RefineLayout lay = refine_layout(*f, k, 0);
+  const RefineLayout lay = refine_layout(*f, k, restart);
   if (!workspace || !aligned(workspace, kAlign) || workspace_bytes < lay.total) return HODLR_ERR_WORKSPACE;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   char* w = static_cast<char*>(workspace);
@@ -573,11 +720,15 @@ hodlr_status hodlr_solve_refined(hodlr_factor_t f, const double* D, const double
     HODLR_CUDA(launch_axpby_cols(N, k, 1.0, R, N, 1.0, X, ldx, s));  // X += correction
     ++it;
   }
-  if (iters) *iters = it;
+  int git = 0;
+  if (!(worst <= tol) && restart > 0 && gmres_max_iter > 0) {
+    // refinement stalled (or ran out of corrections): FGMRES from the current X
+    st = gmres_core(*f, D, U, V, B, ldb, X, ldx, k, tol, restart, gmres_max_iter, true, w, lay, s, &git, &worst);
+    if (st != HODLR_OK && st != HODLR_ERR_NOT_CONVERGED) return st;
+  }
+  if (iters) *iters = it + git;
   if (relres) *relres = worst;
-  DevStatus ds{};
-  HODLR_CUDA(cudaMemcpy(&ds, f->status, sizeof(ds), cudaMemcpyDeviceToHost));
-  if (ds.code != 0) return static_cast<hodlr_status>(ds.code);
+  if ((st = device_status(*f)) != HODLR_OK) return st;
   return worst <= tol ? HODLR_OK : HODLR_ERR_NOT_CONVERGED;
 }
 
@@ -590,110 +741,16 @@ hodlr_status hodlr_gmres(hodlr_factor_t f, const double* D, const double* U, con
     return HODLR_ERR_ARG;
   const RefineLayout lay = refine_layout(*f, k, restart);
   if (!workspace || !aligned(workspace, kAlign) || workspace_bytes < lay.total) return HODLR_ERR_WORKSPACE;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  char* w = static_cast<char*>(workspace);
-  double* r = reinterpret_cast<double*>(w + lay.R);
-  void* sw = w + lay.solve;
-  void* mw = w + lay.mv;
-  double* scratch = reinterpret_cast<double*>(w + lay.dots);
-  double* dev_h = reinterpret_cast<double*>(w + lay.scal);
-  double* Vk = reinterpret_cast<double*>(w + lay.V);
-  double* Zk = reinterpret_cast<double*>(w + lay.Z);
-  double* Wk = reinterpret_cast<double*>(w + lay.W);
-  double* wv = reinterpret_cast<double*>(w + lay.w);
-  const hodlr_desc& d = f->d;
-  const int64_t N = d.N;
-  const int m = restart;
-  std::vector<double> H((size_t)(m + 1) * m), g(m + 1), cs(m), sn(m), h(m + 1), h2(m + 1), y(m);
-  hodlr_status st;
-  int total_it = 0;
-  double worst = 0.0;
-  for (int j = 0; j < k; ++j) {
-    const double* b = B + (int64_t)j * ldb;
-    double* x = X + (int64_t)j * ldx;
-    double nb2 = 0.0;
-    if ((st = col_norms2(N, 1, b, N, dev_h, scratch, &nb2, s)) != HODLR_OK) return st;
-    const double nb = std::sqrt(nb2) > 0.0 ? std::sqrt(nb2) : 1.0;
-    HODLR_CUDA(launch_copy_cols<double, double>(N, 1, b, N, x, N, s));
-    if ((st = solve_any(*f, x, N, 1, sw, 0, s)) != HODLR_OK) return st;
-    int col_it = 0;
-    double rel = INFINITY;
-    // residual r = b - A x of the initial guess (FP64 matvec); after each
-    // cycle r = r - A Z y from the stored FP64 products A z_i, which is
-    // b - A x of the updated x without another matvec
-    if ((st = matvec_core(d, D, U, V, x, N, r, N, 1, mw, s, matvec_ws_bytes(d, 1))) != HODLR_OK) return st;
-    HODLR_CUDA(launch_axpby_cols(N, 1, 1.0, b, N, -1.0, r, N, s));
-    for (;;) {
-      double beta2 = 0.0;
-      if ((st = col_norms2(N, 1, r, N, dev_h, scratch, &beta2, s)) != HODLR_OK) return st;
-      const double beta = std::sqrt(beta2);
-      rel = beta / nb;
-      if (!(rel > tol) || col_it >= max_iter) break;
-      HODLR_CUDA(launch_axpby_cols(N, 1, 1.0 / beta, r, N, 0.0, Vk, N, s));  // v_0 = r / beta
-      std::fill(g.begin(), g.end(), 0.0);
-      g[0] = beta;
-      int nsteps = 0;
-      for (int i = 0; i < m && col_it < max_iter; ++i) {
-        double* vi = Vk + (int64_t)i * N;
-        double* zi = Zk + (int64_t)i * N;
-        HODLR_CUDA(launch_copy_cols<double, double>(N, 1, vi, N, zi, N, s));
-        if ((st = solve_any(*f, zi, N, 1, sw, 0, s)) != HODLR_OK) return st;  // z_i = M^{-1} v_i
-        if ((st = matvec_core(d, D, U, V, zi, N, wv, N, 1, mw, s, matvec_ws_bytes(d, 1))) != HODLR_OK) return st;  // w = A z_i
-        HODLR_CUDA(launch_copy_cols<double, double>(N, 1, wv, N, Wk + (int64_t)i * N, N, s));
-        // classical Gram-Schmidt, twice
-        for (int pass = 0; pass < 2; ++pass) {
-          HODLR_CUDA(launch_multidot(N, i + 1, Vk, N, wv, dev_h, scratch, s));
-          HODLR_CUDA(launch_gemv_sub(N, i + 1, Vk, N, dev_h, wv, s));
-          HODLR_CUDA(cudaMemcpyAsync(pass ? h2.data() : h.data(), dev_h, (size_t)(i + 1) * sizeof(double),
-                                     cudaMemcpyDeviceToHost, s));
-        }
-        double hn2 = 0.0;
-        if ((st = col_norms2(N, 1, wv, N, dev_h, scratch, &hn2, s)) != HODLR_OK) return st;  // syncs
-        double* Hi = H.data() + (size_t)i * (m + 1);
-        for (int q = 0; q <= i; ++q) Hi[q] = h[q] + h2[q];
-        Hi[i + 1] = std::sqrt(hn2);
-        if (Hi[i + 1] > 0.0)
-          HODLR_CUDA(launch_axpby_cols(N, 1, 1.0 / Hi[i + 1], wv, N, 0.0, Vk + (int64_t)(i + 1) * N, N, s));
-        // Givens rotations on column i
-        for (int q = 0; q < i; ++q) {
-          const double t = cs[q] * Hi[q] + sn[q] * Hi[q + 1];
-          Hi[q + 1] = -sn[q] * Hi[q] + cs[q] * Hi[q + 1];
-          Hi[q] = t;
-        }
-        const double den = std::hypot(Hi[i], Hi[i + 1]);
-        cs[i] = den > 0.0 ? Hi[i] / den : 1.0;
-        sn[i] = den > 0.0 ? Hi[i + 1] / den : 0.0;
-        Hi[i] = den;
-        Hi[i + 1] = 0.0;
-        g[i + 1] = -sn[i] * g[i];
-        g[i] = cs[i] * g[i];
-        ++nsteps;
-        ++col_it;
-        if (std::fabs(g[i + 1]) / nb <= 0.5 * tol) break;
-      }
-      // y = H(0:n, 0:n)^{-1} g(0:n), x += Z y
-      for (int q = nsteps - 1; q >= 0; --q) {
-        double acc = g[q];
-        for (int p = q + 1; p < nsteps; ++p) acc -= H[(size_t)p * (m + 1) + q] * y[p];
-        const double hq = H[(size_t)q * (m + 1) + q];
-        y[q] = hq != 0.0 ? acc / hq : 0.0;
-      }
-      for (int q = 0; q < nsteps; ++q) h[q] = -y[q];
-      HODLR_CUDA(cudaMemcpyAsync(dev_h, h.data(), (size_t)nsteps * sizeof(double), cudaMemcpyHostToDevice, s));
-      HODLR_CUDA(launch_gemv_sub(N, nsteps, Zk, N, dev_h, x, s));  // x -= Z(-y)
-      for (int q = 0; q < nsteps; ++q) h[q] = y[q];
-      HODLR_CUDA(cudaMemcpyAsync(dev_h, h.data(), (size_t)nsteps * sizeof(double), cudaMemcpyHostToDevice, s));
-      HODLR_CUDA(launch_gemv_sub(N, nsteps, Wk, N, dev_h, r, s));  // r -= (A Z) y
-      HODLR_CUDA(cudaStreamSynchronize(s));
-    }
-    total_it += col_it;
-    if (!(rel <= worst)) worst = rel;
-  }
-  if (iters) *iters = total_it;
+  double worst = INFINITY;
+  int it = 0;
+  hodlr_status st = gmres_core(*f, D, U, V, B, ldb, X, ldx, k, tol, restart, max_iter, false,
+                               static_cast<char*>(workspace), lay, reinterpret_cast<cudaStream_t>(stream), &it,
+                               &worst);
+  if (st != HODLR_OK && st != HODLR_ERR_NOT_CONVERGED) return st;
+  if (iters) *iters = it;
   if (relres) *relres = worst;
-  DevStatus ds{};
-  HODLR_CUDA(cudaMemcpy(&ds, f->status, sizeof(ds), cudaMemcpyDeviceToHost));
-  if (ds.code != 0) return static_cast<hodlr_status>(ds.code);
+  hodlr_status ds = device_status(*f);
+  if (ds != HODLR_OK) return ds;
   return worst <= tol ? HODLR_OK : HODLR_ERR_NOT_CONVERGED;
 }
 
@@ -732,6 +789,10 @@ GradLayout grad_layout(const Factor& F, int k) {
   return l;
 }
 
+// TP: the factor's panel type (FP64 factor: double; FP32 factor: float, whose
+// Y, leaf inverses / LUs and solves then carry FP32 rounding into the
+// gradient; the coupling inverses and every accumulation stay FP64).
+template <typename TP>
 hodlr_status grad_core(const Factor& F, const double* U, const double* V, const double* B, int64_t ldb, int k,
                        double* dD, double* dU, double* dV, double* dB, int64_t lddb, char* w, const GradLayout& lay,
                        cudaStream_t s, double* loss) {
@@ -748,7 +809,7 @@ hodlr_status grad_core(const Factor& F, const double* U, const double* V, const 
   double* Ps = reinterpret_cast<double*>(w + lay.Ps);
   void* sw = w + lay.solve;
   double* dots = reinterpret_cast<double*>(w + lay.dots);
-  const double* Y = static_cast<const double*>(F.Y);
+  const TP* Y = static_cast<const TP*>(F.Y);
   const int64_t ldu = d.ldu, ldv = d.ldv;
   hodlr_status st;
   // X = A^{-1} B, Lam = A^{-T} B, dB = X + Lam
@@ -779,7 +840,7 @@ hodlr_status grad_core(const Factor& F, const double* U, const double* V, const 
   HODLR_CUDA(launch_copy_cols<double, double>(N, rL, V, ldv, Z, N, s));
   for (int c = 2; c <= L; ++c) {
     const int anc = r * (c - 1);
-    HODLR_CUDA((launch_project<double, double>(N, r, c, Y, N, c - 1, Z, N, anc, Ps, 1, s)));
+    HODLR_CUDA((launch_project<TP, double>(N, r, c, Y, N, c - 1, Z, N, anc, Ps, 1, s)));
     HODLR_CUDA(launch_coupling_apply_any(F, c, Ps, anc, anc, 0, 1, s));
     const int64_t ws = chunks_per_node(N, c) * (int64_t)r * anc;
     HODLR_CUDA((launch_update<double, double>(N, r, c, V, ldv, c - 1, Z, N, anc, Ps, ws, 1, -1.0, 1, s)));
@@ -789,7 +850,7 @@ hodlr_status grad_core(const Factor& F, const double* U, const double* V, const 
   for (int c = 1; c <= L; ++c) {
     HODLR_CUDA(launch_coupling_h(F, c, H, HT, s));
     const int64_t ws = (int64_t)r * r;
-    HODLR_CUDA((launch_update<double, double>(N, r, c, Y, N, c - 1, dV + (int64_t)(c - 1) * r * N, N, r, HT, ws, 0,
+    HODLR_CUDA((launch_update<TP, double>(N, r, c, Y, N, c - 1, dV + (int64_t)(c - 1) * r * N, N, r, HT, ws, 0,
                                               1.0, 1, s)));
     HODLR_CUDA((launch_update<double, double>(N, r, c, Z, N, c - 1, dU + (int64_t)(c - 1) * r * N, N, r, H, ws, 0,
                                               1.0, 1, s)));
@@ -800,20 +861,20 @@ hodlr_status grad_core(const Factor& F, const double* U, const double* V, const 
   for (int c = 2; c <= L; ++c) {
     const int64_t ws = chunks_per_node(N, c) * (int64_t)r * r;
     for (int j = 0; j <= c - 2; ++j) {
-      HODLR_CUDA((launch_project<double, double>(N, r, c, Y, N, j, V + (int64_t)(c - 1) * r * ldv, ldv, r, Ps, 1, s)));
+      HODLR_CUDA((launch_project<TP, double>(N, r, c, Y, N, j, V + (int64_t)(c - 1) * r * ldv, ldv, r, Ps, 1, s)));
       HODLR_CUDA(launch_reduce_chunks(N, r, c, Ps, r, s));
       HODLR_CUDA((launch_update<double, double>(N, r, c, Pb, N, j, dU + (int64_t)(c - 1) * r * N, N, r, Ps, ws, 1,
                                                 1.0, 1, s)));
       HODLR_CUDA((launch_project<double, double>(N, r, c, Pb, N, j, U + (int64_t)(c - 1) * r * ldu, ldu, r, Ps, 1, s)));
       HODLR_CUDA(launch_reduce_chunks(N, r, c, Ps, r, s));
-      HODLR_CUDA((launch_update<double, double>(N, r, c, Y, N, j, dV + (int64_t)(c - 1) * r * N, N, r, Ps, ws, 1, 1.0,
+      HODLR_CUDA((launch_update<TP, double>(N, r, c, Y, N, j, dV + (int64_t)(c - 1) * r * N, N, r, Ps, ws, 1, 1.0,
                                                 1, s)));
     }
   }
   // leaves: dD_b += D_b^{-T} + Pb(I_b, :) Y(I_b, :)^T
   HODLR_CUDA(launch_leaf_identity(N, m, E, s));
   HODLR_CUDA((launch_leaf_solve<double, double>(F, E, N, E, N, m, 0, s)));
-  HODLR_CUDA(launch_leaf_outer(N, m, rL, Pb, N, Y, N, 1.0, 1.0, E, dD, s));
+  HODLR_CUDA(launch_leaf_outer<TP>(N, m, rL, Pb, N, Y, N, 1.0, 1.0, E, dD, s));
   if (loss) {
     HODLR_CUDA(launch_dots(N, k, B, ldb, X, N, dots + dot_scratch_elems(N, k), dots, s));
     std::vector<double> q(k);
@@ -834,7 +895,8 @@ hodlr_status grad_core(const Factor& F, const double* U, const double* V, const 
 extern "C" {
 
 hodlr_status hodlr_grad_workspace_size(hodlr_factor_t f, int32_t k, size_t* bytes) {
-  if (!valid_factor(f) || k < 1 || k > 64 || !bytes) return HODLR_ERR_ARG;
+  if (!valid_factor(f) || (f->prec != HODLR_PREC_FP64 && f->prec != HODLR_PREC_FP32) || k < 1 || k > 64 || !bytes)
+    return HODLR_ERR_ARG;
   *bytes = grad_layout(*f, k).total;
   return HODLR_OK;
 }
@@ -842,13 +904,16 @@ hodlr_status hodlr_grad_workspace_size(hodlr_factor_t f, int32_t k, size_t* byte
 hodlr_status hodlr_grad(hodlr_factor_t f, const double* U, const double* V, const double* B, int64_t ldb, int32_t k,
                         double* dD, double* dU, double* dV, double* dB, int64_t lddb, void* workspace,
                         size_t workspace_bytes, hodlr_stream_t stream, double* loss) {
-  if (!valid_factor(f) || f->prec != HODLR_PREC_FP64 || !U || !V || !B || !dD || !dU || !dV || !dB || k < 1 ||
-      k > 64 || ldb < f->d.N || lddb < f->d.N)
+  if (!valid_factor(f) || (f->prec != HODLR_PREC_FP64 && f->prec != HODLR_PREC_FP32) || !U || !V || !B || !dD ||
+      !dU || !dV || !dB || k < 1 || k > 64 || ldb < f->d.N || lddb < f->d.N)
     return HODLR_ERR_ARG;
   const GradLayout lay = grad_layout(*f, k);
   if (!workspace || !aligned(workspace, kAlign) || workspace_bytes < lay.total) return HODLR_ERR_WORKSPACE;
-  hodlr_status st = grad_core(*f, U, V, B, ldb, k, dD, dU, dV, dB, lddb, static_cast<char*>(workspace), lay,
-                              reinterpret_cast<cudaStream_t>(stream), loss);
+  char* w = static_cast<char*>(workspace);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  hodlr_status st = f->prec == HODLR_PREC_FP64
+                        ? grad_core<double>(*f, U, V, B, ldb, k, dD, dU, dV, dB, lddb, w, lay, s, loss)
+                        : grad_core<float>(*f, U, V, B, ldb, k, dD, dU, dV, dB, lddb, w, lay, s, loss);
   if (st != HODLR_OK) return st;
   if (loss) {
     DevStatus ds{};
@@ -861,6 +926,8 @@ hodlr_status hodlr_grad(hodlr_factor_t f, const double* U, const double* V, cons
 int64_t hodlr_launch_count(void) { return g_launches.load(); }
 
 void hodlr_tc_enable(int32_t on) { g_use_tc = on != 0; }
+
+void hodlr_coupling_fp64_enable(int32_t on) { g_coupling_fp64 = on != 0; }
 
 void hodlr_profile_enable(int32_t on) { g_prof.store(on != 0); }
 

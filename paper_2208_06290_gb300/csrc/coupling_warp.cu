@@ -497,7 +497,7 @@ cudaError_t launch_coupling_factor_warp(const Factor& F, int c, cudaStream_t s) 
   const size_t sm = (size_t)kCwWarps * 3 * 32 * kCwLd * sizeof(double);
   // FP64 and FP32 factors: the whole inverse in FP64; BF16 factor: S and its
   // inverse in FP64, the products of the explicit inverse in FP32
-  const bool full = F.prec != HODLR_PREC_BF16;
+  const bool full = F.prec != HODLR_PREC_BF16 || g_coupling_fp64;
   if (full)
     cudaFuncSetAttribute(coupling_factor_warp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   else

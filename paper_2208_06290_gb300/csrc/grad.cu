@@ -26,8 +26,9 @@ cudaError_t launch_leaf_identity(int64_t N, int m, double* E, cudaStream_t s) {
 // out in the leaf-block layout of D (column-major m x m blocks), A and B
 // N x K column-major, Tadd N x m column-major (ld N). CTA = one leaf x a
 // 64 x 64 output tile; K streamed 32 at a time; 4 x 4 outputs per thread.
+template <typename TB>
 __global__ void __launch_bounds__(256) leaf_outer_kernel(int64_t N, int m, int K, const double* __restrict__ A,
-                                                         int64_t lda, const double* __restrict__ B, int64_t ldb,
+                                                         int64_t lda, const TB* __restrict__ B, int64_t ldb,
                                                          double alpha, double beta, const double* __restrict__ Tadd,
                                                          double* __restrict__ out) {
   __shared__ double sA[32][64 + 1];
@@ -46,7 +47,7 @@ __global__ void __launch_bounds__(256) leaf_outer_kernel(int64_t N, int m, int K
       const int ii = e & 63, kk = e >> 6;
       const int k = k0 + kk;
       sA[kk][ii] = (k < K && i0 + ii < m) ? A[(int64_t)k * lda + row0 + i0 + ii] : 0.0;
-      sB[kk][ii] = (k < K && j0 + ii < m) ? B[(int64_t)k * ldb + row0 + j0 + ii] : 0.0;
+      sB[kk][ii] = (k < K && j0 + ii < m) ? (double)B[(int64_t)k * ldb + row0 + j0 + ii] : 0.0;
     }
     __syncthreads();
 #pragma unroll 4
@@ -80,16 +81,22 @@ __global__ void __launch_bounds__(256) leaf_outer_kernel(int64_t N, int m, int K
   }
 }
 
-cudaError_t launch_leaf_outer(int64_t N, int m, int K, const double* A, int64_t lda, const double* B, int64_t ldb,
+template <typename TB>
+cudaError_t launch_leaf_outer(int64_t N, int m, int K, const double* A, int64_t lda, const TB* B, int64_t ldb,
                               double alpha, double beta, const double* Tadd, double* out, cudaStream_t s) {
   ProfScope prof_(KC_LEAF_MATVEC, s);
   const int nleaf = (int)(N / m);
-  note_work(8.0 * ((double)N * K * 2 + (double)N * m * (beta != 0.0 ? 2 : 1) + (Tadd ? (double)N * m : 0.0)),
+  note_work((8.0 + sizeof(TB)) * (double)N * K +
+                8.0 * ((double)N * m * (beta != 0.0 ? 2 : 1) + (Tadd ? (double)N * m : 0.0)),
             2.0 * (double)N * m * K);
   dim3 grid(nleaf, (m + 63) / 64, (m + 63) / 64);
-  { leaf_outer_kernel<<<grid, 256, 0, s>>>(N, m, K, A, lda, B, ldb, alpha, beta, Tadd, out); note_launches(1); }
+  { leaf_outer_kernel<TB><<<grid, 256, 0, s>>>(N, m, K, A, lda, B, ldb, alpha, beta, Tadd, out); note_launches(1); }
   return cudaGetLastError();
 }
+template cudaError_t launch_leaf_outer<double>(int64_t, int, int, const double*, int64_t, const double*, int64_t,
+                                               double, double, const double*, double*, cudaStream_t);
+template cudaError_t launch_leaf_outer<float>(int64_t, int, int, const double*, int64_t, const float*, int64_t,
+                                              double, double, const double*, double*, cudaStream_t);
 
 // H_alpha for the children of every parent at child level c, from
 // G = K~^{-T}: the first child gets G21 = G(r:2r, 0:r), the second G12 =

@@ -247,6 +247,8 @@ cudaError_t launch_solve_k1_chain(const Factor& F, const TB* Y, const TB* Vp, in
 // factors; their leaf solves are GEMMs with it.
 bool leaf_uses_inverse(const Factor& F);
 cudaError_t launch_leaf_inv(const Factor& F, const double* D, cudaStream_t s);
+bool leaf_inv_tc_supported(const Factor& F);
+cudaError_t launch_leaf_inv_tc(const Factor& F, const double* D, float* Dtc, cudaStream_t s);
 template <typename TIN, typename TOUT>
 cudaError_t launch_leaf_apply_inv(const Factor& F, const TIN* in, int64_t ldin, TOUT* out, int64_t ldout, int ncols,
                                   int trans, cudaStream_t s);
@@ -256,7 +258,8 @@ cudaError_t launch_coupling_apply_any(const Factor& F, int c, double* P, int64_t
                                       int trans, cudaStream_t s);
 // Gradient helpers (grad.cu)
 cudaError_t launch_leaf_identity(int64_t N, int m, double* E, cudaStream_t s);
-cudaError_t launch_leaf_outer(int64_t N, int m, int K, const double* A, int64_t lda, const double* B, int64_t ldb,
+template <typename TB>
+cudaError_t launch_leaf_outer(int64_t N, int m, int K, const double* A, int64_t lda, const TB* B, int64_t ldb,
                               double alpha, double beta, const double* Tadd, double* out, cudaStream_t s);
 cudaError_t launch_coupling_h(const Factor& F, int c, double* H, double* HT, cudaStream_t s);
 
@@ -284,6 +287,12 @@ cudaError_t launch_multidot(int64_t N, int k, const double* X, int64_t ldx, cons
 // w -= X h  (X N x k, h k device vector)
 cudaError_t launch_gemv_sub(int64_t N, int k, const double* X, int64_t ldx, const double* h, double* w,
                             cudaStream_t s);
+cudaError_t launch_bdots(int64_t N, int k, int nq, const double* V, const double* w, double* out, double* scratch,
+                         cudaStream_t s);
+cudaError_t launch_bgemv(int64_t N, int k, int nq, const double* V, const double* coef, double alpha, double* y,
+                         int64_t ldy, cudaStream_t s);
+cudaError_t launch_scale_inv_norm(int64_t N, int k, const double* w, const double* nrm2, double* out,
+                                  cudaStream_t s);
 cudaError_t launch_logdet_reduce(const Factor& F, cudaStream_t s);
 
 // Tensor-core (tcgen05 + TMA) projection of the BF16 factor; supported when
@@ -304,5 +313,6 @@ bool leaf_apply_tc_supported(const Factor& F);
 cudaError_t launch_leaf_apply_tc(const Factor& F, const double* U, int64_t ldu, cudaStream_t s);
 // Set by hodlr_tc_enable (process-wide; default on).
 extern bool g_use_tc;
+extern bool g_coupling_fp64;  // BF16 factor: form S = I - T_a T_b and the inverse's products in FP64
 
 }  // namespace hodlr

@@ -356,9 +356,7 @@ cudaError_t launch_leaf_solve(const Factor& F, const TIN* in, int64_t ldin, TOUT
                               int ncols, int trans, cudaStream_t s) {
   ProfScope prof_(KC_LEAF_SOLVE, s);
   if (ncols <= 0) return cudaSuccess;
-  if constexpr (!std::is_same<TIN, double>::value || !std::is_same<TOUT, double>::value) {
-    if (leaf_uses_inverse(F)) return launch_leaf_apply_inv<TIN, TOUT>(F, in, ldin, out, ldout, ncols, trans, s);
-  }
+  if (leaf_uses_inverse(F)) return launch_leaf_apply_inv<TIN, TOUT>(F, in, ldin, out, ldout, ncols, trans, s);
   if (F.prec == HODLR_PREC_FP64) return leaf_solve_tl<double>(F, in, ldin, out, ldout, ncols, trans, s);
   return leaf_solve_tl<float>(F, in, ldin, out, ldout, ncols, trans, s);
 }

@@ -227,7 +227,10 @@ bool leaf_uses_inverse(const Factor& F) { return F.prec != HODLR_PREC_FP64 && F.
 cudaError_t launch_leaf_inv(const Factor& F, const double* D, cudaStream_t s) {
   const int m = F.d.m;
   const int nleaf = 1 << F.d.L;
-  note_work((8.0 + 4.0) * nleaf * m * m, 2.0 * (double)m * m * m * nleaf);
+  // D_b read (FP64), D_b^{-1} written (FP32), plus its tensor-core operand copy
+  note_work((8.0 + 4.0 + (F.leaf_tc ? 4.0 : 0.0)) * nleaf * m * m, 2.0 * (double)m * m * m * nleaf);
+  if (leaf_inv_tc_supported(F))
+    return launch_leaf_inv_tc(F, D, F.leaf_tc ? reinterpret_cast<float*>(F.P) : nullptr, s);
   if (m > 64) {
     const size_t sm = (size_t)128 * 129 * 4;
     cudaFuncSetAttribute(leaf_inv_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -363,5 +366,7 @@ template cudaError_t launch_leaf_apply_inv<double, __nv_bfloat16>(const Factor&,
                                                                   __nv_bfloat16*, int64_t, int, int, cudaStream_t);
 template cudaError_t launch_leaf_apply_inv<float, float>(const Factor&, const float*, int64_t, float*, int64_t, int,
                                                          int, cudaStream_t);
+template cudaError_t launch_leaf_apply_inv<double, double>(const Factor&, const double*, int64_t, double*, int64_t,
+                                                           int, int, cudaStream_t);
 
 }  // namespace hodlr

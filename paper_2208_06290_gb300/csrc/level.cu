@@ -1114,6 +1114,7 @@ cudaError_t launch_logdet_reduce(const Factor& F, cudaStream_t s) {
   template cudaError_t launch_update<TB, TR>(int64_t, int, int, const TB*, int64_t, int, TR*, int64_t, int,   \
                                              const double*, int64_t, int, double, int, cudaStream_t);
 HODLR_INST(double, double)
+HODLR_INST(float, double)
 HODLR_INST(float, float)
 HODLR_INST(__nv_bfloat16, __nv_bfloat16)
 HODLR_INST(__nv_bfloat16, float)

@@ -28,6 +28,7 @@ hodlr_status matvec_core_ext(const hodlr_desc& d, const double* D, const double*
                              int64_t ldx, double* Y, int64_t ldy, int k, void* work, cudaStream_t s,
                              size_t work_bytes);
 size_t matvec_scratch_bytes(const hodlr_desc& d, int k);
+hodlr_status check_desc_ext(const hodlr_desc* d);
 
 namespace {
 
@@ -47,10 +48,8 @@ using namespace hodlr;
 extern "C" hodlr_status hodlr_matvec_noalloc(const hodlr_desc* desc, const double* D, const double* U,
                                              const double* V, const double* X, int64_t ldx, double* Y, int64_t ldy,
                                              int32_t k, hodlr_stream_t stream) {
-  if (!desc || desc->L < 1 || desc->L > 24 || desc->m < 1 || desc->m > 256 || desc->r < 1 || desc->r > 64 ||
-      desc->r > desc->m || desc->reserved != 0 || desc->N != ((int64_t)desc->m << desc->L) || desc->ldu < desc->N ||
-      desc->ldv < desc->N)
-    return HODLR_ERR_ARG;
+  const hodlr_status st = check_desc_ext(desc);  // the descriptor rules of every other entry point
+  if (st != HODLR_OK) return st;
   if (!D || !U || !V || !X || !Y || k < 1 || ldx < desc->N || ldy < desc->N || X == Y) return HODLR_ERR_ARG;
   if (matvec_scratch_bytes(*desc, k) > kNoAllocScratchBytes) return HODLR_ERR_SCRATCH_LIMIT;
   int dev = 0;

@@ -832,23 +832,6 @@ struct LeafTcSmem {
   static constexpr uint32_t kBytes = kBarOff + 64 + 128;
 };
 
-__host__ __device__ constexpr uint32_t idesc_tf32_f32(int M, int N) {
-  return (1u << 4)                     // D format: F32
-         | (2u << 7)                   // A format: TF32
-         | (2u << 10)                  // B format: TF32
-         | ((uint32_t)(N >> 3) << 17)  // N / 8
-         | ((uint32_t)(M >> 4) << 24); // M / 16
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
 }  // namespace
 
 __global__ void __launch_bounds__(256, 2) leaf_apply_tc_kernel(const __grid_constant__ CUtensorMap mapY,
@@ -933,11 +916,11 @@ __global__ void __launch_bounds__(256, 2) leaf_apply_tc_kernel(const __grid_cons
       }
       tc::tc_fence_after();
       if (tid == 0) {
-        const uint32_t idesc = idesc_tf32_f32(128, nc);
+        const uint32_t idesc = tc::idesc_tf32_f32(128, nc);
         const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
 #pragma unroll
         for (int ks = 0; ks < 16; ++ks)  // K = 8 per MMA: two cores along K
-          mma_tf32(tmem, tc::desc_noswz_kmajor(a0 + ks * 256, 128, kSBO),
+          tc::mma_tf32(tmem, tc::desc_noswz_kmajor(a0 + ks * 256, 128, kSBO),
                    tc::desc_noswz_kmajor(b0 + ks * 256, 128, kSBO), idesc, ks != 0);
         tc::mma_commit(bar_mma);
         mma_pending = true;

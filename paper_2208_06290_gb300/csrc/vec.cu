@@ -170,4 +170,77 @@ cudaError_t launch_gemv_sub(int64_t N, int k, const double* X, int64_t ldx, cons
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Batched Krylov-basis kernels of the lockstep multi-column FGMRES: basis
+// vector q of right-hand side j is column q * k + j of a column-major block
+// (ld N), so the q-th vectors of all k columns form one N x k matrix.
+
+// out[q * k + j] = V(:, q * k + j) . w(:, j) for q < nq, fixed-order two-stage
+// sums (stage 2 is dot_stage2 over the nb partials of each (q, j)).
+__global__ void bdot_stage1(int64_t N, int k, const double* __restrict__ V, const double* __restrict__ w,
+                            double* __restrict__ scratch) {
+  __shared__ double sh[256];
+  const int qj = blockIdx.y;
+  const int j = qj % k;
+  const double* v = V + (int64_t)qj * N;
+  const double* x = w + (int64_t)j * N;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    acc += v[i] * x[i];
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) scratch[(size_t)qj * gridDim.x + blockIdx.x] = t;
+}
+
+cudaError_t launch_bdots(int64_t N, int k, int nq, const double* V, const double* w, double* out, double* scratch,
+                         cudaStream_t s) {
+  ProfScope prof_(KC_VECTOR, s);
+  if (k <= 0 || nq <= 0) return cudaSuccess;
+  int64_t nb = (N + 255) / 256;
+  if (nb > kDotBlocks) nb = kDotBlocks;
+  note_work(8.0 * N * k * (nq + 1.0), 2.0 * N * k * nq);
+  { bdot_stage1<<<dim3((unsigned)nb, nq * k), 256, 0, s>>>(N, k, V, w, scratch); note_launches(1); }
+  { dot_stage2<<<nq * k, 256, 0, s>>>(scratch, (int)nb, out); note_launches(1); }
+  return cudaGetLastError();
+}
+
+// y(:, j) += alpha * sum_{q < nq} coef[q * k + j] V(:, q * k + j)   (coef on the device)
+__global__ void bgemv_kernel(int64_t N, int k, int nq, const double* __restrict__ V, const double* __restrict__ coef,
+                             double alpha, double* __restrict__ y, int64_t ldy) {
+  const int j = blockIdx.y;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int q = 0; q < nq; ++q) acc += V[(int64_t)(q * k + j) * N + i] * coef[q * k + j];
+    y[(int64_t)j * ldy + i] += alpha * acc;
+  }
+}
+
+cudaError_t launch_bgemv(int64_t N, int k, int nq, const double* V, const double* coef, double alpha, double* y,
+                         int64_t ldy, cudaStream_t s) {
+  ProfScope prof_(KC_VECTOR, s);
+  if (k <= 0 || nq <= 0) return cudaSuccess;
+  note_work(8.0 * N * k * (nq + 2.0), 2.0 * N * k * nq);
+  { bgemv_kernel<<<dim3(grid_for(N), k), 256, 0, s>>>(N, k, nq, V, coef, alpha, y, ldy); note_launches(1); }
+  return cudaGetLastError();
+}
+
+// out(:, j) = w(:, j) / sqrt(nrm2[j]) (0 where nrm2[j] is 0): the next Arnoldi
+// vectors, scaled on the device from the device norms.
+__global__ void scale_inv_norm_kernel(int64_t N, const double* __restrict__ w, const double* __restrict__ nrm2,
+                                      double* __restrict__ out) {
+  const int j = blockIdx.y;
+  const double nn = nrm2[j];
+  const double sc = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    out[(int64_t)j * N + i] = w[(int64_t)j * N + i] * sc;
+}
+
+cudaError_t launch_scale_inv_norm(int64_t N, int k, const double* w, const double* nrm2, double* out,
+                                  cudaStream_t s) {
+  ProfScope prof_(KC_VECTOR, s);
+  if (k <= 0) return cudaSuccess;
+  note_work(16.0 * N * k, 1.0 * N * k);
+  { scale_inv_norm_kernel<<<dim3(grid_for(N), k), 256, 0, s>>>(N, w, nrm2, out); note_launches(1); }
+  return cudaGetLastError();
+}
+
 }  // namespace hodlr

@@ -3,11 +3,12 @@
 The solver's input is the HODLR operator (D, U_big, V_big). These generators
 build it from a dense matrix that is never formed: leaf blocks are evaluated
 exactly, and every off-diagonal sibling block A(I_alpha, I_beta) is compressed
-to the fixed rank r: blocks up to 2048 rows by a randomized range finder with
-one power iteration (Gaussian test matrix, oversampling 10) evaluated tile by
-tile, larger blocks by a skeleton (CUR) approximation from 8r sampled rows
-and columns. The compression error is not part of the solver's problem: the
-oracle and the GPU path both take the generated (D, U, V) as the matrix.
+to the fixed rank r by a randomized SVD (range finder with one power
+iteration, Gaussian test matrix, oversampling 10), every block of every size
+evaluated tile by tile. The compression error is not part of the solver's
+problem: the oracle and the GPU path both take the generated (D, U, V) as the
+matrix; ``stats`` (when given a dict) receives, per level, an estimate of the
+relative compression error of the level's first blocks.
 
 Workloads (structure of the paper's Sec. 4 experiments; real field):
 * ``bie_hodlr``: 2D Laplace double-layer second-kind BIE on the star curve
@@ -177,53 +178,42 @@ def _rsvd_blocks(entries, row_start, col_start, n, r, g, device, oversample=10, 
     return Uo, Vo
 
 
-def _cur_blocks(entries, row_start, col_start, n, r, s, g, device, budget=1 << 27):
-    """Skeleton (CUR) approximation of large blocks from s sampled columns J
-    and rows I: K ~= K(:, J) K(I, J)^+ K(I, :), truncated to rank r through
-    the SVD of the s x s core. Costs O(n s) entries per block instead of n^2;
-    accurate for the smooth kernels used here."""
-    nblk = row_start.numel()
-    Uo = torch.empty(nblk, n, r, device=device)
-    Vo = torch.empty(nblk, n, r, device=device)
-    ar = torch.arange(n, device=device)
-    bs = max(1, budget // (n * s))
-    for b0 in range(0, nblk, bs):
-        b1 = min(nblk, b0 + bs)
-        nb = b1 - b0
-        J = torch.rand(nb, n, generator=g, device=device).argsort(dim=1)[:, :s].sort(dim=1).values
-        I = torch.rand(nb, n, generator=g, device=device).argsort(dim=1)[:, :s].sort(dim=1).values
-        rows = row_start[b0:b1, None] + ar[None, :]
-        cols = col_start[b0:b1, None] + ar[None, :]
-        C = entries(rows, col_start[b0:b1, None] + J)                          # (nb, n, s)
-        R = entries(row_start[b0:b1, None] + I, cols)                          # (nb, s, n)
-        W = entries(row_start[b0:b1, None] + I, col_start[b0:b1, None] + J)
-        Qc, Rc = _orth(C)                                                      # Q on the device, R on the CPU
-        Qr, Rr = _orth(R.transpose(1, 2))
-        W = W.double().cpu()                                                   # s x s cores: CPU, FP64
-        M = Rc @ torch.linalg.pinv(W, rtol=1e-12) @ Rr.transpose(1, 2)
-        Um, Sm, Vmh = torch.linalg.svd(M)
-        sq = torch.sqrt(Sm[:, :r])
-        Ucore = (Um[:, :, :r] * sq[:, None, :]).float().to(device)
-        Vcore = (Vmh.transpose(1, 2)[:, :, :r] * sq[:, None, :]).float().to(device)
-        Uo[b0:b1] = Qc @ Ucore
-        Vo[b0:b1] = Qr @ Vcore
-    return Uo, Vo
-
-
 def compress_blocks(entries, row_start, col_start, n, r, g, device):
-    """Rank-r factors of the n x n blocks at (row_start[b], col_start[b]):
-    randomized SVD up to n = 2048, CUR with 8r samples above."""
-    s = 8 * r
-    if n > 2048 and n > 2 * s:
-        return _cur_blocks(entries, row_start, col_start, n, r, s, g, device)
+    """Rank-r factors of the n x n blocks at (row_start[b], col_start[b]) by
+    the randomized SVD (Gaussian test matrix, oversampling 10, one power
+    iteration), at every block size."""
     return _rsvd_blocks(entries, row_start, col_start, n, r, g, device)
 
 
-def _assemble(shape: HodlrShape, leaf_fn, entries, seed, device, symmetric):
+def compression_error(entries, row_start, col_start, n, Ub, Vb, g, device, nprobe=4, budget=1 << 27):
+    """Relative error |(K - U V^T) w| / |K w| of the first blocks' rank-r
+    factors along nprobe Gaussian vectors w, blocks evaluated tile by tile
+    (an estimate of the spectral-norm error, for the record)."""
+    nb = min(int(row_start.numel()), 4)
+    ar = torch.arange(n, device=device)
+    tr = max(1, budget // max(n, 1))
+    errs = []
+    for b in range(nb):
+        w = torch.randn(n, nprobe, generator=g, device=device)
+        kw = torch.empty(n, nprobe, device=device)
+        for r0 in range(0, n, tr):
+            r1 = min(n, r0 + tr)
+            blk = entries((row_start[b] + ar[r0:r1])[None, :], (col_start[b] + ar)[None, :])[0]
+            kw[r0:r1] = blk @ w
+        uv = Ub[b] @ (Vb[b].T @ w)
+        errs.append(float((kw - uv).norm() / kw.norm().clamp(min=1e-300)))
+    return max(errs) if errs else 0.0
+
+
+def _assemble(shape: HodlrShape, leaf_fn, entries, seed, device, symmetric, stats=None):
     """D (column-major blocks), U, V (column-major N x rL) in FP64."""
     N, L, r, m = shape.N, shape.L, shape.r, shape.m
     g = torch.Generator(device=device)
     g.manual_seed(seed + 1000)
+    ge = torch.Generator(device=device)  # probes of the error estimates (leaves g's draws unchanged)
+    ge.manual_seed(seed + 2000)
+    if stats is not None:
+        stats.setdefault("compression_rel_err", {})
     Dt = torch.empty(shape.nleaf, m, m, device=device, dtype=torch.float64)
     step = max(1, (1 << 26) // (m * m))
     for b0 in range(0, shape.nleaf, step):
@@ -240,6 +230,9 @@ def _assemble(shape: HodlrShape, leaf_fn, entries, seed, device, symmetric):
             # blocks A(I_left, I_right) of the 2^(c-1) pairs; U = V by the symmetric split
             j = torch.arange(1 << (c - 1), device=device)
             Ub, Vb = compress_blocks(entries, 2 * j * n, (2 * j + 1) * n, n, r, g, device)
+            if stats is not None:
+                stats["compression_rel_err"][c] = compression_error(entries, 2 * j * n, (2 * j + 1) * n, n, Ub, Vb,
+                                                                    ge, device)
             for jj in range(1 << (c - 1)):
                 Ut[cols, (2 * jj) * n:(2 * jj + 1) * n] = Ub[jj].T.double()
                 Ut[cols, (2 * jj + 1) * n:(2 * jj + 2) * n] = Vb[jj].T.double()
@@ -248,6 +241,9 @@ def _assemble(shape: HodlrShape, leaf_fn, entries, seed, device, symmetric):
             # block b < 2^c: rows of node b, columns of its sibling b ^ 1
             b = torch.arange(1 << c, device=device)
             Ub, Vb = compress_blocks(entries, b * n, (b ^ 1) * n, n, r, g, device)
+            if stats is not None:
+                stats["compression_rel_err"][c] = compression_error(entries, b * n, (b ^ 1) * n, n, Ub, Vb, ge,
+                                                                    device)
             Ut[cols] = Ub.transpose(1, 2).permute(1, 0, 2).reshape(r, N).double()
             Vt[cols] = Vb[b ^ 1].transpose(1, 2).permute(1, 0, 2).reshape(r, N).double()
         if _VERBOSE:
@@ -257,7 +253,7 @@ def _assemble(shape: HodlrShape, leaf_fn, entries, seed, device, symmetric):
     return D, Ut.T, Vt.T
 
 
-def bie_hodlr(shape: HodlrShape, device="cpu", seed=2):
+def bie_hodlr(shape: HodlrShape, device="cpu", seed=2, stats=None):
     """HODLR operator of the star-curve Laplace BIE (see module doc)."""
     shape.validate()
     N, m = shape.N, shape.m
@@ -275,10 +271,11 @@ def bie_hodlr(shape: HodlrShape, device="cpu", seed=2):
     def entries(rows, cols):
         return bie_block(x32, n32, w32, rows, cols)
 
-    return _assemble(shape, leaf_fn, entries, seed, device, symmetric=False)
+    return _assemble(shape, leaf_fn, entries, seed, device, symmetric=False, stats=stats)
 
 
-def kernel_hodlr(shape: HodlrShape, dim: int, kind: str, scale: float, nugget: float, device="cpu", seed=1):
+def kernel_hodlr(shape: HodlrShape, dim: int, kind: str, scale: float, nugget: float, device="cpu", seed=1,
+                 stats=None):
     """HODLR operator of a symmetric kernel matrix on kd-ordered uniform points.
     kind 'gaussian': exp(-d^2 / (2 scale^2)); kind 'matern32':
     (1 + sqrt(3) d / scale) exp(-sqrt(3) d / scale). Returns (D, U, V, points)."""
@@ -309,5 +306,5 @@ def kernel_hodlr(shape: HodlrShape, dim: int, kind: str, scale: float, nugget: f
         d2 = ((p32[rows][:, :, None, :] - p32[cols][:, None, :, :]) ** 2).sum(-1)
         return kfun(d2)
 
-    D, U, V = _assemble(shape, leaf_fn, entries, seed, device, symmetric=True)
+    D, U, V = _assemble(shape, leaf_fn, entries, seed, device, symmetric=True, stats=stats)
     return D, U, V, pts

@@ -6,6 +6,7 @@ import os
 import re
 
 import pytest
+import torch
 
 from oracle import costs as ocosts
 
@@ -16,7 +17,7 @@ HEADER = os.path.join(ROOT, "include", "hodlr.h")
 def _declared():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(hodlr_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(hodlr_[a-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -87,3 +88,28 @@ def test_product_costs_equal_oracle_loop_counts(N, m, r, L):
     for k in (1, 3):
         assert costs.solve_flops(N, m, r, L, k) == pytest.approx(ocosts.loop_solve_flops(N, m, r, L, k), rel=1e-12)
         assert costs.matvec_flops(N, m, r, L, k) == pytest.approx(ocosts.matvec_flops(N, m, r, L, k), rel=1e-12)
+
+
+def test_binding_rejects_mismatched_widths_before_the_c_call(hb):
+    """A Y narrower than X would let the kernels write past Y's end: the
+    binding refuses it before any pointer reaches the library (CPU tensors
+    suffice, the check comes first)."""
+    N, L, r = 256, 2, 4
+    D = torch.zeros(1 << L, N >> L, N >> L, dtype=torch.float64).transpose(1, 2)
+    U = torch.zeros(r * L, N, dtype=torch.float64).T
+    X = torch.zeros(3, N, dtype=torch.float64).T
+    Y = torch.zeros(1, N, dtype=torch.float64).T
+    for fn in (hb.hodlr_matvec_noalloc, hb.hodlr_matvec):
+        with pytest.raises(ValueError, match="same number of columns"):
+            fn(D, U, U, L, r, X, Y)
+
+
+def test_binding_rejects_operands_off_the_current_device(hb):
+    N, L, r = 256, 2, 4
+    D = torch.zeros(1 << L, N >> L, N >> L, dtype=torch.float64).transpose(1, 2)
+    U = torch.zeros(r * L, N, dtype=torch.float64).T
+    X = torch.zeros(2, N, dtype=torch.float64).T
+    with pytest.raises(ValueError, match="CUDA"):
+        hb.hodlr_matvec_noalloc(D, U, U, L, r, X, X.clone())
+    with pytest.raises(ValueError, match="CUDA"):
+        hb._on_current_device(X)
