@@ -138,9 +138,11 @@ def make_inputs(w, device, rank=0, stats=None):
         if w["data"] == "bie":
             D, U, V = bie_hodlr(shape, device=device, seed=w["seed"], stats=stats)
         elif w["data"] == "gaussian":
-            D, U, V, _ = kernel_hodlr(shape, 2, "gaussian", 0.1, 1e-2, device=device, seed=w["seed"], stats=stats)
+            D, U, V, pts = kernel_hodlr(shape, 2, "gaussian", 0.1, 1e-2, device=device, seed=w["seed"], stats=stats)
         else:
-            D, U, V, _ = kernel_hodlr(shape, 3, "matern32", 0.2, 1e-3, device=device, seed=w["seed"], stats=stats)
+            D, U, V, pts = kernel_hodlr(shape, 3, "matern32", 0.2, 1e-3, device=device, seed=w["seed"], stats=stats)
+        if stats is not None and w["data"] != "bie":
+            stats["points"] = pts
         g = torch.Generator(device=device)
         g.manual_seed(w["seed"] + 1000 * rank)
     else:
@@ -284,12 +286,12 @@ def run_native(args, w, rank, world):
     def step():
         F = hb.hodlr_factor(D, U, V, L, r, prec)
         if w["solver"] == "gmres":
-            _, it, rr, code = hb.hodlr_gmres(F, D, U, V, B, tol=1e-10, restart=30, max_iter=300, X=X,
-                                             raise_on_fail=False)
+            _, it, rr, code = hb.hodlr_gmres(F, D, U, V, B, tol=1e-10, restart=30, max_iter=args.gmres_max_iter,
+                                             X=X, raise_on_fail=False)
         elif w["solver"] == "refine":
             _, it, rr, code = hb.hodlr_solve_refined(F, D, U, V, B, tol=1e-10, max_iter=50, X=X,
                                                      raise_on_fail=False, restart=w.get("restart", 0),
-                                                     gmres_max_iter=300)
+                                                     gmres_max_iter=args.gmres_max_iter)
         else:
             X.copy_(B)
             hb.hodlr_solve(F, X)
@@ -454,6 +456,59 @@ def run_native(args, w, rank, world):
         del g32, g64
         torch.cuda.empty_cache()
 
+    # the relative residual any FP64 solver can be expected to reach on this
+    # operator: about eps |A|_2 |x| / |b| (backward-stable arithmetic); |A|_2
+    # by power iteration on A (symmetric kernels) or A^T A (the BIE, with the
+    # transposed operator D_b^T, U <-> V)
+    def norm2_estimate(iters=20):
+        sym = w["data"] in ("gaussian", "matern")
+        Dt = None
+        if not sym:  # D_b^T in the column-major block layout
+            Dt = torch.empty_like(D.transpose(1, 2).contiguous()).transpose(1, 2)
+            Dt.copy_(D.transpose(1, 2))
+        g = torch.Generator(device=dev).manual_seed(11)
+        v = torch.randn(1, N, generator=g, device=dev, dtype=torch.float64).T
+        lam = 0.0
+        for _ in range(iters):
+            v = v / v.norm()
+            y = hb.hodlr_matvec(D, U, V, L, r, v)
+            if sym:
+                lam = float(y.norm().item())
+            else:
+                y = hb.hodlr_matvec(Dt, V, U, L, r, y)
+                lam = math.sqrt(float(y.norm().item()))
+            v = y
+        return lam
+
+    normA = norm2_estimate()
+    xn = float((X.norm(dim=0) / B.norm(dim=0)).max().item())
+    attainable = {"norm2_A_estimate": normA, "max_x_over_b": xn,
+                  "eps_normA_x_over_b": 1.1102230246251565e-16 * normA * xn}
+
+    # GPU construction of the same operator family (hodlr_compress: exact leaf
+    # blocks, partial-pivoted cross approximation at rank r), timed alone
+    construction = None
+    if w["data"] in ("bie", "gaussian", "matern"):
+        kind = {"bie": "bie_star", "gaussian": "gaussian", "matern": "matern32"}[w["data"]]
+        ckw = {"gaussian": dict(scale=0.1, nugget=1e-2), "matern": dict(scale=0.2, nugget=1e-3)}.get(w["data"], {})
+        pts = gen_stats.get("points")
+
+        def build_op():
+            return hb.hodlr_compress(N, L, r, kind, pts, **ckw)
+
+        t_c = timed(lambda: build_op(), 2)
+        Dc, Uc, Vc = build_op()
+        # relative difference from the randomized-SVD operator the step factors
+        # (both approximate the same dense matrix; sampled rows, FP64 matvec)
+        probe = torch.randn(1, N, generator=torch.Generator(device=dev).manual_seed(9), device=dev,
+                            dtype=torch.float64).T
+        y_c = hb.hodlr_matvec(Dc, Uc, Vc, L, r, probe)
+        y_g = hb.hodlr_matvec(D, U, V, L, r, probe)
+        construction = {"seconds": t_c, "kernel": kind, "rank": r, "method": "partial-pivoted cross approximation",
+                        "rel_diff_vs_rsvd_operator_on_random_vector": float(((y_c - y_g).norm() / y_g.norm()).item())}
+        del Dc, Uc, Vc, y_c, y_g
+        torch.cuda.empty_cache()
+
     # FP64 pipe rate of this GPU, measured by the library's register-only
     # FMA probe (CUDA events on the launching stream, best of three)
     pk = peaks()
@@ -510,13 +565,16 @@ def run_native(args, w, rank, world):
                    "l2": "inputs larger than L2 (D, U, V = %.1f GB FP64)" % (8.0 * (m * N + 2 * r * N * L) / 1e9),
                    "kernel_classes_from": f"separate profiled pass of {nprof} steps after the timed region",
                    "restart": w.get("restart", 30 if w["solver"] == "gmres" else 0),
+                   "gmres_max_iter": args.gmres_max_iter,
                    "compression_rel_err_by_level": {str(c): float(f"{e:.3g}") for c, e in
                                                     gen_stats.get("compression_rel_err", {}).items()}},
-        "mixed": {"iterations": iters, "relres_reported": relres, "relres_fp64_matvec": rel_true, **err_vs_fp64},
+        "mixed": {"iterations": iters, "relres_reported": relres, "relres_fp64_matvec": rel_true, **err_vs_fp64,
+                  "attainable_relres_bound": attainable},
         "fp64": fp64,
         "e2e": e2e,
         "adjoint": adjoint,
         "grad": grad,
+        "construction": construction,
         "roofline": roof,
         "fp64_pipe_measured": fp64_meas,
         "kernel_time_share": share,
@@ -633,12 +691,22 @@ def main(argv=None):
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--prec", choices=["fp64", "fp32", "bf16"], default=None,
+                    help="override the workload's factor precision")
+    ap.add_argument("--solver", choices=["direct", "refine", "gmres"], default=None,
+                    help="override the workload's outer solver")
+    ap.add_argument("--gmres-max-iter", type=int, default=300,
+                    help="FGMRES inner-iteration cap (the outer solver or the refinement's continuation)")
     ap.add_argument("--coupling-fp64", action="store_true",
                     help="BF16 factor: form the coupling products in FP64 (precision experiment)")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "native":
         ap.error("--warmup must be >= 3")
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.prec:
+        w["prec"] = args.prec
+    if args.solver:
+        w["solver"] = args.solver
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -117,6 +117,19 @@ HODLR_API hodlr_status hodlr_factor(const hodlr_desc* desc, const double* D, con
                           hodlr_prec prec, void* workspace, size_t workspace_bytes,
                           hodlr_stream_t stream, hodlr_factor_t* out);
 
+/* In-place FP64 factorization (Sec. 3.2: the leaf LUs and Y_big take the
+ * place of D and U_big): as hodlr_factor with HODLR_PREC_FP64, but the leaf
+ * LU factors overwrite D (same block layout) and Y_big (D^{-1} U_big after
+ * the level updates of Eq. e:node2) overwrites U, which must have ldu == N;
+ * the workspace holds neither. The factor keeps using D, U and V: the caller must keep them
+ * allocated and unchanged while the factor is in use, and keep its own copy of
+ * the operator for residuals (hodlr_matvec, the refined solvers). V must not
+ * alias U. */
+HODLR_API hodlr_status hodlr_factor_inplace_workspace_size(const hodlr_desc* desc, size_t* bytes);
+HODLR_API hodlr_status hodlr_factor_inplace(const hodlr_desc* desc, double* D, double* U, const double* V,
+                                            void* workspace, size_t workspace_bytes, hodlr_stream_t stream,
+                                            hodlr_factor_t* out);
+
 /* Synchronizes the factor's stream and returns the first device-side error
  * (HODLR_OK if none). where / detail (may be NULL) locate it: leaf index and
  * column for a leaf, heap node number (root = 1) and column for a coupling. */
@@ -202,13 +215,18 @@ HODLR_API hodlr_status hodlr_matvec_noalloc(const hodlr_desc* desc, const double
  *   starting from X = f^{-1} B, until max_j |b_j - A x_j| / |b_j| <= tol or
  *   max_iter corrections; it stops early when the residual grows twice in a
  *   row. If tol is not reached then and restart > 0, flexible GMRES(restart)
- *   continues from the refined X for at most gmres_max_iter inner iterations
- *   (restart = 0: no continuation; the workspace then holds no Krylov basis).
+ *   continues from the best refined iterate for at most gmres_max_iter inner
+ *   iterations (restart = 0: no continuation; the workspace then holds no
+ *   Krylov basis).
  * hodlr_gmres: flexible GMRES (restart length `restart`, at most max_iter
  *   inner iterations in total) right-preconditioned by f, started from
  *   X = f^{-1} B, stopping on the FP64 residual <= tol. Per cycle the residual
  *   is b - A x of the first iterate (one FP64 matvec) and then r - (A Z) y
- *   from the stored FP64 products A z_i. Classical Gram-Schmidt twice, per
+ *   from the stored FP64 products A z_i; when that recursive residual meets
+ *   tol while its accumulated rounding bound (about eps sum |y_i| |A z_i|, the
+ *   drift between it and b - A x on ill-conditioned operators) could exceed
+ *   tol / 100, b - A x is recomputed and iteration continues from it.
+ *   Classical Gram-Schmidt twice, per
  *   column; a column whose residual estimate has converged stops extending
  *   its basis while the others continue.
  * Both write the solution to X (N x k, ldx), leave B unchanged, return
@@ -258,6 +276,60 @@ HODLR_API hodlr_status hodlr_grad_workspace_size(hodlr_factor_t f, int32_t k, si
 HODLR_API hodlr_status hodlr_grad(hodlr_factor_t f, const double* U, const double* V, const double* B, int64_t ldb,
                                   int32_t k, double* dD, double* dU, double* dV, double* dB, int64_t lddb,
                                   void* workspace, size_t workspace_bytes, hodlr_stream_t stream, double* loss);
+
+/* ----------------------------------------------------------- construction --
+ * GPU construction of the HODLR approximation (Sec. 2.2) of a built-in
+ * kernel or boundary-integral matrix, in the layout every other entry point
+ * takes. Leaf blocks D_b are evaluated exactly in FP64. Every off-diagonal
+ * sibling block A(I_alpha, I_beta) is compressed to the fixed rank r of desc
+ * by a partial-pivoted cross approximation (the approximate partial-pivoted
+ * LU the paper's kernel experiments used for this step): with i_0 the
+ * block's first row, for k = 0 .. r-1 the residual row at i_k, its largest
+ * entry (column j_k, first maximum among unused columns), v_k = row / that
+ * entry, the residual column u_k at j_k and i_{k+1} = its largest entry among
+ * the unused rows; A(I_alpha, I_beta) ~= sum u_k v_k^T = U_alpha V_beta^T.
+ * A block whose residual vanishes keeps zero bases from then on. Entries and
+ * residual updates are FP32 (the bases are stored in FP64). For the symmetric
+ * kernel matrices one cross per sibling pair gives both blocks, so U = V.
+ *
+ * Kernels (hodlr_kernel_desc.kind):
+ *   HODLR_KERNEL_BIE_STAR: 2D Laplace double-layer second-kind BIE on the
+ *     star curve rho(t) = 1 + 0.3 cos 5t, N trapezoid nodes t_i = 2 pi i / N
+ *     in curve order: A = -1/2 I + D, D(i, j) = n_j.(x_i - x_j) /
+ *     (2 pi |x_i - x_j|^2) w_j (n the outward normal, w_j = |gamma'(t_j)|
+ *     2 pi / N), diagonal -1/2 - w_i kappa_i / (4 pi) (kappa the curvature);
+ *     points, dim, scale and nugget are ignored.
+ *   HODLR_KERNEL_GAUSSIAN: exp(-|x_i - x_j|^2 / (2 scale^2)) + nugget delta_ij;
+ *   HODLR_KERNEL_MATERN32: (1 + sqrt(3) d / scale) exp(-sqrt(3) d / scale)
+ *     + nugget delta_ij, d = |x_i - x_j|;
+ *   for these two, points is a DEVICE array of N points of dim (1..3) FP64
+ *   coordinates, point i at points + i * dim, already in the cluster tree's
+ *   order (node i of level c owns points i N / 2^c ..).
+ * D, U, V are outputs in the layout of hodlr_factor (ldu, ldv of desc).
+ * pivots (optional, device, 2 r (2^(L+1) - 2) int32): per level c = 1..L at
+ * offset 2 r (2^c - 2), the pivot rows [block][k] then the pivot columns
+ * [block][k] (indices local to the block; -1 after a vanished residual); the
+ * blocks of level c are its 2^c nodes (row node = block; for a symmetric
+ * kernel only the even ones are used). Workspace:
+ * hodlr_compress_workspace_size. Enqueued on the stream; no allocation. */
+typedef enum {
+  HODLR_KERNEL_BIE_STAR = 0,
+  HODLR_KERNEL_GAUSSIAN = 1,
+  HODLR_KERNEL_MATERN32 = 2
+} hodlr_kernel;
+
+typedef struct {
+  int32_t kind;          /* hodlr_kernel */
+  int32_t dim;           /* point dimension, 1..3 (kernel matrices) */
+  const double* points;  /* device, N x dim (kernel matrices), NULL for the BIE */
+  double scale;          /* Gaussian sigma / Matern lengthscale */
+  double nugget;         /* added to the diagonal (kernel matrices) */
+} hodlr_kernel_desc;
+
+HODLR_API hodlr_status hodlr_compress_workspace_size(const hodlr_desc* desc, size_t* bytes);
+HODLR_API hodlr_status hodlr_compress(const hodlr_desc* desc, const hodlr_kernel_desc* kern, double* D, double* U,
+                                      double* V, int32_t* pivots, void* workspace, size_t workspace_bytes,
+                                      hodlr_stream_t stream);
 
 /* ------------------------------------------------------------ diagnostics --
  * Accounting of the library's own kernel launches, for benchmarks; not part

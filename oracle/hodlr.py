@@ -342,3 +342,50 @@ def grad_blocks(rec: RecursiveHODLR, B, leaves=(), pairs=()):
         out[("U", c, a)] = -Lam[ra] @ (X[rs].T @ Vs) + recT.solve(embed(t, rs, Vs))[ra]
         out[("V", c, sib)] = -X[rs] @ (Lam[ra].T @ Ua) + rec.solve(embed(t, ra, Ua))[rs]
     return out
+
+
+# --------------------------------------------------------------------------
+# Construction (Sec. 2.2): partial-pivoted cross approximation of one block
+# --------------------------------------------------------------------------
+def cross_approximation(M, r, rows=None, cols=None):
+    """Rank-r partial-pivoted cross approximation of the dense block M
+    (n x n'), in FP64: i_0 = 0; for k = 0 .. r-1 the residual row
+    rho = M(i_k, :) - sum_{l<k} u_l(i_k) v_l, its largest entry among unused
+    columns j_k (first maximum), v_k = rho / rho(j_k), the residual column
+    u_k = M(:, j_k) - sum_{l<k} v_l(j_k) u_l, and i_{k+1} the largest entry of
+    |u_k| among unused rows (first maximum). A vanishing residual ends the
+    approximation (remaining columns zero). With `rows`, `cols` given (pivot
+    sequences, -1 = ended), those pivots are taken instead of the maxima.
+    Returns (U (n x r), V (n' x r), rows, cols) with M ~= U V^T."""
+    M = np.asarray(M, dtype=np.float64)
+    n, n2 = M.shape
+    U = np.zeros((n, r))
+    V = np.zeros((n2, r))
+    prow, pcol = [], []
+    i = 0
+    for k in range(r):
+        if rows is not None:
+            i = rows[k]
+        if i < 0:
+            break
+        prow.append(i)
+        rho = M[i, :] - U[i, :k] @ V[:, :k].T
+        if cols is not None:
+            j = cols[k]
+            if j < 0:
+                break
+        else:
+            a = np.abs(rho)
+            a[pcol] = -1.0
+            j = int(np.argmax(a))
+            if rho[j] == 0.0:
+                break
+        pcol.append(j)
+        V[:, k] = rho / rho[j]
+        U[:, k] = M[:, j] - U[:, :k] @ V[j, :k]
+        a = np.abs(U[:, k])
+        a[prow] = -1.0
+        i = int(np.argmax(a))
+        if a[i] <= 0.0:
+            i = -1
+    return U, V, prow, pcol

@@ -24,7 +24,7 @@ class HodlrSolveLogdet(torch.autograd.Function):
         if prec not in ("fp64", "fp32"):
             raise ValueError("prec must be 'fp64' or 'fp32'")
         F = hb.hodlr_factor(D, U, V, L, r, prec)
-        X = hb.hodlr_solve(F, B.detach().T.contiguous().T)
+        X = hb.hodlr_solve(F, B.detach().clone())  # clone keeps B's column-major strides
         _, logabsdet = hb.hodlr_logdet(F)
         ctx.F = F
         ctx.save_for_backward(U, V, B)

@@ -41,7 +41,16 @@ EXPORTED = (
     "hodlr_gmres", "hodlr_launch_count", "hodlr_profile_enable", "hodlr_profile_reset", "hodlr_profile_read",
     "hodlr_profile_name", "hodlr_profile_work", "hodlr_tc_enable", "hodlr_grad_workspace_size", "hodlr_grad",
     "hodlr_matvec_noalloc", "hodlr_probe_fp64_fma", "hodlr_coupling_fp64_enable",
+    "hodlr_compress_workspace_size", "hodlr_compress", "hodlr_factor_inplace_workspace_size",
+    "hodlr_factor_inplace",
 )
+
+KERNEL = {"bie_star": 0, "gaussian": 1, "matern32": 2}
+
+
+class hodlr_kernel_desc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("dim", ctypes.c_int32), ("points", ctypes.c_void_p),
+                ("scale", ctypes.c_double), ("nugget", ctypes.c_double)]
 
 
 class HodlrError(RuntimeError):
@@ -82,6 +91,10 @@ _SIGS = {
     "hodlr_profile_work": ([_c.POINTER(_dbl), _c.POINTER(_dbl), _i32], _i32),
     "hodlr_tc_enable": ([_i32], None),
     "hodlr_coupling_fp64_enable": ([_i32], None),
+    "hodlr_compress_workspace_size": ([_vp, _c.POINTER(_sz)], _c.c_int),
+    "hodlr_compress": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _c.c_int),
+    "hodlr_factor_inplace_workspace_size": ([_vp, _c.POINTER(_sz)], _c.c_int),
+    "hodlr_factor_inplace": ([_vp, _vp, _vp, _vp, _vp, _sz, _vp, _c.POINTER(_vp)], _c.c_int),
     "hodlr_matvec_noalloc": ([_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64, _i32, _vp], _c.c_int),
     "hodlr_probe_fp64_fma": ([_i64, _i32, _vp, _vp, _c.POINTER(_i64)], _c.c_int),
     "hodlr_grad_workspace_size": ([_vp, _i32, _c.POINTER(_sz)], _c.c_int),
@@ -205,6 +218,24 @@ def hodlr_factor(D, U, V, L: int, r: int, prec: str = "fp64") -> FactorHandle:
     _check(_LIB.hodlr_factor(ctypes.byref(desc), _ptr(D), _ptr(U), _ptr(V), PREC[prec], _ptr(ws), ws.numel(),
                              _stream(), ctypes.byref(h)), "hodlr_factor: ")
     return FactorHandle(h, desc, prec, ws, (V,) if prec == "fp64" else ())
+
+
+def hodlr_factor_inplace(D, U, V, L: int, r: int) -> FactorHandle:
+    """FP64 factorization that overwrites D with the leaf LUs and U (leading
+    dimension N) with Y_big; the returned factor keeps D, U and V alive."""
+    N = U.shape[0]
+    _check_D(D, N, L)
+    _on_current_device(D, U, V)
+    desc = make_desc(N, L, r, U, V)
+    if desc.ldu != N or U.shape[1] != r * L or V.shape[1] != r * L:
+        raise ValueError("U must be (N, r L) with leading dimension N; V (N, r L)")
+    out = ctypes.c_size_t()
+    _check(_LIB.hodlr_factor_inplace_workspace_size(ctypes.byref(desc), ctypes.byref(out)))
+    ws = _workspace(out.value, U.device)
+    h = ctypes.c_void_p()
+    _check(_LIB.hodlr_factor_inplace(ctypes.byref(desc), _ptr(D), _ptr(U), _ptr(V), _ptr(ws), ws.numel(), _stream(),
+                                     ctypes.byref(h)), "hodlr_factor_inplace: ")
+    return FactorHandle(h, desc, "fp64", ws, (D, U, V))
 
 
 def hodlr_factor_status(F: FactorHandle):
@@ -420,3 +451,39 @@ def hodlr_matvec_noalloc(D, U, V, L: int, r: int, X: torch.Tensor, Y: torch.Tens
     _check(_LIB.hodlr_matvec_noalloc(ctypes.byref(desc), _ptr(D), _ptr(U), _ptr(V), _ptr(X), ldx, _ptr(Y), ldy,
                                      X.shape[1], _stream()), "hodlr_matvec_noalloc: ")
     return Y
+
+
+# --------------------------------------------------------------- construction
+def hodlr_compress(N: int, L: int, r: int, kind: str, points: torch.Tensor | None = None, scale: float = 1.0,
+                   nugget: float = 0.0, want_pivots: bool = False, device=None):
+    """(D, U, V[, pivots]) of the HODLR approximation of a built-in kernel or
+    BIE matrix, built on the GPU (leaf blocks exact, off-diagonal blocks by a
+    partial-pivoted cross approximation at rank r). points: (N, dim) float64
+    CUDA tensor in tree order (kernel matrices), None for 'bie_star'."""
+    if kind not in KERNEL:
+        raise ValueError(f"kind must be one of {sorted(KERNEL)}")
+    m = N >> L
+    if device is None:
+        device = points.device if points is not None else torch.device("cuda", torch.cuda.current_device())
+    dim = 0
+    if points is not None:
+        if points.dim() != 2 or points.shape[0] != N or not points.is_contiguous() or points.dtype != torch.float64:
+            raise ValueError("points must be a contiguous (N, dim) float64 tensor")
+        _on_current_device(points)
+        dim = points.shape[1]
+    elif kind != "bie_star":
+        raise ValueError("kernel matrices need points")
+    desc = hodlr_desc(N=N, L=L, m=m, r=r, reserved=0, ldu=N, ldv=N)
+    kd = hodlr_kernel_desc(kind=KERNEL[kind], dim=dim, points=points.data_ptr() if points is not None else None,
+                           scale=float(scale), nugget=float(nugget))
+    D = torch.empty(1 << L, m, m, dtype=torch.float64, device=device).transpose(1, 2)
+    U = torch.empty(r * L, N, dtype=torch.float64, device=device).T
+    V = torch.empty(r * L, N, dtype=torch.float64, device=device).T
+    piv = torch.empty(2 * r * ((2 << L) - 2), dtype=torch.int32, device=device) if want_pivots else None
+    out = ctypes.c_size_t()
+    _check(_LIB.hodlr_compress_workspace_size(ctypes.byref(desc), ctypes.byref(out)))
+    ws = _workspace(out.value, device)
+    _check(_LIB.hodlr_compress(ctypes.byref(desc), ctypes.byref(kd), _ptr(D), _ptr(U), _ptr(V),
+                               _ptr(piv) if piv is not None else None, _ptr(ws), ws.numel(), _stream()),
+           "hodlr_compress: ")
+    return (D, U, V, piv) if want_pivots else (D, U, V)

@@ -39,7 +39,7 @@ long long g_n[KC_COUNT];
 double g_bytes[KC_COUNT], g_flops[KC_COUNT];
 const char* kClassName[KC_COUNT] = {"leaf_lu", "leaf_solve", "project", "coupling", "coupling_apply",
                                     "update", "reduce_chunks", "leaf_matvec", "vector", "logdet",
-                                    "project_tc", "update_tc", "matvec"};
+                                    "project_tc", "update_tc", "matvec", "compress"};
 
 cudaEvent_t pool_get() {
   std::lock_guard<std::mutex> g(g_mu);
@@ -115,7 +115,9 @@ size_t max_partial_elems(const hodlr_desc& d, int ncols_per_level_factor, int k)
   return best;
 }
 
-Layout factor_layout(const hodlr_desc& d, hodlr_prec prec) {
+// inplace (FP64 only): the leaf LUs overwrite the caller's D and Y_big its U
+// (ldu = N), so neither is part of the workspace.
+Layout factor_layout(const hodlr_desc& d, hodlr_prec prec, bool inplace = false) {
   Layout l{};
   const size_t nleaf = (size_t)1 << d.L;
   const size_t N = (size_t)d.N;
@@ -128,9 +130,9 @@ Layout factor_layout(const hodlr_desc& d, hodlr_prec prec) {
   l.ld_out = take(2 * sizeof(double));
   l.leaf_ld = take(nleaf * 2 * sizeof(double));
   l.node_ld = take((nleaf - 1) * 2 * sizeof(double) + 16);
-  l.lu = take(nleaf * d.m * d.m * tl);
-  l.perm = take(N * sizeof(int));
-  l.Y = take(N * rL * tp);
+  l.lu = inplace ? 0 : take(nleaf * d.m * d.m * tl);
+  l.perm = take(2 * N * sizeof(int));  // LU: row permutations; inverse form: p and step (see leaf_inv*.cu)
+  l.Y = inplace ? 0 : take(N * rL * tp);
   l.Vp = prec == HODLR_PREC_FP64 ? 0 : take(N * rL * tp);
   l.K = take((nleaf - 1) * 4 * (size_t)d.r * d.r * sizeof(double) + 16);
   {
@@ -174,9 +176,16 @@ hodlr_status factor_levels(Factor& F, cudaStream_t s) {
   for (int c = d.L; c >= 1; --c) {
     const int rc = d.r * c;
     const int anc = d.r * (c - 1);
+    // levels where every node is one row chunk and the fused tensor-core update
+    // follows: the projection writes the ancestor columns straight into the
+    // update's BF16 right-hand-side operand
+    bool rhs_ready = false;
     if constexpr (std::is_same<TP, __nv_bfloat16>::value) {
+      rhs_ready = g_use_tc && anc > 0 && project_tc_supported(d.N, d.r, c) && update_tc_supported(d.N, d.r, c) &&
+                  chunks_per_node(d.N, c) == 1;
       if (g_use_tc && project_tc_supported(d.N, d.r, c))
-        HODLR_CUDA(launch_project_tc(d.N, d.r, d.L, c, Vp, F.ldvp, Y, F.P, F.status, s));
+        HODLR_CUDA(launch_project_tc(d.N, d.r, d.L, c, Vp, F.ldvp, Y, F.P, F.status, s,
+                                     rhs_ready ? F.rhs16 : nullptr));
       else
         HODLR_CUDA(launch_project<TP, TP>(d.N, d.r, c, Vp, F.ldvp, c - 1, Y, d.N, rc, F.P, 0, s));
     } else {
@@ -191,7 +200,7 @@ hodlr_status factor_levels(Factor& F, cudaStream_t s) {
       if constexpr (std::is_same<TP, __nv_bfloat16>::value) {
         if (g_use_tc && update_tc_supported(d.N, d.r, c)) {
           // W' = K~^{-1} [W_beta; W_alpha] applied inside the update
-          HODLR_CUDA(launch_update_coupled_tc(F, c, s));
+          HODLR_CUDA(launch_update_coupled_tc(F, c, s, rhs_ready));
           done = true;
         }
       }
@@ -346,14 +355,15 @@ hodlr_status hodlr_factor_workspace_size(const hodlr_desc* desc, hodlr_prec prec
   return HODLR_OK;
 }
 
-hodlr_status hodlr_factor(const hodlr_desc* desc, const double* D, const double* U, const double* V,
-                          hodlr_prec prec, void* workspace, size_t workspace_bytes, hodlr_stream_t stream,
-                          hodlr_factor_t* out) {
+static hodlr_status factor_entry(const hodlr_desc* desc, const double* D, const double* U, const double* V,
+                                 hodlr_prec prec, bool inplace, void* workspace, size_t workspace_bytes,
+                                 hodlr_stream_t stream, hodlr_factor_t* out) {
   hodlr_status st = check_desc(desc);
   if (st != HODLR_OK) return st;
   if (!prec_ok(prec) || !D || !U || !V || !out) return HODLR_ERR_ARG;
   if (!aligned(D, 8) || !aligned(U, 8) || !aligned(V, 8)) return HODLR_ERR_ARG;
-  const Layout lay = factor_layout(*desc, prec);
+  if (inplace && (prec != HODLR_PREC_FP64 || desc->ldu != desc->N || U == V)) return HODLR_ERR_ARG;
+  const Layout lay = factor_layout(*desc, prec, inplace);
   if (!workspace || !aligned(workspace, kAlign) || workspace_bytes < lay.total) return HODLR_ERR_WORKSPACE;
   hodlr_factor_s* F = new (std::nothrow) hodlr_factor_s();
   if (!F) return HODLR_ERR_ARG;
@@ -367,9 +377,9 @@ hodlr_status hodlr_factor(const hodlr_desc* desc, const double* D, const double*
   F->ld_out = reinterpret_cast<double*>(w + lay.ld_out);
   F->leaf_ld = reinterpret_cast<double*>(w + lay.leaf_ld);
   F->node_ld = reinterpret_cast<double*>(w + lay.node_ld);
-  F->lu = w + lay.lu;
+  F->lu = inplace ? static_cast<void*>(const_cast<double*>(D)) : static_cast<void*>(w + lay.lu);
   F->perm = reinterpret_cast<int*>(w + lay.perm);
-  F->Y = w + lay.Y;
+  F->Y = inplace ? static_cast<void*>(const_cast<double*>(U)) : static_cast<void*>(w + lay.Y);
   F->K = reinterpret_cast<double*>(w + lay.K);
   F->P = reinterpret_cast<double*>(w + lay.P);
   F->P_elems = max_partial_elems(d, 1, 0);
@@ -416,6 +426,25 @@ hodlr_status hodlr_factor(const hodlr_desc* desc, const double* D, const double*
   if (r != HODLR_OK) return fail(r);
   *out = F;
   return HODLR_OK;
+}
+
+hodlr_status hodlr_factor(const hodlr_desc* desc, const double* D, const double* U, const double* V,
+                          hodlr_prec prec, void* workspace, size_t workspace_bytes, hodlr_stream_t stream,
+                          hodlr_factor_t* out) {
+  return factor_entry(desc, D, U, V, prec, false, workspace, workspace_bytes, stream, out);
+}
+
+hodlr_status hodlr_factor_inplace_workspace_size(const hodlr_desc* desc, size_t* bytes) {
+  hodlr_status st = check_desc(desc);
+  if (st != HODLR_OK) return st;
+  if (!bytes || desc->ldu != desc->N) return HODLR_ERR_ARG;
+  *bytes = factor_layout(*desc, HODLR_PREC_FP64, true).total;
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_factor_inplace(const hodlr_desc* desc, double* D, double* U, const double* V, void* workspace,
+                                  size_t workspace_bytes, hodlr_stream_t stream, hodlr_factor_t* out) {
+  return factor_entry(desc, D, U, V, HODLR_PREC_FP64, true, workspace, workspace_bytes, stream, out);
 }
 
 hodlr_status hodlr_factor_status(hodlr_factor_t f, int64_t* where, int64_t* detail) {
@@ -497,7 +526,7 @@ namespace {
 // (restart each), stored so that the q-th vectors of all columns form one
 // N x k block (column q * k + j, ld N).
 struct RefineLayout {
-  size_t R, solve, mv, dots, scal, V, Z, W, w, total;
+  size_t R, solve, mv, dots, scal, V, Z, W, w, Xb, total;
 };
 
 RefineLayout refine_layout(const Factor& F, int k, int restart) {
@@ -517,6 +546,7 @@ RefineLayout refine_layout(const Factor& F, int k, int restart) {
     l.Z = take(N * m * kk * sizeof(double));
     l.W = take(N * m * kk * sizeof(double));
     l.w = take(N * kk * sizeof(double));
+    l.Xb = take(N * kk * sizeof(double));  // refinement's best iterate, FGMRES's starting point
   }
   l.total = off;
   return l;
@@ -571,6 +601,10 @@ hodlr_status gmres_core(const Factor& F, const double* D, const double* U, const
   std::vector<double> H((size_t)k * (m + 1) * m), g((size_t)k * (m + 1)), cs((size_t)k * m), sn((size_t)k * m),
       y(m);
   std::vector<int> nsteps(k), done(k);
+  // |A z_i| per column and inner step (the raw Hessenberg column's norm), and
+  // a running bound on |r (recursive) - (b - A x)| / |b| from the rounding of
+  // x += Z y and r -= (A Z) y (about eps sum_i |y_i| |A z_i| per cycle)
+  std::vector<double> hnorm((size_t)k * m), drift(k, 0.0);
   if ((st = col_norms2(N, k, B, ldb, dev_nb, scratch, nb.data(), s)) != HODLR_OK) return st;
   for (int j = 0; j < k; ++j) nb[j] = std::sqrt(nb[j]) > 0.0 ? std::sqrt(nb[j]) : 1.0;
   // r = B - A X (FP64 matvec) once; later cycles update it from W
@@ -580,6 +614,18 @@ hodlr_status gmres_core(const Factor& F, const double* D, const double* U, const
   double worst = INFINITY;
   for (;;) {
     if ((st = col_norms2(N, k, R, N, dev_nr, scratch, nr.data(), s)) != HODLR_OK) return st;
+    // a column that looks converged while its drift bound could hide tol is
+    // checked against the true residual: r = b - A x (one FP64 matvec for all
+    // columns), which also restarts every column from its true residual
+    bool verify = false;
+    for (int j = 0; j < k; ++j)
+      verify |= std::sqrt(nr[j]) / nb[j] <= tol && drift[j] > 0.01 * tol;
+    if (verify) {
+      if ((st = matvec_core(d, D, U, V, X, ldx, R, N, k, mw, s, matvec_ws_bytes(d, k))) != HODLR_OK) return st;
+      HODLR_CUDA(launch_axpby_cols(N, k, 1.0, B, ldb, -1.0, R, N, s));
+      if ((st = col_norms2(N, k, R, N, dev_nr, scratch, nr.data(), s)) != HODLR_OK) return st;
+      std::fill(drift.begin(), drift.end(), 0.0);
+    }
     worst = 0.0;
     bool any = false;
     for (int j = 0; j < k; ++j) {
@@ -620,8 +666,13 @@ hodlr_status gmres_core(const Factor& F, const double* D, const double* U, const
         double* gj = g.data() + (size_t)j * (m + 1);
         double* csj = cs.data() + (size_t)j * m;
         double* snj = sn.data() + (size_t)j * m;
-        for (int q = 0; q <= i; ++q) Hi[q] = hh[(size_t)q * k + j] + hh[(size_t)(m + 1) * k + (size_t)q * k + j];
+        double hn2 = 0.0;
+        for (int q = 0; q <= i; ++q) {
+          Hi[q] = hh[(size_t)q * k + j] + hh[(size_t)(m + 1) * k + (size_t)q * k + j];
+          hn2 += Hi[q] * Hi[q];
+        }
         Hi[i + 1] = std::sqrt(hh[(size_t)2 * (m + 1) * k + j]);
+        hnorm[(size_t)j * m + i] = std::sqrt(hn2 + Hi[i + 1] * Hi[i + 1]);
         for (int q = 0; q < i; ++q) {  // earlier Givens rotations on column i
           const double t = csj[q] * Hi[q] + snj[q] * Hi[q + 1];
           Hi[q + 1] = -snj[q] * Hi[q] + csj[q] * Hi[q + 1];
@@ -652,7 +703,12 @@ hodlr_status gmres_core(const Factor& F, const double* D, const double* U, const
         const double hq = Hj[(size_t)q * (m + 1) + q];
         y[q] = hq != 0.0 ? acc / hq : 0.0;
       }
-      for (int q = 0; q < ns; ++q) coef[(size_t)q * k + j] = y[q];
+      double dr = 0.0;
+      for (int q = 0; q < ns; ++q) {
+        coef[(size_t)q * k + j] = y[q];
+        dr += std::fabs(y[q]) * hnorm[(size_t)j * m + q];
+      }
+      drift[j] += 4.0 * 1.1102230246251565e-16 * dr / nb[j];
     }
     HODLR_CUDA(cudaMemcpyAsync(dev_coef, coef.data(), (size_t)nq * k * sizeof(double), cudaMemcpyHostToDevice, s));
     HODLR_CUDA(launch_bgemv(N, k, nq, Zb, dev_coef, 1.0, X, ldx, s));
@@ -700,9 +756,11 @@ hodlr_status hodlr_solve_refined(hodlr_factor_t f, const double* D, const double
   HODLR_CUDA(launch_copy_cols<double, double>(N, k, B, ldb, X, ldx, s));
   if ((st = solve_any(*f, X, ldx, k, sw, 0, s)) != HODLR_OK) return st;
   if ((st = col_norms2(N, k, B, ldb, dev_n, scratch, nb.data(), s)) != HODLR_OK) return st;
-  double prev = INFINITY;
+  double prev = INFINITY, best = INFINITY;
   int grew = 0, it = 0;
   double worst = INFINITY;
+  const bool keep_best = restart > 0 && gmres_max_iter > 0;
+  double* Xb = keep_best ? reinterpret_cast<double*>(w + lay.Xb) : nullptr;
   for (;;) {
     if ((st = matvec_core(d, D, U, V, X, ldx, R, N, k, mw, s, matvec_ws_bytes(d, k))) != HODLR_OK) return st;
     HODLR_CUDA(launch_axpby_cols(N, k, 1.0, B, ldb, -1.0, R, N, s));  // R = B - A X
@@ -711,6 +769,10 @@ hodlr_status hodlr_solve_refined(hodlr_factor_t f, const double* D, const double
     for (int j = 0; j < k; ++j) {
       const double rr = nb[j] > 0.0 ? std::sqrt(nr[j] / nb[j]) : std::sqrt(nr[j]);
       worst = std::isnan(rr) ? INFINITY : (rr > worst ? rr : worst);
+    }
+    if (keep_best && worst < best) {  // the iterate FGMRES continues from if refinement stalls
+      best = worst;
+      HODLR_CUDA(launch_copy_cols<double, double>(N, k, X, ldx, Xb, N, s));
     }
     if (worst <= tol || it >= max_iter) break;
     grew = worst > prev ? grew + 1 : 0;
@@ -721,8 +783,9 @@ hodlr_status hodlr_solve_refined(hodlr_factor_t f, const double* D, const double
     ++it;
   }
   int git = 0;
-  if (!(worst <= tol) && restart > 0 && gmres_max_iter > 0) {
-    // refinement stalled (or ran out of corrections): FGMRES from the current X
+  if (!(worst <= tol) && keep_best) {
+    // refinement stalled (or ran out of corrections): FGMRES from its best iterate
+    HODLR_CUDA(launch_copy_cols<double, double>(N, k, Xb, N, X, ldx, s));
     st = gmres_core(*f, D, U, V, B, ldb, X, ldx, k, tol, restart, gmres_max_iter, true, w, lay, s, &git, &worst);
     if (st != HODLR_OK && st != HODLR_ERR_NOT_CONVERGED) return st;
   }

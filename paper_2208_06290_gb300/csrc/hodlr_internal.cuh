@@ -137,7 +137,11 @@ struct Factor {
   cudaStream_t stream;
   // leaf LUs (column-major m x m blocks) in FP64 or FP32, row permutations
   void* lu;          // double* (FP64) or float*
-  int* perm;         // nleaf * m: row i of the factored block is row perm[i] of D_b
+  // LU form: nleaf * m, row i of the factored block is row perm[i] of D_b.
+  // Inverse form (low precision, m <= 128): lu holds the scaled Gauss-Jordan
+  // tableau T with D_b^{-1}(step(r), p_c) = T(r, c); perm[b m + c] = p_c and
+  // perm[N + b m + r] = step(r)
+  int* perm;
   // Y_big (N x rL, ld N): double (FP64), float (FP32) or bf16 (BF16)
   void* Y;
   // V_big as used by the level kernels: the caller's V (FP64) or a copy
@@ -176,7 +180,7 @@ size_t factor_workspace_bytes(const hodlr_desc& d, hodlr_prec prec);
 // ---------------------------------------------------------------- launch accounting
 enum KernelClass {
   KC_LEAF_LU = 0, KC_LEAF_SOLVE, KC_PROJECT, KC_COUPLING, KC_COUPLING_APPLY, KC_UPDATE, KC_REDUCE,
-  KC_LEAF_MATVEC, KC_VECTOR, KC_LOGDET, KC_PROJECT_TC, KC_UPDATE_TC, KC_MATVEC, KC_COUNT
+  KC_LEAF_MATVEC, KC_VECTOR, KC_LOGDET, KC_PROJECT_TC, KC_UPDATE_TC, KC_MATVEC, KC_COMPRESS, KC_COUNT
 };
 // Called by every launcher right after its kernel launch(es): counts them and,
 // when profiling is on, records the closing event of the bracket that
@@ -299,19 +303,21 @@ cudaError_t launch_logdet_reduce(const Factor& F, cudaStream_t s);
 // r is 32 or 64 and the level's row chunks are multiples of 64 rows.
 bool project_tc_supported(int64_t N, int r, int c);
 cudaError_t launch_project_tc(int64_t N, int r, int L, int c, const __nv_bfloat16* Vp, int64_t ldv,
-                              const __nv_bfloat16* Y, double* P, DevStatus* st, cudaStream_t s);
+                              const __nv_bfloat16* Y, double* P, DevStatus* st, cudaStream_t s,
+                              uint8_t* rhs16 = nullptr);
 // Coupling solve fused into the tensor-core ancestor update (BF16 factor):
 // uses the raw projections in each node's first slot, the coupling inverses
 // and the BF16 right-hand-side staging area rhs16 (rhs_bf16_bytes).
 bool update_tc_supported(int64_t N, int r, int c);
 size_t rhs_bf16_bytes(const hodlr_desc& d);
 size_t kf32_bytes(const hodlr_desc& d);
-cudaError_t launch_update_coupled_tc(const Factor& F, int c, cudaStream_t s);
+cudaError_t launch_update_coupled_tc(const Factor& F, int c, cudaStream_t s, bool rhs_ready = false);
 // Tensor-core (kind::tf32) leaf stage Y = D_b^{-1} U of the BF16 factor
 // (m = 128, r L a multiple of 32; U 16-byte aligned with even ldu).
 bool leaf_apply_tc_supported(const Factor& F);
 cudaError_t launch_leaf_apply_tc(const Factor& F, const double* U, int64_t ldu, cudaStream_t s);
 // Set by hodlr_tc_enable (process-wide; default on).
+hodlr_status check_desc_ext(const hodlr_desc* d);
 extern bool g_use_tc;
 extern bool g_coupling_fp64;  // BF16 factor: form S = I - T_a T_b and the inverse's products in FP64
 

@@ -35,8 +35,8 @@ __device__ __forceinline__ void warp_pivot_search(const T* A, int n, int ld, int
 // SMEM: the block lives in shared memory; otherwise it is factored in place
 // in the LU buffer (global, L2-resident while the CTA runs).
 template <typename TL, bool SMEM>
-__global__ void __launch_bounds__(256) leaf_lu_kernel(int m, const double* __restrict__ D,
-                                                      TL* __restrict__ LU, int* __restrict__ perm,
+__global__ void __launch_bounds__(256) leaf_lu_kernel(int m, const double* D,  // may alias LU (in place)
+                                                      TL* LU, int* __restrict__ perm,
                                                       double* __restrict__ leaf_ld, DevStatus* st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.x;

@@ -39,6 +39,7 @@ namespace hodlr {
 template <int MB>
 __global__ void __launch_bounds__(256, 2) leaf_inv_kernel(int m, const double* __restrict__ D,
                                                           float* __restrict__ Dinv, float* __restrict__ Dtc,
+                                                          int* __restrict__ perm, int64_t N,
                                                           double* __restrict__ leaf_ld, DevStatus* st) {
   constexpr int TT = MB / 16;
   constexpr int TG = TT / 4;            // float4 groups of a thread's rows / columns
@@ -175,14 +176,19 @@ __global__ void __launch_bounds__(256, 2) leaf_inv_kernel(int m, const double* _
 #pragma unroll
     for (int jj = 0; jj < TT; ++jj) a[ii][jj] *= sc;
   }
-  // D^{-1}(step(r), p_c) = tableau(r, c): staged, then written column-major
+  // D^{-1}(step(r), p_c) = tableau(r, c): the tableau T is written as it is
+  // (staged, then column-major), with p and step
 #pragma unroll
   for (int ii = 0; ii < TT; ++ii)
 #pragma unroll
     for (int jj = 0; jj < TT; ++jj) {
       const int r = ty * TT + ii, c = tx * TT + jj;
-      s_stage[s_prow[c] * LD + s_step[r]] = a[ii][jj];
+      s_stage[c * LD + r] = a[ii][jj];
     }
+  for (int e = tid; e < m; e += 256) {
+    perm[(size_t)b * m + e] = s_prow[e];
+    perm[(size_t)N + (size_t)b * m + e] = s_step[e];
+  }
   __syncthreads();
   float* out = Dinv + (size_t)b * m * m;
   for (int e = tid; e < m * m; e += 256) out[e] = s_stage[(e / m) * LD + (e % m)];
@@ -235,10 +241,10 @@ cudaError_t launch_leaf_inv(const Factor& F, const double* D, cudaStream_t s) {
     const size_t sm = (size_t)128 * 129 * 4;
     cudaFuncSetAttribute(leaf_inv_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     float* Dtc = F.leaf_tc ? reinterpret_cast<float*>(F.P) : nullptr;  // m == 128 here
-    { leaf_inv_kernel<128><<<nleaf, 256, sm, s>>>(m, D, static_cast<float*>(F.lu), Dtc, F.leaf_ld, F.status); note_launches(1); }
+    { leaf_inv_kernel<128><<<nleaf, 256, sm, s>>>(m, D, static_cast<float*>(F.lu), Dtc, F.perm, F.d.N, F.leaf_ld, F.status); note_launches(1); }
   } else {
     const size_t sm = (size_t)64 * 65 * 4;
-    { leaf_inv_kernel<64><<<nleaf, 256, sm, s>>>(m, D, static_cast<float*>(F.lu), nullptr, F.leaf_ld, F.status); note_launches(1); }
+    { leaf_inv_kernel<64><<<nleaf, 256, sm, s>>>(m, D, static_cast<float*>(F.lu), nullptr, F.perm, F.d.N, F.leaf_ld, F.status); note_launches(1); }
   }
   return cudaGetLastError();
 }
@@ -249,17 +255,28 @@ cudaError_t launch_leaf_inv(const Factor& F, const double* D, cudaStream_t s) {
 // time; thread tile 8 rows x 4 columns. In-place safe: a CTA reads every input
 // row of its columns before it writes.
 template <typename TIN, typename TOUT>
-__global__ void __launch_bounds__(256) leaf_apply_wide_kernel(int m, const float* __restrict__ Dinv, const TIN* in,
+__global__ void __launch_bounds__(256) leaf_apply_wide_kernel(int m, const float* __restrict__ Dinv,
+                                                              const int* __restrict__ perm, int64_t N, const TIN* in,
                                                               int64_t ldin, TOUT* out, int64_t ldout, int ncols,
                                                               int trans) {
-  __shared__ float sA[32][128 + 4];  // [kk][i] = op(Dinv)(i, k0 + kk)
-  __shared__ float sB[32][64 + 4];   // [kk][j] = in(k0 + kk, j0 + j)
+  __shared__ float sA[32][128 + 4];  // [kk][i] = op(T)(i, k0 + kk)
+  __shared__ float sB[32][64 + 4];   // [kk][j] = in(gather(k0 + kk), j0 + j)
+  __shared__ int s_g[128], s_s[128];  // gather (inputs) and scatter (outputs) rows of the leaf
   const int b = blockIdx.x;
   const int j0 = blockIdx.y * 64;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const float* Ab = Dinv + (size_t)b * m * m;
   const int64_t row0 = (int64_t)b * m;
+  // T holds D^{-1}(step(r), p_c) at (r, c): D^{-1} x = scatter_step(T gather_p(x)),
+  // D^{-T} x = scatter_p(T^T gather_step(x))
+  const int* pp = perm + (size_t)b * m;
+  const int* ps = perm + (size_t)N + (size_t)b * m;
+  for (int e = tid; e < m; e += 256) {
+    s_g[e] = trans ? ps[e] : pp[e];
+    s_s[e] = trans ? pp[e] : ps[e];
+  }
+  __syncthreads();
   float acc[8][4];
 #pragma unroll
   for (int a = 0; a < 8; ++a)
@@ -276,7 +293,7 @@ __global__ void __launch_bounds__(256) leaf_apply_wide_kernel(int m, const float
     for (int e = tid; e < 32 * 64; e += 256) {
       const int kk = e & 31, j = e >> 5;
       const int k = k0 + kk;
-      sB[kk][j] = (k < m && j0 + j < ncols) ? conv<float>(in[(int64_t)(j0 + j) * ldin + row0 + k]) : 0.f;
+      sB[kk][j] = (k < m && j0 + j < ncols) ? conv<float>(in[(int64_t)(j0 + j) * ldin + row0 + s_g[k]]) : 0.f;
     }
     __syncthreads();
 #pragma unroll 4
@@ -300,7 +317,7 @@ __global__ void __launch_bounds__(256) leaf_apply_wide_kernel(int m, const float
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
       const int i = ty + 16 * a;
-      if (i < m) out[(int64_t)j * ldout + row0 + i] = conv<TOUT>(acc[a][c]);
+      if (i < m) out[(int64_t)j * ldout + row0 + s_s[i]] = conv<TOUT>(acc[a][c]);
     }
   }
 }
@@ -308,16 +325,21 @@ __global__ void __launch_bounds__(256) leaf_apply_wide_kernel(int m, const float
 // Narrow (ncols <= 8): thread i of the CTA owns row i; the leaf's right-hand
 // sides are staged in shared memory first (in-place safe).
 template <typename TIN, typename TOUT, int KC>
-__global__ void __launch_bounds__(128) leaf_apply_narrow_kernel(int m, const float* __restrict__ Dinv, const TIN* in,
+__global__ void __launch_bounds__(128) leaf_apply_narrow_kernel(int m, const float* __restrict__ Dinv,
+                                                                const int* __restrict__ perm, int64_t N, const TIN* in,
                                                                 int64_t ldin, TOUT* out, int64_t ldout, int ncols,
                                                                 int trans) {
   __shared__ float sx[128 * KC];
   const int b = blockIdx.x;
   const float* Ab = Dinv + (size_t)b * m * m;
   const int64_t row0 = (int64_t)b * m;
+  // T holds D^{-1}(step(r), p_c) at (r, c): inputs gathered by p (D^{-1}) or
+  // step (D^{-T}), outputs scattered by the other
+  const int* pg = perm + (trans ? (size_t)N : 0) + (size_t)b * m;
+  const int* ps = perm + (trans ? 0 : (size_t)N) + (size_t)b * m;
   for (int e = threadIdx.x; e < m * KC; e += blockDim.x) {
     const int k = e % m, c = e / m;
-    sx[k * KC + c] = c < ncols ? conv<float>(in[(int64_t)c * ldin + row0 + k]) : 0.f;
+    sx[k * KC + c] = c < ncols ? conv<float>(in[(int64_t)c * ldin + row0 + pg[k]]) : 0.f;
   }
   __syncthreads();
   const int i = threadIdx.x;
@@ -330,9 +352,10 @@ __global__ void __launch_bounds__(128) leaf_apply_narrow_kernel(int m, const flo
 #pragma unroll
     for (int c = 0; c < KC; ++c) acc[c] += a * sx[k * KC + c];
   }
+  const int oi = ps[i];
 #pragma unroll
   for (int c = 0; c < KC; ++c)
-    if (c < ncols) out[(int64_t)c * ldout + row0 + i] = conv<TOUT>(acc[c]);
+    if (c < ncols) out[(int64_t)c * ldout + row0 + oi] = conv<TOUT>(acc[c]);
 }
 
 template <typename TIN, typename TOUT>
@@ -342,20 +365,22 @@ cudaError_t launch_leaf_apply_inv(const Factor& F, const TIN* in, int64_t ldin, 
   const int nleaf = 1 << F.d.L;
   const float* Dinv = static_cast<const float*>(F.lu);
   const double Nd = (double)nleaf * m;
+  // the scaled Gauss-Jordan tableau T with D^{-1}(step(r), p_c) = T(r, c); p and
+  // step in F.perm (see the leaf inverse kernels)
   note_work((sizeof(TIN) + sizeof(TOUT)) * Nd * ncols + 4.0 * Nd * m, 2.0 * m * Nd * ncols);
   if (ncols <= 8) {
     const int th = ((m + 31) / 32) * 32;
     if (ncols == 1)
-      { leaf_apply_narrow_kernel<TIN, TOUT, 1><<<nleaf, th, 0, s>>>(m, Dinv, in, ldin, out, ldout, ncols, trans); note_launches(1); }
+      { leaf_apply_narrow_kernel<TIN, TOUT, 1><<<nleaf, th, 0, s>>>(m, Dinv, F.perm, F.d.N, in, ldin, out, ldout, ncols, trans); note_launches(1); }
     else if (ncols <= 2)
-      { leaf_apply_narrow_kernel<TIN, TOUT, 2><<<nleaf, th, 0, s>>>(m, Dinv, in, ldin, out, ldout, ncols, trans); note_launches(1); }
+      { leaf_apply_narrow_kernel<TIN, TOUT, 2><<<nleaf, th, 0, s>>>(m, Dinv, F.perm, F.d.N, in, ldin, out, ldout, ncols, trans); note_launches(1); }
     else if (ncols <= 4)
-      { leaf_apply_narrow_kernel<TIN, TOUT, 4><<<nleaf, th, 0, s>>>(m, Dinv, in, ldin, out, ldout, ncols, trans); note_launches(1); }
+      { leaf_apply_narrow_kernel<TIN, TOUT, 4><<<nleaf, th, 0, s>>>(m, Dinv, F.perm, F.d.N, in, ldin, out, ldout, ncols, trans); note_launches(1); }
     else
-      { leaf_apply_narrow_kernel<TIN, TOUT, 8><<<nleaf, th, 0, s>>>(m, Dinv, in, ldin, out, ldout, ncols, trans); note_launches(1); }
+      { leaf_apply_narrow_kernel<TIN, TOUT, 8><<<nleaf, th, 0, s>>>(m, Dinv, F.perm, F.d.N, in, ldin, out, ldout, ncols, trans); note_launches(1); }
   } else {
     dim3 grid(nleaf, (ncols + 63) / 64);
-    { leaf_apply_wide_kernel<TIN, TOUT><<<grid, 256, 0, s>>>(m, Dinv, in, ldin, out, ldout, ncols, trans); note_launches(1); }
+    { leaf_apply_wide_kernel<TIN, TOUT><<<grid, 256, 0, s>>>(m, Dinv, F.perm, F.d.N, in, ldin, out, ldout, ncols, trans); note_launches(1); }
   }
   return cudaGetLastError();
 }

@@ -31,10 +31,14 @@
 // A_hi B_hi + A_hi B_lo + A_lo B_hi (relative error about 2^-20 per product,
 // near the FP32 arithmetic of the CUDA-core kernel); accumulation is FP32.
 // Every row has been a pivot row once at the end; it is scaled by 1 / its
-// pivot, and entry (r, c) of the tableau is D^{-1}(step(r), p_c), staged in
-// shared memory and written out column-major (and, when asked, in the K-major
-// core layout of the tensor-core leaf apply), with the per-leaf
-// (log|det|, sign) and the status of a zero pivot or a non-finite entry.
+// pivot, and the scaled tableau T satisfies D^{-1}(step(r), p_c) = T(r, c).
+// T is written as it is (no permutation: each lane writes its own row,
+// coalesced), column-major and, when asked, in the K-major core layout of
+// the tensor-core leaf apply, with p (perm[b m + c] = p_c) and its inverse
+// (perm[N + b m + r] = step(r)); the consumers gather their inputs by p and
+// scatter their outputs by step (or the reverse for D^{-T}). Also written:
+// the per-leaf (log|det|, sign) and the status of a zero pivot or a
+// non-finite entry.
 // The MMA completion wait is bounded; a wait that gives up records
 // HODLR_ERR_TIMEOUT, waits (bounded) for the MMA in flight, frees TMEM and
 // returns.
@@ -46,23 +50,21 @@ namespace {
 constexpr int kLiThreads = 128;
 constexpr int kLiCols = 128;             // TMEM columns = tableau columns
 constexpr uint32_t kLiSBO = 1024;        // 8-row groups of a K = 32 operand: 8 cores x 128 B
-constexpr int kLiLD = 129;               // output staging stride (floats)
 
 struct LiSmem {
   static constexpr uint32_t kA = 128 * 32 * 4;    // A operand (one part)
   static constexpr uint32_t kB = 96 * 32 * 4;     // B operand (one part)
   static constexpr uint32_t kAhi = 0, kAlo = kA, kBhi = 2 * kA, kBlo = 2 * kA + kB;
   static constexpr uint32_t kOps = 2 * kA + 2 * kB;
-  static constexpr uint32_t kStage = 128 * kLiLD * 4;  // output staging, aliases the operands
-  static constexpr uint32_t kUnion = kStage > kOps ? kStage : kOps;
-  static constexpr uint32_t kCand = (kUnion + 127) / 128 * 128;  // [2][4][32] floats
-  static constexpr uint32_t kKey = kCand + 2 * 4 * 32 * 4;      // uint32 [2][4]
-  static constexpr uint32_t kKRow = kKey + 32;                  // int [2][4]
-  static constexpr uint32_t kProw = kKRow + 32;                 // int [128]: p_k
+  static constexpr int kTLd = 97;                 // [step][column] staging of the pivot rows (in A_lo)
+  static constexpr uint32_t kCand = kOps;                         // [2][4][32] floats
+  static constexpr uint32_t kKey = kCand + 2 * 4 * 32 * 4;      // uint64 [2][4]: key << 32 | (0xffff - row)
+  static constexpr uint32_t kProw = kKey + 64;                  // int [128]: p_k
   static constexpr uint32_t kPiv = kProw + 512;                 // float [128]
   static constexpr uint32_t kRed = kPiv + 512;                  // per-warp log-det partials
   static constexpr uint32_t kBar = kRed + 4 * 32;
   static constexpr uint32_t kBytes = kBar + 64 + 128;           // + alignment slack
+  static_assert(32 * kTLd * 4 <= kA, "pivot-row staging fits in A_lo");
 };
 
 // x = hi + lo with hi the TF32 part (low 13 significand bits cleared).
@@ -73,15 +75,14 @@ __device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
 
 __global__ void __launch_bounds__(kLiThreads, 3) leaf_inv_tc_kernel(int m, int64_t nleaf, const double* __restrict__ D,
                                                                      float* __restrict__ Dinv,
-                                                                     float* __restrict__ Dtc,
+                                                                     float* __restrict__ Dtc, int* __restrict__ perm,
                                                                      double* __restrict__ leaf_ld, DevStatus* st) {
   using S = LiSmem;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  float* s_stage = reinterpret_cast<float*>(smem);
+  float* s_tr = reinterpret_cast<float*>(smem + S::kAlo);  // pivot rows [step][column], before A_lo is written
   float* s_cand = reinterpret_cast<float*>(smem + S::kCand);
-  uint32_t* s_key = reinterpret_cast<uint32_t*>(smem + S::kKey);
-  int* s_krow = reinterpret_cast<int*>(smem + S::kKRow);
+  unsigned long long* s_key = reinterpret_cast<unsigned long long*>(smem + S::kKey);
   int* s_prow = reinterpret_cast<int*>(smem + S::kProw);
   float* s_piv = reinterpret_cast<float*>(smem + S::kPiv);
   double* s_red = reinterpret_cast<double*>(smem + S::kRed);
@@ -105,8 +106,14 @@ __global__ void __launch_bounds__(kLiThreads, 3) leaf_inv_tc_kernel(int m, int64
   uint32_t ph = 0;
   bool mma_pending = false;  // thread 0's view
   for (int64_t b = blockIdx.x; b < nleaf && ok; b += gridDim.x) {
-    // ---- load row `row` of D_b (identity-padded) into the tableau
+    // ---- load row `row` of D_b (identity-padded) into the tableau; the next
+    // leaf of this CTA is prefetched into L2 meanwhile
     const double* Db = D + (size_t)b * m * m;
+    if (b + gridDim.x < nleaf) {
+      const char* nx = reinterpret_cast<const char*>(D + (size_t)(b + gridDim.x) * m * m);
+      for (int64_t o = (int64_t)tid * 128; o < (int64_t)m * m * 8; o += 128 * kLiThreads)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(nx + o));
+    }
     bool bad = false;
     for (int c0 = 0; c0 < kLiCols; c0 += 32) {
       double x[32];
@@ -144,17 +151,15 @@ __global__ void __launch_bounds__(kLiThreads, 3) leaf_inv_tc_kernel(int m, int64
           float4* o = reinterpret_cast<float4*>(s_cand + (buf * 4 + warp) * 32);
 #pragma unroll
           for (int g = 0; g < 8; ++g) o[g] = make_float4(a[4 * g], a[4 * g + 1], a[4 * g + 2], a[4 * g + 3]);
-          s_key[buf * 4 + warp] = wmax;
-          s_krow[buf * 4 + warp] = row;
+          s_key[buf * 4 + warp] = ((unsigned long long)wmax << 32) | (unsigned long long)(0xffff - row);
         }
         __syncthreads();
-        const uint4 kk = *reinterpret_cast<const uint4*>(s_key + buf * 4);
-        int pw = 0;
-        uint32_t best = kk.x;
-        if (kk.y > best) { best = kk.y; pw = 1; }
-        if (kk.z > best) { best = kk.z; pw = 2; }
-        if (kk.w > best) { best = kk.w; pw = 3; }
-        const int p = s_krow[buf * 4 + pw];
+        // largest key, lowest row on ties (rows of lower warps are lower)
+        const ulonglong2 k01 = *reinterpret_cast<const ulonglong2*>(s_key + buf * 4);
+        const ulonglong2 k23 = *reinterpret_cast<const ulonglong2*>(s_key + buf * 4 + 2);
+        const unsigned long long kb = max(max(k01.x, k01.y), max(k23.x, k23.y));
+        const int p = 0xffff - (int)(kb & 0xffffull);
+        const int pw = p >> 5;
         const float4* prow = reinterpret_cast<const float4*>(s_cand + (buf * 4 + pw) * 32);
         float pr[32];
 #pragma unroll
@@ -180,6 +185,46 @@ __global__ void __launch_bounds__(kLiThreads, 3) leaf_inv_tc_kernel(int m, int64
         }
       }
       // ---- trailing update of the other 96 columns on the tensor cores
+      tc::tmem_st32(tl + k0, a);
+      const bool piv_here = used && my_step >= k0;  // pivot row of this panel
+      const int sl = my_step - k0;
+      // (1) pivot rows of this panel: their old values of the other columns
+      // into the [step][column] staging, zeros into the tableau
+      if (__any_sync(0xffffffffu, piv_here)) {
+        for (int c32 = 0; c32 < kLiCols / 32; ++c32) {
+          if (c32 == q) continue;
+          float v[32];
+          tc::tmem_ld32(tl + c32 * 32, v);
+          if (piv_here) {
+            const int rho0 = c32 < q ? c32 * 32 : c32 * 32 - 32;  // index among the other 96 columns
+            float* o = s_tr + sl * S::kTLd + rho0;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              o[j] = v[j];
+              v[j] = 0.f;
+            }
+          }
+          tc::tmem_st32(tl + c32 * 32, v);
+        }
+      }
+      __syncthreads();
+      // (2) B^T (96 x 32) in the K-major core layout, TF32 hi / lo parts:
+      // item (sq, rho) = 16 bytes of steps 4 sq .. 4 sq + 3 of column rho
+      {
+        uint8_t* bhi = smem + S::kBhi;
+        uint8_t* blo = smem + S::kBlo;
+        for (int it = tid; it < 96 * 8; it += kLiThreads) {
+          const int sq = it / 96, rho = it % 96;
+          float h[4], l[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) tf32_split(s_tr[(4 * sq + e) * S::kTLd + rho], h[e], l[e]);
+          const uint32_t off = (uint32_t)(rho >> 3) * kLiSBO + (uint32_t)sq * 128 + (uint32_t)(rho & 7) * 16;
+          *reinterpret_cast<float4*>(bhi + off) = make_float4(h[0], h[1], h[2], h[3]);
+          *reinterpret_cast<float4*>(blo + off) = make_float4(l[0], l[1], l[2], l[3]);
+        }
+      }
+      __syncthreads();  // the staging (in A_lo) is read
+      // (3) A = T(:, P) (128 x 32), TF32 hi / lo parts, from the panel registers
       {
         uint8_t* ahi = smem + S::kAhi;
         uint8_t* alo = smem + S::kAlo;
@@ -191,33 +236,6 @@ __global__ void __launch_bounds__(kLiThreads, 3) leaf_inv_tc_kernel(int m, int64
           for (int e = 0; e < 4; ++e) tf32_split(a[4 * kc + e], h[e], l[e]);
           *reinterpret_cast<float4*>(ahi + rb + kc * 128) = make_float4(h[0], h[1], h[2], h[3]);
           *reinterpret_cast<float4*>(alo + rb + kc * 128) = make_float4(l[0], l[1], l[2], l[3]);
-        }
-      }
-      tc::tmem_st32(tl + k0, a);
-      const bool piv_here = used && my_step >= k0;  // pivot row of this panel
-      const int sl = my_step - k0;
-      if (__any_sync(0xffffffffu, piv_here)) {
-        uint8_t* bhi = smem + S::kBhi;
-        uint8_t* blo = smem + S::kBlo;
-        for (int c32 = 0; c32 < kLiCols / 32; ++c32) {
-          if (c32 == q) continue;
-          float v[32];
-          tc::tmem_ld32(tl + c32 * 32, v);
-          if (piv_here) {
-            const int rho0 = c32 < q ? c32 * 32 : c32 * 32 - 32;  // index among the other 96 columns
-            const uint32_t kb = (uint32_t)(sl >> 2) * 128 + (uint32_t)(sl & 3) * 4;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int rho = rho0 + j;
-              const uint32_t off = (uint32_t)(rho >> 3) * kLiSBO + (uint32_t)(rho & 7) * 16 + kb;
-              float h, l;
-              tf32_split(v[j], h, l);
-              *reinterpret_cast<float*>(bhi + off) = h;
-              *reinterpret_cast<float*>(blo + off) = l;
-              v[j] = 0.f;
-            }
-          }
-          tc::tmem_st32(tl + c32 * 32, v);
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -257,13 +275,32 @@ __global__ void __launch_bounds__(kLiThreads, 3) leaf_inv_tc_kernel(int m, int64
     }
     if (!ok) break;
 
-    // ---- D^{-1}(step(r), p_c) = t(r, c) / pivot(step(r)), staged column-major
+    // ---- T(r, c) / pivot(step(r)) written row by row (lane r writes row r):
+    // column-major (each warp store is 32 consecutive rows of a column) and,
+    // for the tensor-core leaf apply, in its K-major core layout (16 bytes of
+    // one row per store)
     const float sc = my_piv != 0.f ? 1.f / my_piv : 0.f;
+    float* out = Dinv + (size_t)b * m * m;
     for (int c0 = 0; c0 < kLiCols; c0 += 32) {
       float v[32];
       tc::tmem_ld32(tl + c0, v);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) s_stage[s_prow[c0 + j] * kLiLD + my_step] = v[j] * sc;
+      for (int j = 0; j < 32; ++j) v[j] *= sc;
+      if (row < m) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (c0 + j < m) out[(size_t)(c0 + j) * m + row] = v[j];
+      }
+      if (Dtc) {  // m == 128
+        float4* o = reinterpret_cast<float4*>(Dtc + (size_t)b * 128 * 128 + (size_t)(row >> 3) * 1024 +
+                                              (size_t)(c0 >> 2) * 32 + (row & 7) * 4);
+#pragma unroll
+        for (int g = 0; g < 8; ++g) o[g * 8] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+      }
+    }
+    if (row < m) {
+      perm[(size_t)b * m + row] = s_prow[row];                      // p_c for c = row
+      perm[(size_t)nleaf * m + (size_t)b * m + row] = my_step;      // step(r) for r = row
     }
     // per-step pieces of log|det|: log|pivot|, negative pivots, the first zero
     // pivot, and the inversions of (p_k) (the parity of the row order)
@@ -293,17 +330,6 @@ __global__ void __launch_bounds__(kLiThreads, 3) leaf_inv_tc_kernel(int m, int64
       }
     }
     const bool any_bad = __syncthreads_or(bad) != 0;
-    float* out = Dinv + (size_t)b * m * m;
-    for (int e = tid; e < m * m; e += kLiThreads) out[e] = s_stage[(e / m) * kLiLD + (e % m)];
-    if (Dtc) {
-      float4* o = reinterpret_cast<float4*>(Dtc + (size_t)b * 128 * 128);
-      for (int e4 = tid; e4 < 128 * 128 / 4; e4 += kLiThreads) {
-        const int il = e4 & 7, kq = (e4 >> 3) & 31, ig = e4 >> 8;
-        const int i = ig * 8 + il, k = kq * 4;
-        o[e4] = make_float4(s_stage[k * kLiLD + i], s_stage[(k + 1) * kLiLD + i], s_stage[(k + 2) * kLiLD + i],
-                            s_stage[(k + 3) * kLiLD + i]);
-      }
-    }
     if (tid == 0) {
       const int* rr = reinterpret_cast<const int*>(s_red + 4);
       const double la = s_red[0] + s_red[1] + s_red[2] + s_red[3];
@@ -341,7 +367,7 @@ cudaError_t launch_leaf_inv_tc(const Factor& F, const double* D, float* Dtc, cud
   int64_t grid = (int64_t)sms * 3;  // three CTAs (warpgroups) per SM: 3 x 128 TMEM columns
   if (grid > nleaf) grid = nleaf;
   leaf_inv_tc_kernel<<<(unsigned)grid, kLiThreads, bytes, s>>>(m, nleaf, D, static_cast<float*>(F.lu), Dtc,
-                                                               F.leaf_ld, F.status);
+                                                               F.perm, F.leaf_ld, F.status);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -28,7 +28,6 @@ hodlr_status matvec_core_ext(const hodlr_desc& d, const double* D, const double*
                              int64_t ldx, double* Y, int64_t ldy, int k, void* work, cudaStream_t s,
                              size_t work_bytes);
 size_t matvec_scratch_bytes(const hodlr_desc& d, int k);
-hodlr_status check_desc_ext(const hodlr_desc* d);
 
 namespace {
 

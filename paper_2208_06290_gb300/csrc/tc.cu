@@ -34,11 +34,17 @@ struct ProjSmem {
 // column tile mt). Warp 0 lane 0 issues TMA loads, warp 1 lane 0 issues the
 // MMAs, all four warps drain TMEM (warp w owns TMEM lanes 32w..32w+31 =
 // columns of the tile) and write the FP64 partial.
+// With rhs16 (levels where every node is one chunk, ahead of the fused
+// update): the ancestor columns m < anc of a node's projection are written
+// straight into the BF16 right-hand-side operand of its parent (the layout
+// of rhs_bf16_kernel: rows 0..r-1 from the second child, r..2r-1 from the
+// first), and only the own block (the coupling's T) into P in FP64.
 template <int RN>
 __global__ void __launch_bounds__(128) project_tc_kernel(const __grid_constant__ CUtensorMap mapY,
                                                          const __grid_constant__ CUtensorMap mapV, int64_t ch,
                                                          int64_t nchunks, int vcol, int rc, double* __restrict__ P,
-                                                         DevStatus* st, int level) {
+                                                         DevStatus* st, int level, uint8_t* __restrict__ rhs16,
+                                                         int anc) {
   using S = ProjSmem<RN>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -112,11 +118,29 @@ __global__ void __launch_bounds__(128) project_tc_kernel(const __grid_constant__
     if (ok) {
       const int m = col0 + warp * 32 + lane;
       double* Pq = P + (size_t)q * RN * rc;
+      constexpr int K2 = 2 * RN;
+      constexpr uint32_t kSBOr = (K2 / 8) * 128;
 #pragma unroll
       for (int cc = 0; cc < (RN + 31) / 32; ++cc) {
         float v[32];
         tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + cc * 32, v);
-        if (m < rc) {
+        if (rhs16 && m < anc) {
+          // row k = koff + n of the parent's [W_beta; W_alpha]^T, column m
+          const int koff = (q & 1) ? 0 : RN;
+          constexpr int kNC = 64;  // ancestor columns per block of the operand (the fused update's chunk)
+          uint8_t* base = rhs16 + (size_t)(q >> 1) * anc * K2 * 2 + (size_t)(m / kNC) * kNC * K2 * 2 +
+                          (size_t)((m % kNC) >> 3) * kSBOr + (size_t)(m & 7) * 16;
+#pragma unroll
+          for (int kg = 0; kg < 4; ++kg) {
+            uint32_t pk[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              pk[u] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[kg * 8 + 2 * u])) |
+                      ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[kg * 8 + 2 * u + 1])) << 16);
+            *reinterpret_cast<uint4*>(base + (size_t)((koff + cc * 32) / 8 + kg) * 128) =
+                make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          }
+        } else if (m < rc) {
 #pragma unroll
           for (int j = 0; j < 32; ++j)
             if (cc * 32 + j < RN) Pq[(size_t)m * RN + cc * 32 + j] = (double)v[j];
@@ -185,7 +209,7 @@ int sm_count() {
 
 template <int RN>
 cudaError_t project_tc_go(const __nv_bfloat16* Vp, int64_t ldv, const __nv_bfloat16* Y, int64_t N, int rL, int c,
-                          int rc, double* P, DevStatus* st, cudaStream_t s) {
+                          int rc, double* P, DevStatus* st, cudaStream_t s, uint8_t* rhs16) {
   using S = ProjSmem<RN>;
   CUtensorMap mY, mV;
   if (!make_map(&mY, Y, N, rL, N, kBK, kBM)) return cudaErrorInvalidValue;
@@ -197,7 +221,8 @@ cudaError_t project_tc_go(const __nv_bfloat16* Vp, int64_t ldv, const __nv_bfloa
   int64_t grid = (int64_t)sm_count() * (per_sm < 1 ? 1 : per_sm);
   if (grid > items) grid = items;
   cudaFuncSetAttribute(project_tc_kernel<RN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kBytes);
-  { project_tc_kernel<RN><<<(unsigned)grid, 128, S::kBytes, s>>>(mY, mV, ch, nch, (c - 1) * RN, rc, P, st, c); note_launches(1); }
+  { project_tc_kernel<RN><<<(unsigned)grid, 128, S::kBytes, s>>>(mY, mV, ch, nch, (c - 1) * RN, rc, P, st, c,
+                                                                   rhs16, RN * (c - 1)); note_launches(1); }
   return cudaGetLastError();
 }
 
@@ -208,12 +233,16 @@ bool project_tc_supported(int64_t N, int r, int c) {
 }
 
 cudaError_t launch_project_tc(int64_t N, int r, int L, int c, const __nv_bfloat16* Vp, int64_t ldv,
-                              const __nv_bfloat16* Y, double* P, DevStatus* st, cudaStream_t s) {
+                              const __nv_bfloat16* Y, double* P, DevStatus* st, cudaStream_t s, uint8_t* rhs16) {
   ProfScope prof_(KC_PROJECT_TC, s);
   const int rc = r * c;
-  note_work(2.0 * (double)N * r + 2.0 * (double)N * rc + 8.0 * num_chunks(N, c) * r * rc, 2.0 * N * r * (double)rc);
-  if (r == 32) return project_tc_go<32>(Vp, ldv, Y, N, r * L, c, rc, P, st, s);
-  return project_tc_go<64>(Vp, ldv, Y, N, r * L, c, rc, P, st, s);
+  const double anc = (double)r * (c - 1);
+  note_work(2.0 * (double)N * r + 2.0 * (double)N * rc +
+                (rhs16 ? 8.0 * num_chunks(N, c) * r * r + 2.0 * num_chunks(N, c) * r * anc
+                       : 8.0 * num_chunks(N, c) * r * rc),
+            2.0 * N * r * (double)rc);
+  if (r == 32) return project_tc_go<32>(Vp, ldv, Y, N, r * L, c, rc, P, st, s, rhs16);
+  return project_tc_go<64>(Vp, ldv, Y, N, r * L, c, rc, P, st, s, rhs16);
 }
 
 
@@ -241,7 +270,7 @@ cudaError_t launch_project_tc(int64_t N, int r, int L, int c, const __nv_bfloat1
 // stored by TMA. The roles and their pipeline are described at the kernel.
 namespace {
 
-constexpr int kFuNC = 64;    // ancestor columns per MMA chunk (N of the MMA)
+constexpr int kFuNC = 64;    // ancestor columns per MMA chunk (N of the MMA; the projection's rhs16 epilogue uses the same)
 constexpr int kFuBox = 32;   // columns per TMA box of Y (box = 128 rows x 32 columns)
 
 // Rhs^T of every parent of child level c into the B layout above. Thread per
@@ -741,7 +770,7 @@ size_t kf32_bytes(const hodlr_desc& d) {
   return ((size_t)1 << d.L) * (size_t)d.r * (2 * d.r + 4) * 4;
 }
 
-cudaError_t launch_update_coupled_tc(const Factor& F, int c, cudaStream_t s) {
+cudaError_t launch_update_coupled_tc(const Factor& F, int c, cudaStream_t s, bool rhs_ready) {
   const int64_t N = F.d.N;
   const int r = F.d.r;
   const int anc = r * (c - 1);
@@ -752,7 +781,7 @@ cudaError_t launch_update_coupled_tc(const Factor& F, int c, cudaStream_t s) {
   const double* Kc = F.K + F.Koff[c] * 4 * r * r;
   {
     ProfScope prof_(KC_COUPLING_APPLY, s);
-    note_work(8.0 * (double)(1ll << c) * r * anc + 2.0 * (double)parents * anc * 2 * r +
+    note_work((rhs_ready ? 0.0 : 8.0 * (double)(1ll << c) * r * anc + 2.0 * (double)parents * anc * 2 * r) +
                   8.0 * parents * 4.0 * r * r + 4.0 * (1ll << c) * r * (2.0 * r + 4),
               0.0);
     const int64_t total = parents * (int64_t)anc * (2 * r / 8);
@@ -762,16 +791,21 @@ cudaError_t launch_update_coupled_tc(const Factor& F, int c, cudaStream_t s) {
     int64_t gk = (kt + 255) / 256;
     if (gk > 16 * (int64_t)sm_count()) gk = 16 * (int64_t)sm_count();
     if (r == 32) {
-      rhs_bf16_kernel<32><<<(unsigned)grid, 256, 0, s>>>(c, F.P, pstride, anc, F.rhs16);
-      note_launches(1);
+      if (!rhs_ready) {  // else the projection wrote it
+        rhs_bf16_kernel<32><<<(unsigned)grid, 256, 0, s>>>(c, F.P, pstride, anc, F.rhs16);
+        note_launches(1);
+      }
       if (!coupling_writes_kf32(F, c)) {
         kf32_kernel<32><<<(unsigned)gk, 256, 0, s>>>(c, Kc, F.kf32);
         note_launches(1);
       }
     } else {
-      rhs_bf16_kernel<64><<<(unsigned)grid, 256, 0, s>>>(c, F.P, pstride, anc, F.rhs16);
+      if (!rhs_ready) {
+        rhs_bf16_kernel<64><<<(unsigned)grid, 256, 0, s>>>(c, F.P, pstride, anc, F.rhs16);
+        note_launches(1);
+      }
       kf32_kernel<64><<<(unsigned)gk, 256, 0, s>>>(c, Kc, F.kf32);
-      note_launches(2);
+      note_launches(1);
     }
   }
   ProfScope prof_(KC_UPDATE_TC, s);
@@ -837,6 +871,7 @@ struct LeafTcSmem {
 __global__ void __launch_bounds__(256, 2) leaf_apply_tc_kernel(const __grid_constant__ CUtensorMap mapY,
                                                                int64_t nleaf, int rL,
                                                                const float* __restrict__ Acore,
+                                                               const int* __restrict__ perm,
                                                                const double* __restrict__ U, int64_t ldu,
                                                                DevStatus* st) {
   using S = LeafTcSmem;
@@ -851,6 +886,7 @@ __global__ void __launch_bounds__(256, 2) leaf_apply_tc_kernel(const __grid_cons
   uint64_t* bar_mma = bar_a + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_a + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  __shared__ int s_p[128];  // p_c: column c of A = T is column p_c of D_b^{-1}
 
   if (tid == 0) {
     tc::mbar_init(bar_a, 1);
@@ -875,6 +911,13 @@ __global__ void __launch_bounds__(256, 2) leaf_apply_tc_kernel(const __grid_cons
       bulk_load_1d(sA, Acore + (size_t)b * 128 * 128, S::kABytes, bar_a);
       a_pending = true;
     }
+    // A = T with D_b^{-1}(step(r), p_c) = T(r, c): B takes U's rows in the
+    // order p (row c of B = row p_c of U) and row r of the product is row
+    // step(r) of Y
+    __syncthreads();  // the previous leaf's s_p / my_out readers are done
+    if (tid < 128) s_p[tid] = perm[(size_t)b * 128 + tid];
+    const int my_out = perm[(size_t)nleaf * 128 + (size_t)b * 128 + ((warp & 3) * 32 + lane)];
+    __syncthreads();
     for (int ch = 0; ch < nchunks && ok; ++ch) {
       const int col0 = ch * kLaNC;
       const int nc = (rL - col0) < kLaNC ? (rL - col0) : kLaNC;  // multiple of 32
@@ -889,9 +932,9 @@ __global__ void __launch_bounds__(256, 2) leaf_apply_tc_kernel(const __grid_cons
           const int jl = it & 7, kq = (it >> 3) & 31, jg = it >> 8;
           const int j = jg * 8 + jl;
           if (j < nc) {
-            const double* src = U + (int64_t)(col0 + j) * ldu + row0 + kq * 4;
-            v0[u] = *reinterpret_cast<const double2*>(src);
-            v1[u] = *reinterpret_cast<const double2*>(src + 2);
+            const double* src = U + (int64_t)(col0 + j) * ldu + row0;
+            v0[u] = make_double2(src[s_p[kq * 4]], src[s_p[kq * 4 + 1]]);
+            v1[u] = make_double2(src[s_p[kq * 4 + 2]], src[s_p[kq * 4 + 3]]);
           }
         }
 #pragma unroll
@@ -932,12 +975,11 @@ __global__ void __launch_bounds__(256, 2) leaf_apply_tc_kernel(const __grid_cons
       mma_pending = false;
       tc::tc_fence_after();
       // warps w and w+4 share TMEM lanes 32 (w % 4) .. +31 and split the columns
-      const int m = (warp & 3) * 32 + lane;
       for (int cb = (warp >> 2) * 32; cb < nc; cb += 64) {
         float v[32];
         tc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + cb, v);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) sY[(cb + j) * 128 + m] = __float2bfloat16_rn(v[j]);
+        for (int j = 0; j < 32; ++j) sY[(cb + j) * 128 + my_out] = __float2bfloat16_rn(v[j]);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tc::tc_fence_before();
@@ -982,7 +1024,7 @@ cudaError_t launch_leaf_apply_tc(const Factor& F, const double* U, int64_t ldu, 
   cudaFuncSetAttribute(leaf_apply_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kBytes);
   {
     leaf_apply_tc_kernel<<<(unsigned)grid, 256, S::kBytes, s>>>(mY, nleaf, rL, reinterpret_cast<const float*>(F.P),
-                                                                 U, ldu, F.status);
+                                                                 F.perm, U, ldu, F.status);
     note_launches(1);
   }
   return cudaGetLastError();

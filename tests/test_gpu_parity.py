@@ -338,3 +338,25 @@ def test_refinement_hands_over_to_fgmres(cuda_lib):
     X2, it2, rr2, code2 = hb.hodlr_solve_refined(F, D, U, V, B, tol=1e-10, max_iter=0, restart=0,
                                                  raise_on_fail=False)
     assert code2 == hb.HODLR_ERR_NOT_CONVERGED and it2 == 0 and rr2 > 1e-10
+
+
+@pytest.mark.parametrize("N,L,r", [(4096, 6, 16), (2048, 3, 32)])
+def test_inplace_fp64_factor(cuda_lib, N, L, r):
+    """The in-place FP64 factor (leaf LUs over D, Y_big over U) solves,
+    adjoint-solves and gives the log-determinant as the out-of-place one, to
+    the oracle's tolerance, from a smaller workspace."""
+    hb = cuda_lib
+    (Dm, Um, Vm, Bm), (D, U, V, B) = make_case(N, L, r, seed=N + 3 * r, k=2)
+    rec = RecursiveHODLR(Dm, Um, Vm, L)
+    F = hb.hodlr_factor(D, U, V, L, r, "fp64")
+    D2, U2 = D.clone(), U.clone()   # clone keeps the column-major strides
+    assert D2.stride() == D.stride() and U2.stride() == U.stride()
+    Fi = hb.hodlr_factor_inplace(D2, U2, V, L, r)
+    assert hb.hodlr_factor_status(Fi)[0] == 0
+    assert Fi.workspace.numel() < F.workspace.numel()
+    assert not torch.equal(D2, D) and not torch.equal(U2, U)   # overwritten
+    close(hb.hodlr_solve(Fi, B.clone()).cpu().numpy(), rec.solve(Bm), SOL_TOL)
+    close(hb.hodlr_solve_adjoint(Fi, B.clone()).cpu().numpy(), rec.solve_adjoint(Bm), SOL_TOL)
+    s, la = hb.hodlr_logdet(Fi)
+    so, lao = rec.slogdet()
+    assert s == so and abs(la - lao) <= LD_TOL * max(1.0, abs(lao))
