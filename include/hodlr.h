@@ -69,6 +69,9 @@ typedef enum {
 /* Arithmetic of the factorization (not of the input, which is always FP64).
  *   FP64: everything in FP64.
  *   FP32: leaf LU, leaf solves and panel products in FP32 (FP32 accumulate).
+ *   TF32: as FP32 (Y_big and V_big stored in FP32), but the per-level
+ *         projections V^T Y run on the tensor cores with TF32 operands (the
+ *         FP32 values' top 10 significand bits) and FP32 accumulation.
  *   BF16: as FP32, but Y_big and V_big are stored in bfloat16 and the panel
  *         products read them as such (FP32 accumulate).
  * In every precision the 2r x 2r coupling matrices are formed, factored and
@@ -77,6 +80,7 @@ typedef enum {
 typedef enum {
   HODLR_PREC_FP64 = 0,
   HODLR_PREC_FP32 = 1,
+  HODLR_PREC_TF32 = 2,
   HODLR_PREC_BF16 = 3
 } hodlr_prec;
 
@@ -267,8 +271,8 @@ HODLR_API hodlr_status hodlr_gmres(hodlr_factor_t f, const double* D, const doub
  * and leaf below alpha; dD_b also gets D_b^{-T}.
  * dD has D's layout, dU and dV are N x rL with leading dimension N, dB is
  * N x k (lddb). Results overwrite the outputs. If loss is not NULL the call
- * synchronizes and stores the loss value. FP64 and FP32 factors
- * (HODLR_ERR_ARG otherwise). With an FP32 factor the solves, Y_big and the
+ * synchronizes and stores the loss value. FP64, FP32 and TF32 factors
+ * (HODLR_ERR_ARG for BF16). With an FP32 factor the solves, Y_big and the
  * leaf inverses / LUs carry FP32 rounding (coupling inverses, log-dets and
  * accumulations stay FP64): its gradient approximates the FP64 one to about
  * the FP32 factor's solve accuracy. */
@@ -288,8 +292,13 @@ HODLR_API hodlr_status hodlr_grad(hodlr_factor_t f, const double* U, const doubl
  * entry (column j_k, first maximum among unused columns), v_k = row / that
  * entry, the residual column u_k at j_k and i_{k+1} = its largest entry among
  * the unused rows; A(I_alpha, I_beta) ~= sum u_k v_k^T = U_alpha V_beta^T.
- * A block whose residual vanishes keeps zero bases from then on. Entries and
- * residual updates are FP32 (the bases are stored in FP64). For the symmetric
+ * A block whose residual vanishes keeps zero bases from then on; with
+ * tol > 0 a block also stops at the first step whose pivot is at most
+ * tol times its first pivot (tolerance-driven, per-block ranks <= r; the
+ * bases beyond a block's rank are zero, so the output is the zero-padded
+ * uniform layout of a variable-rank HODLR matrix). Entries are evaluated
+ * from FP64 geometry and rounded to FP32; the residual updates are FP32; the
+ * bases are stored in FP64. For the symmetric
  * kernel matrices one cross per sibling pair gives both blocks, so U = V.
  *
  * Kernels (hodlr_kernel_desc.kind):
@@ -310,8 +319,10 @@ HODLR_API hodlr_status hodlr_grad(hodlr_factor_t f, const double* U, const doubl
  * offset 2 r (2^c - 2), the pivot rows [block][k] then the pivot columns
  * [block][k] (indices local to the block; -1 after a vanished residual); the
  * blocks of level c are its 2^c nodes (row node = block; for a symmetric
- * kernel only the even ones are used). Workspace:
- * hodlr_compress_workspace_size. Enqueued on the stream; no allocation. */
+ * kernel only the even ones are used). ranks (optional, device,
+ * 2^(L+1) - 2 int32): the rank of every block, level c at offset 2^c - 2.
+ * Workspace: hodlr_compress_workspace_size. Enqueued on the stream; no
+ * allocation. */
 typedef enum {
   HODLR_KERNEL_BIE_STAR = 0,
   HODLR_KERNEL_GAUSSIAN = 1,
@@ -324,12 +335,27 @@ typedef struct {
   const double* points;  /* device, N x dim (kernel matrices), NULL for the BIE */
   double scale;          /* Gaussian sigma / Matern lengthscale */
   double nugget;         /* added to the diagonal (kernel matrices) */
+  double tol;            /* relative pivot tolerance of the cross approximation, 0 <= tol < 1 (0: rank r) */
 } hodlr_kernel_desc;
 
 HODLR_API hodlr_status hodlr_compress_workspace_size(const hodlr_desc* desc, size_t* bytes);
 HODLR_API hodlr_status hodlr_compress(const hodlr_desc* desc, const hodlr_kernel_desc* kern, double* D, double* U,
-                                      double* V, int32_t* pivots, void* workspace, size_t workspace_bytes,
-                                      hodlr_stream_t stream);
+                                      double* V, int32_t* pivots, int32_t* ranks, void* workspace,
+                                      size_t workspace_bytes, hodlr_stream_t stream);
+
+/* Variable ranks per level (Eq. e:u, Sec. 3.2 with per-level widths): the
+ * ragged Ur / Vr (N x sum r_c, leading dimensions ldur, ldvr >= N) hold level
+ * c's bases in columns off_c .. off_c + r_c - 1 (off_c = r_1 + ... + r_{c-1}),
+ * each node's basis left-aligned (zeros right of a lower-rank node's basis).
+ * hodlr_pack_level_ranks writes the same matrix in the uniform layout of
+ * desc (r >= every r_c; level blocks zero-padded on the right), which every
+ * other entry point takes; the padding changes no product (U_alpha V_beta^T
+ * is unchanged) and costs r / r_c of a level's panel work. level_ranks is a
+ * HOST array of L entries; workspace >= 2 L ints (device). Synchronizes the
+ * stream. */
+HODLR_API hodlr_status hodlr_pack_level_ranks(const hodlr_desc* desc, const int32_t* level_ranks, const double* Ur,
+                                              int64_t ldur, const double* Vr, int64_t ldvr, double* U, double* V,
+                                              void* workspace, size_t workspace_bytes, hodlr_stream_t stream);
 
 /* ------------------------------------------------------------ diagnostics --
  * Accounting of the library's own kernel launches, for benchmarks; not part

@@ -389,3 +389,26 @@ def cross_approximation(M, r, rows=None, cols=None):
         if a[i] <= 0.0:
             i = -1
     return U, V, prow, pcol
+
+
+def assemble_dense_level_ranks(D, Ur, Vr, L, level_ranks):
+    """The N x N matrix of a HODLR matrix with per-level ranks r_c in the
+    ragged layout (level c's bases in columns sum(r_1..r_{c-1}) .. + r_c - 1):
+    leaf blocks on the diagonal and A(I_alpha, I_beta) = U_alpha V_beta^T with
+    U_alpha, V_beta the r_c-column blocks of their level (Eq. e:rank)."""
+    nleaf, m, _ = D.shape
+    N = nleaf * m
+    A = np.zeros((N, N))
+    for b in range(nleaf):
+        A[b * m:(b + 1) * m, b * m:(b + 1) * m] = D[b]
+    off = 0
+    for c in range(1, L + 1):
+        n = N >> c
+        cols = slice(off, off + level_ranks[c - 1])
+        for j in range(1 << (c - 1)):
+            a, b = 2 * j, 2 * j + 1
+            ra, rb = slice(a * n, (a + 1) * n), slice(b * n, (b + 1) * n)
+            A[ra, rb] = Ur[ra, cols] @ Vr[rb, cols].T
+            A[rb, ra] = Ur[rb, cols] @ Vr[ra, cols].T
+        off += level_ranks[c - 1]
+    return A

@@ -32,7 +32,7 @@ HODLR_ERR_NOT_CONVERGED = 7
 HODLR_ERR_TIMEOUT = 8
 HODLR_ERR_SCRATCH_LIMIT = 9
 
-PREC = {"fp64": 0, "fp32": 1, "bf16": 3}
+PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
 
 EXPORTED = (
     "hodlr_strerror", "hodlr_factor_workspace_size", "hodlr_factor", "hodlr_factor_status", "hodlr_free",
@@ -42,7 +42,7 @@ EXPORTED = (
     "hodlr_profile_name", "hodlr_profile_work", "hodlr_tc_enable", "hodlr_grad_workspace_size", "hodlr_grad",
     "hodlr_matvec_noalloc", "hodlr_probe_fp64_fma", "hodlr_coupling_fp64_enable",
     "hodlr_compress_workspace_size", "hodlr_compress", "hodlr_factor_inplace_workspace_size",
-    "hodlr_factor_inplace",
+    "hodlr_factor_inplace", "hodlr_pack_level_ranks",
 )
 
 KERNEL = {"bie_star": 0, "gaussian": 1, "matern32": 2}
@@ -50,7 +50,7 @@ KERNEL = {"bie_star": 0, "gaussian": 1, "matern32": 2}
 
 class hodlr_kernel_desc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("dim", ctypes.c_int32), ("points", ctypes.c_void_p),
-                ("scale", ctypes.c_double), ("nugget", ctypes.c_double)]
+                ("scale", ctypes.c_double), ("nugget", ctypes.c_double), ("tol", ctypes.c_double)]
 
 
 class HodlrError(RuntimeError):
@@ -92,8 +92,9 @@ _SIGS = {
     "hodlr_tc_enable": ([_i32], None),
     "hodlr_coupling_fp64_enable": ([_i32], None),
     "hodlr_compress_workspace_size": ([_vp, _c.POINTER(_sz)], _c.c_int),
-    "hodlr_compress": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _c.c_int),
+    "hodlr_compress": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp], _c.c_int),
     "hodlr_factor_inplace_workspace_size": ([_vp, _c.POINTER(_sz)], _c.c_int),
+    "hodlr_pack_level_ranks": ([_vp, _c.POINTER(_i32), _vp, _i64, _vp, _i64, _vp, _vp, _vp, _sz, _vp], _c.c_int),
     "hodlr_factor_inplace": ([_vp, _vp, _vp, _vp, _vp, _sz, _vp, _c.POINTER(_vp)], _c.c_int),
     "hodlr_matvec_noalloc": ([_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64, _i32, _vp], _c.c_int),
     "hodlr_probe_fp64_fma": ([_i64, _i32, _vp, _vp, _c.POINTER(_i64)], _c.c_int),
@@ -455,11 +456,14 @@ def hodlr_matvec_noalloc(D, U, V, L: int, r: int, X: torch.Tensor, Y: torch.Tens
 
 # --------------------------------------------------------------- construction
 def hodlr_compress(N: int, L: int, r: int, kind: str, points: torch.Tensor | None = None, scale: float = 1.0,
-                   nugget: float = 0.0, want_pivots: bool = False, device=None):
-    """(D, U, V[, pivots]) of the HODLR approximation of a built-in kernel or
-    BIE matrix, built on the GPU (leaf blocks exact, off-diagonal blocks by a
-    partial-pivoted cross approximation at rank r). points: (N, dim) float64
-    CUDA tensor in tree order (kernel matrices), None for 'bie_star'."""
+                   nugget: float = 0.0, want_pivots: bool = False, device=None, tol: float = 0.0,
+                   want_ranks: bool = False):
+    """(D, U, V[, pivots][, ranks]) of the HODLR approximation of a built-in
+    kernel or BIE matrix, built on the GPU (leaf blocks exact, off-diagonal
+    blocks by a partial-pivoted cross approximation at rank r, or stopped at
+    the relative pivot tolerance tol: per-block ranks, zero-padded bases).
+    points: (N, dim) float64 CUDA tensor in tree order (kernel matrices),
+    None for 'bie_star'."""
     if kind not in KERNEL:
         raise ValueError(f"kind must be one of {sorted(KERNEL)}")
     m = N >> L
@@ -475,15 +479,38 @@ def hodlr_compress(N: int, L: int, r: int, kind: str, points: torch.Tensor | Non
         raise ValueError("kernel matrices need points")
     desc = hodlr_desc(N=N, L=L, m=m, r=r, reserved=0, ldu=N, ldv=N)
     kd = hodlr_kernel_desc(kind=KERNEL[kind], dim=dim, points=points.data_ptr() if points is not None else None,
-                           scale=float(scale), nugget=float(nugget))
+                           scale=float(scale), nugget=float(nugget), tol=float(tol))
     D = torch.empty(1 << L, m, m, dtype=torch.float64, device=device).transpose(1, 2)
     U = torch.empty(r * L, N, dtype=torch.float64, device=device).T
     V = torch.empty(r * L, N, dtype=torch.float64, device=device).T
     piv = torch.empty(2 * r * ((2 << L) - 2), dtype=torch.int32, device=device) if want_pivots else None
+    rk = torch.empty((2 << L) - 2, dtype=torch.int32, device=device) if want_ranks else None
     out = ctypes.c_size_t()
     _check(_LIB.hodlr_compress_workspace_size(ctypes.byref(desc), ctypes.byref(out)))
     ws = _workspace(out.value, device)
     _check(_LIB.hodlr_compress(ctypes.byref(desc), ctypes.byref(kd), _ptr(D), _ptr(U), _ptr(V),
-                               _ptr(piv) if piv is not None else None, _ptr(ws), ws.numel(), _stream()),
-           "hodlr_compress: ")
-    return (D, U, V, piv) if want_pivots else (D, U, V)
+                               _ptr(piv) if piv is not None else None, _ptr(rk) if rk is not None else None,
+                               _ptr(ws), ws.numel(), _stream()), "hodlr_compress: ")
+    return (D, U, V) + ((piv,) if want_pivots else ()) + ((rk,) if want_ranks else ())
+
+
+def hodlr_pack_level_ranks(Ur: torch.Tensor, Vr: torch.Tensor, L: int, level_ranks, r: int | None = None):
+    """Uniform (U, V) of width r (default max rank) from the ragged per-level
+    layout (level c's bases in columns sum(r_1..r_{c-1}) .. + r_c - 1)."""
+    lr = [int(x) for x in level_ranks]
+    if len(lr) != L:
+        raise ValueError("level_ranks needs L entries")
+    r = max(lr) if r is None else r
+    N = Ur.shape[0]
+    ldur, ldvr = _ld(Ur, N), _ld(Vr, N)
+    if Ur.shape[1] != sum(lr) or Vr.shape[1] != sum(lr):
+        raise ValueError("Ur, Vr must have sum(level_ranks) columns")
+    _on_current_device(Ur, Vr)
+    U = torch.empty(r * L, N, dtype=torch.float64, device=Ur.device).T
+    V = torch.empty(r * L, N, dtype=torch.float64, device=Ur.device).T
+    desc = hodlr_desc(N=N, L=L, m=N >> L, r=r, reserved=0, ldu=N, ldv=N)
+    ws = _workspace(2 * L * 4, Ur.device)
+    arr = (ctypes.c_int32 * L)(*lr)
+    _check(_LIB.hodlr_pack_level_ranks(ctypes.byref(desc), arr, _ptr(Ur), ldur, _ptr(Vr), ldvr, _ptr(U), _ptr(V),
+                                       _ptr(ws), ws.numel(), _stream()), "hodlr_pack_level_ranks: ")
+    return U, V

@@ -99,7 +99,8 @@ struct Layout {
 size_t panel_elem_bytes(hodlr_prec p) {
   switch (p) {
     case HODLR_PREC_FP64: return 8;
-    case HODLR_PREC_FP32: return 4;
+    case HODLR_PREC_FP32:
+    case HODLR_PREC_TF32: return 4;
     default: return 2;
   }
 }
@@ -157,7 +158,7 @@ hodlr_status check_desc(const hodlr_desc* d) {
 }
 
 bool prec_ok(hodlr_prec p) {
-  return p == HODLR_PREC_FP64 || p == HODLR_PREC_FP32 || p == HODLR_PREC_BF16;
+  return p == HODLR_PREC_FP64 || p == HODLR_PREC_FP32 || p == HODLR_PREC_TF32 || p == HODLR_PREC_BF16;
 }
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
@@ -186,6 +187,11 @@ hodlr_status factor_levels(Factor& F, cudaStream_t s) {
       if (g_use_tc && project_tc_supported(d.N, d.r, c))
         HODLR_CUDA(launch_project_tc(d.N, d.r, d.L, c, Vp, F.ldvp, Y, F.P, F.status, s,
                                      rhs_ready ? F.rhs16 : nullptr));
+      else
+        HODLR_CUDA(launch_project<TP, TP>(d.N, d.r, c, Vp, F.ldvp, c - 1, Y, d.N, rc, F.P, 0, s));
+    } else if constexpr (std::is_same<TP, float>::value) {
+      if (F.prec == HODLR_PREC_TF32 && g_use_tc && project_tc_supported(d.N, d.r, c))
+        HODLR_CUDA(launch_project_tc32(d.N, d.r, d.L, c, Vp, F.ldvp, Y, F.P, F.status, s));
       else
         HODLR_CUDA(launch_project<TP, TP>(d.N, d.r, c, Vp, F.ldvp, c - 1, Y, d.N, rc, F.P, 0, s));
     } else {
@@ -265,7 +271,7 @@ hodlr_status solve_any(const Factor& F, double* B, int64_t ldb, int k, void* wor
                                                     align_up((size_t)d.N * k * sizeof(float)))
                         : nullptr;
   HODLR_CUDA((launch_copy_cols<float, double>(d.N, k, B, ldb, xw, d.N, s)));
-  hodlr_status st = F.prec == HODLR_PREC_FP32
+  hodlr_status st = F.prec != HODLR_PREC_BF16  // FP32 panels (FP32 and TF32 factors)
                         ? solve_core<float, float>(F, xw, d.N, k, Ps, trans, s, parts)
                         : solve_core<__nv_bfloat16, float>(F, xw, d.N, k, Ps, trans, s, parts);
   if (st != HODLR_OK) return st;
@@ -404,7 +410,7 @@ static hodlr_status factor_entry(const hodlr_desc* desc, const double* D, const 
     if (launch_leaf_solve<double, double>(*F, U, d.ldu, static_cast<double*>(F->Y), d.N, rL, 0, s) != cudaSuccess)
       return fail(HODLR_ERR_CUDA);
     r = factor_levels<double>(*F, s);
-  } else if (prec == HODLR_PREC_FP32) {
+  } else if (prec == HODLR_PREC_FP32 || prec == HODLR_PREC_TF32) {
     if (launch_copy_cols<float, double>(d.N, rL, V, d.ldv, static_cast<float*>(const_cast<void*>(F->Vp)), d.N, s) !=
         cudaSuccess)
       return fail(HODLR_ERR_CUDA);
@@ -958,7 +964,7 @@ hodlr_status grad_core(const Factor& F, const double* U, const double* V, const 
 extern "C" {
 
 hodlr_status hodlr_grad_workspace_size(hodlr_factor_t f, int32_t k, size_t* bytes) {
-  if (!valid_factor(f) || (f->prec != HODLR_PREC_FP64 && f->prec != HODLR_PREC_FP32) || k < 1 || k > 64 || !bytes)
+  if (!valid_factor(f) || f->prec == HODLR_PREC_BF16 || k < 1 || k > 64 || !bytes)
     return HODLR_ERR_ARG;
   *bytes = grad_layout(*f, k).total;
   return HODLR_OK;
@@ -967,7 +973,7 @@ hodlr_status hodlr_grad_workspace_size(hodlr_factor_t f, int32_t k, size_t* byte
 hodlr_status hodlr_grad(hodlr_factor_t f, const double* U, const double* V, const double* B, int64_t ldb, int32_t k,
                         double* dD, double* dU, double* dV, double* dB, int64_t lddb, void* workspace,
                         size_t workspace_bytes, hodlr_stream_t stream, double* loss) {
-  if (!valid_factor(f) || (f->prec != HODLR_PREC_FP64 && f->prec != HODLR_PREC_FP32) || !U || !V || !B || !dD ||
+  if (!valid_factor(f) || f->prec == HODLR_PREC_BF16 || !U || !V || !B || !dD ||
       !dU || !dV || !dB || k < 1 || k > 64 || ldb < f->d.N || lddb < f->d.N)
     return HODLR_ERR_ARG;
   const GradLayout lay = grad_layout(*f, k);

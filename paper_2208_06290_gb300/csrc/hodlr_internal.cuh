@@ -305,6 +305,8 @@ bool project_tc_supported(int64_t N, int r, int c);
 cudaError_t launch_project_tc(int64_t N, int r, int L, int c, const __nv_bfloat16* Vp, int64_t ldv,
                               const __nv_bfloat16* Y, double* P, DevStatus* st, cudaStream_t s,
                               uint8_t* rhs16 = nullptr);
+cudaError_t launch_project_tc32(int64_t N, int r, int L, int c, const float* Vp, int64_t ldv, const float* Y,
+                                double* P, DevStatus* st, cudaStream_t s);
 // Coupling solve fused into the tensor-core ancestor update (BF16 factor):
 // uses the raw projections in each node's first slot, the coupling inverses
 // and the BF16 right-hand-side staging area rhs16 (rhs_bf16_bytes).

@@ -94,6 +94,74 @@ __global__ void __launch_bounds__(256) mv1_leaf_project16_kernel(int rL, int ngr
   if (lane < 16 && c0 + lane < rL) pleaf[(size_t)b * rL + c0 + lane] = t;
 }
 
+// 1 (m = 128, 4 | nleaf, 16-byte aligned V and x, even ldv). One warp per
+// (4 consecutive leaves, 16 basis columns): the 8 lanes of group g cover
+// leaf 4w + g, lane q of the group rows 16q .. 16q+15 (eight 16-byte loads
+// per column), so each lane's partial is a 16-row dot product and the
+// per-leaf totals take a transposed butterfly over the group's 3 lane bits
+// (14 FP64 adds per lane against 256 FMAs; the FP64 pipe is this kernel's
+// bound). Lane q of a group ends with the totals of columns 2q and 2q + 1
+// of its leaf.
+__global__ void __launch_bounds__(256) mv1_leaf_project_g8_kernel(int rL, int ngroups, int64_t nleaf,
+                                                                  const double* __restrict__ V, int64_t ldv,
+                                                                  const double* __restrict__ x,
+                                                                  double* __restrict__ pleaf) {
+  const int lane = threadIdx.x & 31;
+  const int64_t item = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (item >= (nleaf / 4) * ngroups) return;  // whole warp
+  const int64_t b = (item / ngroups) * 4 + (lane >> 3);
+  const int c0 = (int)(item % ngroups) * 16;
+  const int q = lane & 7;
+  const int64_t row = b * 128 + 16 * q;
+  double xv[16];
+#pragma unroll
+  for (int t = 0; t < 16; t += 4) {
+    double a[4];
+    load4(x + row + t, a);
+    xv[t] = a[0];
+    xv[t + 1] = a[1];
+    xv[t + 2] = a[2];
+    xv[t + 3] = a[3];
+  }
+  double v[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    v[j] = 0.0;
+    if (c0 + j < rL) {
+      const double* col = V + (int64_t)(c0 + j) * ldv + row;
+      double acc = 0.0;
+#pragma unroll
+      for (int t = 0; t < 16; t += 4) {
+        double a[4];
+        load4(col + t, a);
+        acc = fma(a[0], xv[t], acc);
+        acc = fma(a[1], xv[t + 1], acc);
+        acc = fma(a[2], xv[t + 2], acc);
+        acc = fma(a[3], xv[t + 3], acc);
+      }
+      v[j] = acc;
+    }
+  }
+  // transposed butterfly over lane bits 2, 1, 0 (within the group of 8):
+  // after the step on bit s the lanes with that bit set keep the upper half
+  // of the remaining columns
+  int base = 0;
+#pragma unroll
+  for (int s = 4, h = 8; s >= 1; s >>= 1, h >>= 1) {
+    const bool upper = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const double send = upper ? v[i] : v[i + h];
+      const double keep = upper ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+    base += upper ? h : 0;
+  }
+  // v[0], v[1]: totals of columns c0 + base, c0 + base + 1 of leaf b
+  if (c0 + base < rL) pleaf[(size_t)b * rL + c0 + base] = v[0];
+  if (c0 + base + 1 < rL) pleaf[(size_t)b * rL + c0 + base + 1] = v[1];
+}
+
 // 2a. Partial sums over runs of at most 64 consecutive leaves (never across
 // a node boundary), all levels in one launch: one CTA of r threads per
 // (level c, run), runs numbered level by level; thread j sums column
@@ -191,7 +259,11 @@ cudaError_t launch_matvec1(const hodlr_desc& d, const double* D, const double* U
     note_work(8.0 * ((double)d.N * rL + d.N + nleaf * rL), 2.0 * d.N * rL);
     const bool vec16 = m == 128 && ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(x)) % 16 == 0) &&
                        d.ldv % 2 == 0;
-    if (vec16) {
+    if (vec16 && nleaf % 4 == 0) {
+      const int ngroups = (rL + 15) / 16;
+      const int64_t warps = nleaf / 4 * ngroups;
+      { mv1_leaf_project_g8_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(rL, ngroups, nleaf, V, d.ldv, x, pleaf); note_launches(1); }
+    } else if (vec16) {
       const int ngroups = (rL + 15) / 16;
       const int64_t warps = nleaf * ngroups;
       { mv1_leaf_project16_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(rL, ngroups, nleaf, V, d.ldv, x, pleaf); note_launches(1); }

@@ -15,14 +15,14 @@ namespace hodlr {
 
 namespace {
 
-constexpr int kBK = 64;       // rows per stage
+constexpr int kBK = 64;       // rows per stage (BF16; 32 for FP32 tiles: 128 bytes of each column either way)
 constexpr int kBM = 128;      // Y columns per tile
 constexpr int kStages = 4;
-constexpr uint32_t kABytes = kBM * kBK * 2;
+constexpr uint32_t kABytes = kBM * 128;  // 128 columns x 128 bytes of rows
 
 template <int RN>
 struct ProjSmem {
-  static constexpr uint32_t kBBytes = RN * kBK * 2;
+  static constexpr uint32_t kBBytes = RN * 128;
   static constexpr uint32_t kStageBytes = kABytes + kBBytes;
   static constexpr uint32_t kBarOff = kStages * kStageBytes;
   static constexpr uint32_t kBytes = kBarOff + 256 + 1024;  // + barriers, + alignment slack
@@ -39,7 +39,10 @@ struct ProjSmem {
 // straight into the BF16 right-hand-side operand of its parent (the layout
 // of rhs_bf16_kernel: rows 0..r-1 from the second child, r..2r-1 from the
 // first), and only the own block (the coupling's T) into P in FP64.
-template <int RN>
+// T = __nv_bfloat16 (BF16 factor, kind::f16, 64 rows per stage) or float
+// (TF32 factor: FP32 tiles read by kind::tf32, 32 rows per stage); both give
+// 128-byte swizzled rows, 4 MMAs of 32 bytes of K per stage.
+template <int RN, typename T = __nv_bfloat16>
 __global__ void __launch_bounds__(128) project_tc_kernel(const __grid_constant__ CUtensorMap mapY,
                                                          const __grid_constant__ CUtensorMap mapV, int64_t ch,
                                                          int64_t nchunks, int vcol, int rc, double* __restrict__ P,
@@ -71,9 +74,11 @@ __global__ void __launch_bounds__(128) project_tc_kernel(const __grid_constant__
   tc::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
+  constexpr int kRows = 128 / (int)sizeof(T);  // rows per stage
+  constexpr bool kTF32 = sizeof(T) == 4;
   const int mtiles = (rc + kBM - 1) / kBM;
   const int64_t items = nchunks * mtiles;
-  const int nk = (int)(ch / kBK);
+  const int nk = (int)(ch / kRows);
   uint32_t kt_global = 0;  // stage-use counter shared by producer and MMA issuer (same sequence)
   uint32_t item_count = 0;
   bool ok = true;
@@ -89,11 +94,11 @@ __global__ void __launch_bounds__(128) project_tc_kernel(const __grid_constant__
         if (g >= (uint32_t)kStages && !tc::mbar_wait(&empty[s], ((g / kStages) - 1) & 1)) { ok = false; break; }
         uint8_t* a = smem + s * S::kStageBytes;
         tc::mbar_expect_tx(&full[s], S::kStageBytes);
-        tc::tma_load_2d(a, &mapY, (int32_t)(row0 + kt * kBK), col0, &full[s]);
-        tc::tma_load_2d(a + kABytes, &mapV, (int32_t)(row0 + kt * kBK), vcol, &full[s]);
+        tc::tma_load_2d(a, &mapY, (int32_t)(row0 + kt * kRows), col0, &full[s]);
+        tc::tma_load_2d(a + kABytes, &mapV, (int32_t)(row0 + kt * kRows), vcol, &full[s]);
       }
     } else if (warp == 1 && lane == 0) {
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(kBM, RN);
+      constexpr uint32_t idesc = kTF32 ? tc::idesc_tf32_f32(kBM, RN) : tc::idesc_bf16_f32(kBM, RN);
       for (int kt = 0; kt < nk; ++kt) {
         const uint32_t g = kt_global + kt;
         const int s = g % kStages;
@@ -103,8 +108,12 @@ __global__ void __launch_bounds__(128) project_tc_kernel(const __grid_constant__
         const uint64_t ad = tc::desc_sw128_kmajor(a);
         const uint64_t bd = tc::desc_sw128_kmajor(a + kABytes);
 #pragma unroll
-        for (int kk = 0; kk < kBK / 16; ++kk)
-          tc::mma_bf16(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kt | kk) != 0);
+        for (int kk = 0; kk < 4; ++kk) {  // 32 bytes of K each (16 BF16 / 8 TF32)
+          if constexpr (kTF32)
+            tc::mma_tf32(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kt | kk) != 0);
+          else
+            tc::mma_bf16(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kt | kk) != 0);
+        }
         tc::mma_commit(&empty[s]);
       }
       tc::mma_commit(done);
@@ -124,7 +133,7 @@ __global__ void __launch_bounds__(128) project_tc_kernel(const __grid_constant__
       for (int cc = 0; cc < (RN + 31) / 32; ++cc) {
         float v[32];
         tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + cc * 32, v);
-        if (rhs16 && m < anc) {
+        if (!kTF32 && rhs16 && m < anc) {
           // row k = koff + n of the parent's [W_beta; W_alpha]^T, column m
           const int koff = (q & 1) ? 0 : RN;
           constexpr int kNC = 64;  // ancestor columns per block of the operand (the fused update's chunk)
@@ -184,14 +193,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // 2-D BF16 tensor map over a column-major rows x cols matrix (leading
 // dimension ld elements), box = box_rows (inner) x box_cols, 128-byte swizzle.
 bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
-              int box_cols) {
+              int box_cols, bool fp32 = false) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
-  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * (fp32 ? 4 : 2)};
   cuuint32_t box[2] = {(cuuint32_t)box_rows, (cuuint32_t)box_cols};
   cuuint32_t estr[2] = {1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+  return fn(map, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+            const_cast<void*>(base), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -207,22 +217,24 @@ int sm_count() {
   return n;
 }
 
-template <int RN>
-cudaError_t project_tc_go(const __nv_bfloat16* Vp, int64_t ldv, const __nv_bfloat16* Y, int64_t N, int rL, int c,
+template <int RN, typename T>
+cudaError_t project_tc_go(const T* Vp, int64_t ldv, const T* Y, int64_t N, int rL, int c,
                           int rc, double* P, DevStatus* st, cudaStream_t s, uint8_t* rhs16) {
   using S = ProjSmem<RN>;
+  constexpr bool f32 = sizeof(T) == 4;
+  constexpr int kRows = 128 / (int)sizeof(T);
   CUtensorMap mY, mV;
-  if (!make_map(&mY, Y, N, rL, N, kBK, kBM)) return cudaErrorInvalidValue;
-  if (!make_map(&mV, Vp, N, rL, ldv, kBK, RN)) return cudaErrorInvalidValue;
+  if (!make_map(&mY, Y, N, rL, N, kRows, kBM, f32)) return cudaErrorInvalidValue;
+  if (!make_map(&mV, Vp, N, rL, ldv, kRows, RN, f32)) return cudaErrorInvalidValue;
   const int64_t ch = chunk_rows(N, c);
   const int64_t nch = num_chunks(N, c);
   const int64_t items = nch * ((rc + kBM - 1) / kBM);
   const int per_sm = (int)((227 * 1024) / S::kBytes);
   int64_t grid = (int64_t)sm_count() * (per_sm < 1 ? 1 : per_sm);
   if (grid > items) grid = items;
-  cudaFuncSetAttribute(project_tc_kernel<RN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kBytes);
-  { project_tc_kernel<RN><<<(unsigned)grid, 128, S::kBytes, s>>>(mY, mV, ch, nch, (c - 1) * RN, rc, P, st, c,
-                                                                   rhs16, RN * (c - 1)); note_launches(1); }
+  cudaFuncSetAttribute(project_tc_kernel<RN, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kBytes);
+  { project_tc_kernel<RN, T><<<(unsigned)grid, 128, S::kBytes, s>>>(mY, mV, ch, nch, (c - 1) * RN, rc, P, st, c,
+                                                                      rhs16, RN * (c - 1)); note_launches(1); }
   return cudaGetLastError();
 }
 
@@ -241,8 +253,18 @@ cudaError_t launch_project_tc(int64_t N, int r, int L, int c, const __nv_bfloat1
                 (rhs16 ? 8.0 * num_chunks(N, c) * r * r + 2.0 * num_chunks(N, c) * r * anc
                        : 8.0 * num_chunks(N, c) * r * rc),
             2.0 * N * r * (double)rc);
-  if (r == 32) return project_tc_go<32>(Vp, ldv, Y, N, r * L, c, rc, P, st, s, rhs16);
-  return project_tc_go<64>(Vp, ldv, Y, N, r * L, c, rc, P, st, s, rhs16);
+  if (r == 32) return project_tc_go<32, __nv_bfloat16>(Vp, ldv, Y, N, r * L, c, rc, P, st, s, rhs16);
+  return project_tc_go<64, __nv_bfloat16>(Vp, ldv, Y, N, r * L, c, rc, P, st, s, rhs16);
+}
+
+// TF32 factor: FP32 panels, projections on kind::tf32
+cudaError_t launch_project_tc32(int64_t N, int r, int L, int c, const float* Vp, int64_t ldv, const float* Y,
+                                double* P, DevStatus* st, cudaStream_t s) {
+  ProfScope prof_(KC_PROJECT_TC, s);
+  const int rc = r * c;
+  note_work(4.0 * (double)N * r + 4.0 * (double)N * rc + 8.0 * num_chunks(N, c) * r * rc, 2.0 * N * r * (double)rc);
+  if (r == 32) return project_tc_go<32, float>(Vp, ldv, Y, N, r * L, c, rc, P, st, s, nullptr);
+  return project_tc_go<64, float>(Vp, ldv, Y, N, r * L, c, rc, P, st, s, nullptr);
 }
 
 

@@ -70,7 +70,10 @@ def test_small_leading_dimension_rejected(hb):
 def test_bad_precision_rejected(hb):
     d = hb.hodlr_desc(N=256, L=2, m=64, r=4, reserved=0, ldu=256, ldv=256)
     out = ctypes.c_size_t()
-    assert hb._LIB.hodlr_factor_workspace_size(ctypes.byref(d), 2, ctypes.byref(out)) == hb.HODLR_ERR_ARG
+    for bad in (-1, 4, 7):
+        assert hb._LIB.hodlr_factor_workspace_size(ctypes.byref(d), bad, ctypes.byref(out)) == hb.HODLR_ERR_ARG
+    for good in hb.PREC.values():
+        assert hb._LIB.hodlr_factor_workspace_size(ctypes.byref(d), good, ctypes.byref(out)) == hb.HODLR_OK
 
 
 def test_factor_rejects_small_workspace_before_any_launch(hb):

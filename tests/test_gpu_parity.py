@@ -106,7 +106,7 @@ def test_dense_c0_configuration(cuda_lib):
     assert s == sd and abs(la - lad) <= LD_TOL * abs(lad)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
 @pytest.mark.parametrize("N,L,r", [(256, 2, 4), (384, 3, 5), (800, 3, 8), (4096, 6, 16), (2048, 3, 32),
                                    (1024, 4, 64), (1 << 14, 6, 8), (1 << 13, 6, 16), (1 << 14, 7, 32)])
 def test_mixed_refined_reaches_1e10(cuda_lib, prec, N, L, r):
@@ -128,6 +128,30 @@ def test_mixed_refined_reaches_1e10(cuda_lib, prec, N, L, r):
     # near the identity, so BF16 panels add little (bounds 1e-5 / 1e-4 leave
     # orders of margin over the measured errors)
     assert abs(la - lao) <= (1e-5 if prec == "fp32" else 1e-4) * max(1.0, abs(lao))
+
+
+@pytest.mark.parametrize("N,L,r", [(1 << 14, 7, 32), (1 << 15, 7, 64), (1 << 16, 9, 32)])
+def test_tf32_factor_projects_on_tensor_cores(cuda_lib, N, L, r):
+    """The TF32 factor (FP32 panels, projections on tcgen05 kind::tf32) runs
+    every level's projection on the tensor cores and agrees with the FP32
+    factor to TF32 rounding (operands with a 10-bit significand: products
+    within 2^-11 relative, FP32 accumulation): solutions within 1e-2 of each
+    other and of the oracle's exact solve, refined to the spec residual."""
+    hb = cuda_lib
+    (Dm, Um, Vm, Bm), (D, U, V, B) = make_case(N, L, r, seed=91 + r, k=2)
+    F32 = hb.hodlr_factor(D, U, V, L, r, "fp32")
+    X32 = hb.hodlr_solve(F32, B.clone()).cpu().numpy()
+    hb.hodlr_profile_reset()
+    hb.hodlr_profile_enable(True)
+    Ft = hb.hodlr_factor(D, U, V, L, r, "tf32")
+    hb.hodlr_profile_enable(False)
+    assert hb.hodlr_profile_read()["project_tc"][1] == L
+    assert hb.hodlr_factor_status(Ft)[0] == 0
+    Xt = hb.hodlr_solve(Ft, B.clone()).cpu().numpy()
+    close(Xt, X32, 1e-2)
+    close(Xt, RecursiveHODLR(Dm, Um, Vm, L).solve(Bm), 1e-2)
+    X, it, rr, code = hb.hodlr_solve_refined(Ft, D, U, V, B, tol=1e-10, max_iter=60)
+    assert code == 0 and rr <= 1e-10
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
@@ -248,9 +272,12 @@ def test_bf16_tensor_core_factor_matches_cuda_core(cuda_lib, N, L, r):
 
 
 @pytest.mark.parametrize("N,L,r", [(256, 2, 4), (384, 3, 5), (128, 1, 3), (4096, 6, 16), (2048, 3, 32),
-                                   (1 << 14, 6, 64)])
+                                   (1 << 14, 6, 64), (256, 1, 4), (1 << 10, 3, 8), (1 << 12, 5, 16),
+                                   (1 << 14, 7, 32), (3 << 10, 5, 24)])
 def test_matvec_fp64_single_rhs(cuda_lib, N, L, r):
-    """k = 1 takes the four-launch path (all levels' projections per leaf)."""
+    """k = 1 takes the four-launch path (all levels' projections per leaf);
+    leaves of 128 rows use the vectorized projection kernels (16 rows per
+    lane when the leaves come in fours, 4 rows per lane otherwise)."""
     hb = cuda_lib
     (Dm, Um, Vm, Bm), (D, U, V, B) = make_case(N, L, r, seed=5 * N + r, k=1)
     Y = hb.hodlr_matvec(D, U, V, L, r, B)
