@@ -125,11 +125,28 @@ def _qr(Y):
     return _orth(Y)[0]
 
 
-def _svd(B):
-    """SVD of small wide matrices (rank-r core factors): on the CPU in FP64,
-    where LAPACK handles batches of small matrices quickly."""
-    U, S, Vh = torch.linalg.svd(B.double().cpu(), full_matrices=False)
-    return U.to(B.device, B.dtype), S.to(B.device, B.dtype), Vh.to(B.device, B.dtype)
+def _core_split(Bt, r, rtol=1e-14):
+    """Rank-r split of the small wide cores B = Bt^T (p x n, p = r + oversampling):
+    with B B^T = E diag(lambda) E^T (FP64 Gram matrix formed on the device,
+    eigendecomposed on the CPU), the left factor E_r diag(sigma_r)^(1/2) and
+    the right factor B^T E_r diag(sigma_r)^(-1/2), sigma = lambda^(1/2), for
+    the r largest lambda; their product E_r E_r^T B is B projected on its
+    dominant left singular subspace, as the truncated SVD gives. Directions
+    with lambda <= rtol * lambda_max (below the Gram matrix's resolution) get
+    zero columns. Cores of very low rank have many zero rows (directions the
+    range finder dropped); the eigensolver takes them as they are, unlike
+    some LAPACK builds' SVD."""
+    Bd = Bt.double()
+    G = (Bd.transpose(1, 2) @ Bd).cpu()
+    lam, E = torch.linalg.eigh(G)                         # ascending
+    lam = lam[:, -r:].flip(-1)
+    E = E[:, :, -r:].flip(-1)
+    keep = lam > rtol * lam[:, :1].clamp(min=1e-300)
+    q = torch.where(keep, lam.clamp(min=1e-300) ** 0.25, torch.zeros_like(lam))   # sigma^(1/2)
+    qinv = torch.where(keep, 1.0 / q.clamp(min=1e-300), torch.zeros_like(lam))
+    left = (E * q[:, None, :]).to(Bt.device, Bt.dtype)       # p x r
+    right = (E * qinv[:, None, :]).to(Bt.device)             # p x r, applied to B^T below
+    return left, (Bd @ right).to(Bt.dtype)
 
 
 def _rsvd_blocks(entries, row_start, col_start, n, r, g, device, oversample=10, budget=1 << 27):
@@ -170,11 +187,10 @@ def _rsvd_blocks(entries, row_start, col_start, n, r, g, device, oversample=10, 
         Om = torch.randn(nb, n, p, generator=g, device=device)
         Q = _qr(times(Om))
         Q = _qr(times(_qr(ttimes(Q))))
-        Bt = ttimes(Q)                                  # block^T Q
-        Ub_, S, Vh = _svd(Bt.transpose(1, 2))
-        sq = torch.sqrt(S[:, :r])
-        Uo[b0:b1] = (Q @ Ub_[:, :, :r]) * sq[:, None, :]
-        Vo[b0:b1] = Vh[:, :r, :].transpose(1, 2) * sq[:, None, :]
+        Bt = ttimes(Q)                                  # block^T Q = B^T
+        left, right = _core_split(Bt, r)
+        Uo[b0:b1] = Q @ left
+        Vo[b0:b1] = right
     return Uo, Vo
 
 
@@ -258,7 +274,6 @@ def bie_hodlr(shape: HodlrShape, device="cpu", seed=2, stats=None):
     shape.validate()
     N, m = shape.N, shape.m
     x, nrm, w, kappa = star_curve(N, device=device, dtype=torch.float64)
-    x32, n32, w32 = x.float(), nrm.float(), w.float()
     diag = (-0.5 - w * kappa / (4 * math.pi))
 
     def leaf_fn(b0, b1):
@@ -269,7 +284,11 @@ def bie_hodlr(shape: HodlrShape, device="cpu", seed=2, stats=None):
         return blk
 
     def entries(rows, cols):
-        return bie_block(x32, n32, w32, rows, cols)
+        # FP64 geometry: for neighbouring points n(y).(x - y) is second order
+        # in the spacing while x - y is first order, so FP32 coordinates lose
+        # most of its digits (the whole entry at N = 2^16); the compression
+        # then runs on the FP32-rounded entries.
+        return bie_block(x, nrm, w, rows, cols).float()
 
     return _assemble(shape, leaf_fn, entries, seed, device, symmetric=False, stats=stats)
 
@@ -285,7 +304,6 @@ def kernel_hodlr(shape: HodlrShape, dim: int, kind: str, scale: float, nugget: f
     g.manual_seed(seed)
     pts = torch.rand(N, dim, generator=g, device=device, dtype=torch.float64)
     pts = pts[kd_order(pts, m)].contiguous()
-    p32 = pts.float()
 
     def kfun(d2):
         if kind == "gaussian":
@@ -303,8 +321,9 @@ def kernel_hodlr(shape: HodlrShape, dim: int, kind: str, scale: float, nugget: f
         return K
 
     def entries(rows, cols):
-        d2 = ((p32[rows][:, :, None, :] - p32[cols][:, None, :, :]) ** 2).sum(-1)
-        return kfun(d2)
+        # squared distances from the FP64 points, the kernel in FP32
+        d2 = ((pts[rows][:, :, None, :] - pts[cols][:, None, :, :]) ** 2).sum(-1)
+        return kfun(d2.float())
 
     D, U, V = _assemble(shape, leaf_fn, entries, seed, device, symmetric=True, stats=stats)
     return D, U, V, pts
