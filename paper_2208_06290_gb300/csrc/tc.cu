@@ -17,23 +17,83 @@ namespace {
 
 constexpr int kBK = 64;       // rows per stage (BF16; 32 for FP32 tiles: 128 bytes of each column either way)
 constexpr int kBM = 128;      // Y columns per tile
-constexpr int kStages = 4;
 constexpr uint32_t kABytes = kBM * 128;  // 128 columns x 128 bytes of rows
+constexpr int kPjThreads = 192;          // 4 epilogue warps, producer, MMA issuer
 
+// Stage ring: 5 x 20 KB (r = 32) or 4 x 24 KB (r = 64), two CTAs per SM.
 template <int RN>
 struct ProjSmem {
+  static constexpr int kNS = RN <= 32 ? 5 : 4;
   static constexpr uint32_t kBBytes = RN * 128;
   static constexpr uint32_t kStageBytes = kABytes + kBBytes;
-  static constexpr uint32_t kBarOff = kStages * kStageBytes;
-  static constexpr uint32_t kBytes = kBarOff + 256 + 1024;  // + barriers, + alignment slack
+  static constexpr uint32_t kBarOff = kNS * kStageBytes;
+  static constexpr uint32_t kBytes = kBarOff + 256 + 1024;  // + barriers, TMEM slot, flag; + alignment slack
+  static_assert(8 * (2 * kNS + 5) + 8 <= 256, "barrier area");
+  static_assert(2 * (kBytes + 1024) <= 228 * 1024, "two CTAs per SM");
 };
+
+
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  const uint32_t a = tc::smem_u32(bar);
+  const long long t0 = clock64();
+  for (uint32_t it = 0; it < tc::kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 15) == 15) {
+      if (*abort_flag) return false;
+      if (clock64() - t0 > tc::kSpinCycles) {
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+__device__ __forceinline__ void named_bar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// AND of pred over the `count` threads of named barrier `id` (all of them
+// take the same branch afterwards).
+__device__ __forceinline__ bool named_bar_and(int id, int count, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.cta.red.and.pred q, %2, %3, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "r"(count)
+      : "memory");
+  return r != 0;
+}
+
+// Lane 0 waits, the warp learns the outcome (warp-uniform).
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  int r = 1;
+  if ((threadIdx.x & 31) == 0) r = wait_or_abort(bar, parity, abort_flag) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, r, 0) != 0;
+}
 
 }  // namespace
 
-// Persistent: CTA i handles work items i, i + gridDim.x, ... (item = chunk q,
-// column tile mt). Warp 0 lane 0 issues TMA loads, warp 1 lane 0 issues the
-// MMAs, all four warps drain TMEM (warp w owns TMEM lanes 32w..32w+31 =
-// columns of the tile) and write the FP64 partial.
+// Persistent and warp-specialized (192 threads); CTA i handles work items
+// i, i + gridDim.x, ... (item = chunk q, column tile mt):
+//   warp 4, lane 0 (producer): TMA loads of the Y tile and the V block into a
+//     ring of stages, running ahead across items;
+//   warp 5, lane 0 (MMA issuer): one tcgen05.mma chain per item (K = the
+//     chunk's rows) into one of two TMEM accumulators;
+//   warps 0-3 (epilogue; warp w reads TMEM lanes 32w..32w+31 = columns of the
+//     tile): drain an accumulator and write the FP64 partial while the MMAs of
+//     the next item run into the other one.
+// Hand-offs are mbarriers; every wait is bounded and also gives up when
+// another thread has raised the CTA's abort flag; the copies and MMAs in
+// flight are let land (bounded) before the TMEM is freed.
 // With rhs16 (levels where every node is one chunk, ahead of the fused
 // update): the ancestor columns m < anc of a node's projection are written
 // straight into the BF16 right-hand-side operand of its parent (the layout
@@ -43,32 +103,42 @@ struct ProjSmem {
 // (TF32 factor: FP32 tiles read by kind::tf32, 32 rows per stage); both give
 // 128-byte swizzled rows, 4 MMAs of 32 bytes of K per stage.
 template <int RN, typename T = __nv_bfloat16>
-__global__ void __launch_bounds__(128) project_tc_kernel(const __grid_constant__ CUtensorMap mapY,
-                                                         const __grid_constant__ CUtensorMap mapV, int64_t ch,
-                                                         int64_t nchunks, int vcol, int rc, double* __restrict__ P,
-                                                         DevStatus* st, int level, uint8_t* __restrict__ rhs16,
-                                                         int anc) {
+__global__ void __launch_bounds__(kPjThreads) project_tc_kernel(const __grid_constant__ CUtensorMap mapY,
+                                                                const __grid_constant__ CUtensorMap mapV, int64_t ch,
+                                                                int64_t nchunks, int vcol, int rc,
+                                                                double* __restrict__ P, DevStatus* st, int level,
+                                                                uint8_t* __restrict__ rhs16, int anc) {
   using S = ProjSmem<RN>;
+  constexpr int NS = S::kNS;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::kBarOff);
-  uint64_t* empty = full + kStages;
-  uint64_t* done = empty + kStages;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr uint32_t kTmemCols = RN < 32 ? 32 : RN;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::kBarOff);  // [NS] TMA transaction count
+  uint64_t* empty = full + NS;                                       // [NS] MMA commit
+  uint64_t* acc_full = empty + NS;                                   // [2]  MMA commit
+  uint64_t* acc_empty = acc_full + 2;                                // [2]  128 epilogue threads
+  uint64_t* drain = acc_empty + 2;                                   //      MMA commit at exit
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr uint32_t kAcc = RN < 32 ? 32 : RN;  // TMEM columns of one accumulator
+  constexpr uint32_t kTmemCols = 2 * kAcc;
 
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+  if (tid == 0) {
+    for (int s = 0; s < NS; ++s) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
-    tc::mbar_init(done, 1);
+    for (int a = 0; a < 2; ++a) {
+      tc::mbar_init(&acc_full[a], 1);
+      tc::mbar_init(&acc_empty[a], 128);
+    }
+    tc::mbar_init(drain, 1);
+    *abort_flag = 0;
     tc::fence_mbar_init();
     tc::prefetch_tmap(&mapY);
     tc::prefetch_tmap(&mapV);
   }
-  if (warp == 0) tc::tmem_alloc(tmem_slot, kTmemCols);
+  if (warp == 5) tc::tmem_alloc(tmem_slot, kTmemCols);
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
@@ -79,52 +149,75 @@ __global__ void __launch_bounds__(128) project_tc_kernel(const __grid_constant__
   const int mtiles = (rc + kBM - 1) / kBM;
   const int64_t items = nchunks * mtiles;
   const int nk = (int)(ch / kRows);
-  uint32_t kt_global = 0;  // stage-use counter shared by producer and MMA issuer (same sequence)
-  uint32_t item_count = 0;
-  bool ok = true;
-  for (int64_t it = blockIdx.x; it < items; it += gridDim.x, ++item_count) {
-    const int64_t q = it / mtiles;
-    const int mt = (int)(it % mtiles);
-    const int64_t row0 = q * ch;
-    const int col0 = mt * kBM;
-    if (warp == 0 && lane == 0) {
-      for (int kt = 0; kt < nk; ++kt) {
-        const uint32_t g = kt_global + kt;
-        const int s = g % kStages;
-        if (g >= (uint32_t)kStages && !tc::mbar_wait(&empty[s], ((g / kStages) - 1) & 1)) { ok = false; break; }
-        uint8_t* a = smem + s * S::kStageBytes;
-        tc::mbar_expect_tx(&full[s], S::kStageBytes);
-        tc::tma_load_2d(a, &mapY, (int32_t)(row0 + kt * kRows), col0, &full[s]);
-        tc::tma_load_2d(a + kABytes, &mapV, (int32_t)(row0 + kt * kRows), vcol, &full[s]);
-      }
-    } else if (warp == 1 && lane == 0) {
-      constexpr uint32_t idesc = kTF32 ? tc::idesc_tf32_f32(kBM, RN) : tc::idesc_bf16_f32(kBM, RN);
-      for (int kt = 0; kt < nk; ++kt) {
-        const uint32_t g = kt_global + kt;
-        const int s = g % kStages;
-        if (!tc::mbar_wait(&full[s], (g / kStages) & 1)) { ok = false; break; }
-        tc::tc_fence_after();
-        const uint32_t a = tc::smem_u32(smem + s * S::kStageBytes);
-        const uint64_t ad = tc::desc_sw128_kmajor(a);
-        const uint64_t bd = tc::desc_sw128_kmajor(a + kABytes);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {  // 32 bytes of K each (16 BF16 / 8 TF32)
-          if constexpr (kTF32)
-            tc::mma_tf32(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kt | kk) != 0);
-          else
-            tc::mma_bf16(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kt | kk) != 0);
+
+  if (warp == 4) {
+    // ---------------------------------------------------------------- producer
+    if (lane == 0) {
+      uint32_t g = 0;  // stage uses issued
+      bool ok = true;
+      for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        const int64_t row0 = (it / mtiles) * ch;
+        const int col0 = (int)(it % mtiles) * kBM;
+        for (int kt = 0; kt < nk; ++kt, ++g) {
+          const int s = g % NS;
+          if (g >= (uint32_t)NS && !(ok = wait_or_abort(&empty[s], ((g / NS) - 1) & 1, abort_flag))) break;
+          uint8_t* a = smem + s * S::kStageBytes;
+          tc::mbar_expect_tx(&full[s], S::kStageBytes);
+          tc::tma_load_2d(a, &mapY, (int32_t)(row0 + kt * kRows), col0, &full[s]);
+          tc::tma_load_2d(a + kABytes, &mapV, (int32_t)(row0 + kt * kRows), vcol, &full[s]);
         }
-        tc::mma_commit(&empty[s]);
       }
-      tc::mma_commit(done);
+      // let the last copies land before the CTA can exit (bounded)
+      for (uint32_t q = 0; q < (uint32_t)NS && q < g; ++q) {
+        const uint32_t u = g - 1 - q;
+        tc::mbar_wait(&full[u % NS], (u / NS) & 1);
+      }
     }
-    kt_global += nk;
-    // epilogue: wait for the accumulator, drain TMEM, write the FP64 partial.
-    // ok is made block-uniform first: tcgen05.ld is warp-collective.
-    if (!tc::mbar_wait(done, item_count & 1)) ok = false;
-    ok = __syncthreads_and(ok) != 0;
-    tc::tc_fence_after();
-    if (ok) {
+  } else if (warp == 5) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = kTF32 ? tc::idesc_tf32_f32(kBM, RN) : tc::idesc_bf16_f32(kBM, RN);
+      uint32_t g = 0, i = 0;
+      bool ok = true, issued = false;
+      for (int64_t it = blockIdx.x; it < items && ok; it += gridDim.x, ++i) {
+        const uint32_t a = i & 1;
+        if (i >= 2 && !(ok = wait_or_abort(&acc_empty[a], ((i >> 1) - 1) & 1, abort_flag))) break;
+        tc::tc_fence_after();
+        for (int kt = 0; kt < nk; ++kt, ++g) {
+          const int s = g % NS;
+          if (!(ok = wait_or_abort(&full[s], (g / NS) & 1, abort_flag))) break;
+          tc::tc_fence_after();
+          const uint32_t sa = tc::smem_u32(smem + s * S::kStageBytes);
+          const uint64_t ad = tc::desc_sw128_kmajor(sa);
+          const uint64_t bd = tc::desc_sw128_kmajor(sa + kABytes);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {  // 32 bytes of K each (16 BF16 / 8 TF32)
+            if constexpr (kTF32)
+              tc::mma_tf32(tmem + a * kAcc, ad + 2 * kk, bd + 2 * kk, idesc, (kt | kk) != 0);
+            else
+              tc::mma_bf16(tmem + a * kAcc, ad + 2 * kk, bd + 2 * kk, idesc, (kt | kk) != 0);
+          }
+          issued = true;
+          tc::mma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        tc::mma_commit(&acc_full[a]);
+      }
+      // every MMA issued has finished before the TMEM is freed (bounded)
+      if (issued) {
+        tc::mma_commit(drain);
+        tc::mbar_wait(drain, 0);
+      }
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    uint32_t i = 0;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x, ++i) {
+      const int64_t q = it / mtiles;
+      const int col0 = (int)(it % mtiles) * kBM;
+      const uint32_t a = i & 1;
+      if (!warp_wait(&acc_full[a], (i >> 1) & 1, abort_flag)) break;  // warp-uniform: tcgen05.ld is collective
+      tc::tc_fence_after();
       const int m = col0 + warp * 32 + lane;
       double* Pq = P + (size_t)q * RN * rc;
       constexpr int K2 = 2 * RN;
@@ -132,7 +225,7 @@ __global__ void __launch_bounds__(128) project_tc_kernel(const __grid_constant__
 #pragma unroll
       for (int cc = 0; cc < (RN + 31) / 32; ++cc) {
         float v[32];
-        tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + cc * 32, v);
+        tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + a * kAcc + cc * 32, v);
         if (!kTF32 && rhs16 && m < anc) {
           // row k = koff + n of the parent's [W_beta; W_alpha]^T, column m
           const int koff = (q & 1) ? 0 : RN;
@@ -150,28 +243,21 @@ __global__ void __launch_bounds__(128) project_tc_kernel(const __grid_constant__
                 make_uint4(pk[0], pk[1], pk[2], pk[3]);
           }
         } else if (m < rc) {
+          // 16-byte stores of the thread's 32 consecutive doubles
+          double2* dst = reinterpret_cast<double2*>(Pq + (size_t)m * RN + cc * 32);
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (cc * 32 + j < RN) Pq[(size_t)m * RN + cc * 32 + j] = (double)v[j];
+          for (int j = 0; j < 16; ++j)
+            if (cc * 32 + 2 * j < RN) dst[j] = make_double2((double)v[2 * j], (double)v[2 * j + 1]);
         }
       }
-    }
-    tc::tc_fence_before();
-    __syncthreads();
-    tc::tc_fence_after();
-    if (!__syncthreads_and(ok)) break;
-  }
-  // the producer's loads have all landed once the last full[] phases completed
-  if (warp == 0 && lane == 0) {
-    for (int s = 0; s < kStages && (uint32_t)s < kt_global; ++s) {
-      const uint32_t last = kt_global - 1 - ((kt_global - 1 - s) % kStages);
-      if (!tc::mbar_wait(&full[last % kStages], (last / kStages) & 1)) ok = false;
+      tc::tc_fence_before();
+      tc::mbar_arrive(&acc_empty[a]);
     }
   }
-  if (!ok && threadIdx.x == 0) set_status(st, HODLR_ERR_TIMEOUT, level, 0);
   tc::tc_fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+  if (tid == 0 && *abort_flag) set_status(st, HODLR_ERR_TIMEOUT, level, 0);
+  if (warp == 5) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
 // ---------------------------------------------------------------------------
@@ -233,7 +319,7 @@ cudaError_t project_tc_go(const T* Vp, int64_t ldv, const T* Y, int64_t N, int r
   int64_t grid = (int64_t)sm_count() * (per_sm < 1 ? 1 : per_sm);
   if (grid > items) grid = items;
   cudaFuncSetAttribute(project_tc_kernel<RN, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kBytes);
-  { project_tc_kernel<RN, T><<<(unsigned)grid, 128, S::kBytes, s>>>(mY, mV, ch, nch, (c - 1) * RN, rc, P, st, c,
+  { project_tc_kernel<RN, T><<<(unsigned)grid, kPjThreads, S::kBytes, s>>>(mY, mV, ch, nch, (c - 1) * RN, rc, P, st, c,
                                                                       rhs16, RN * (c - 1)); note_launches(1); }
   return cudaGetLastError();
 }
@@ -440,53 +526,6 @@ __global__ void kf32_kernel(int c, const double* __restrict__ Kinv, float* __res
     const int rowoff = (node & 1) ? RK : 0;
     Kf[(size_t)node * RK * LD + (size_t)k * LD + q] = (float)Kj[(size_t)q * K2 + rowoff + k];
   }
-}
-
-__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  const uint32_t a = tc::smem_u32(bar);
-  const long long t0 = clock64();
-  for (uint32_t it = 0; it < tc::kSpinLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if ((it & 15) == 15) {
-      if (*abort_flag) return false;
-      if (clock64() - t0 > tc::kSpinCycles) {
-        *abort_flag = 1;
-        return false;
-      }
-    }
-  }
-  *abort_flag = 1;
-  return false;
-}
-
-__device__ __forceinline__ void named_bar_sync(int id, int count) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
-
-// AND of pred over the `count` threads of named barrier `id` (all of them
-// take the same branch afterwards).
-__device__ __forceinline__ bool named_bar_and(int id, int count, bool pred) {
-  uint32_t r;
-  asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.cta.red.and.pred q, %2, %3, p;\n"
-      " selp.u32 %0, 1, 0, q;\n}\n"
-      : "=r"(r)
-      : "r"((uint32_t)pred), "r"(id), "r"(count)
-      : "memory");
-  return r != 0;
-}
-
-// Lane 0 waits, the warp learns the outcome (warp-uniform).
-__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  int r = 1;
-  if ((threadIdx.x & 31) == 0) r = wait_or_abort(bar, parity, abort_flag) ? 1 : 0;
-  return __shfl_sync(0xffffffffu, r, 0) != 0;
 }
 
 }  // namespace
@@ -866,167 +905,263 @@ namespace hodlr {
 // Y(I_b, :) = D_b^{-1} U_big(I_b, :) for every leaf b of m = 128 rows, with
 // tcgen05.mma kind::tf32 (FP32 operands read as TF32, FP32 accumulation):
 // M = 128 rows of the leaf, N = kLaNC columns of U per MMA chain, K = 128.
-//   A = D_b^{-1}: written by the leaf inverse in the K-major core-matrix
+//   A = the leaf's Gauss-Jordan tableau T (D_b^{-1} with permuted rows and
+//       columns), written by the leaf inverse in the K-major core-matrix
 //       layout (8-row x 16-byte cores, LBO = 128 B along K, SBO = 4096 B
 //       between 8-row groups), 64 KB per leaf, staged by one bulk copy;
-//   B = U(I_b, cols)^T: U is column-major, i.e. K-contiguous per column; each
-//       thread converts 4 consecutive FP64 rows of one column to FP32 and
-//       stores one 16-byte core row;
-//   D (TMEM, FP32) -> BF16 into a [column][row] tile, stored by TMA.
+//   B(c, :) = U(p_c, cols): FP64 tiles of U staged by TMA, gathered by p and
+//       converted in shared memory into the 128-byte swizzled K-major layout;
+//   D (TMEM, FP32) -> BF16, row r to row step(r) of a [column][row] tile,
+//       stored by TMA.
 // FP64 -> FP32 for the TF32 operand: the FP64 sign and exponent are rebiased
 // and the top 23 significand bits kept (truncation; the MMA uses the top 10),
 // on the integer pipe; magnitudes below 2^-126 become zero.
 namespace {
 
-constexpr int kLaNC = 64;  // columns of U per MMA chain
+constexpr int kLaNC = 32;       // columns of U per chunk (N of the MMA)
+constexpr int kLaStages = 3;    // FP64 U tiles in flight
+constexpr int kLaThreads = 320; // 4 converter warps, 4 epilogue warps, producer, MMA issuer
 
 struct LeafTcSmem {
-  static constexpr uint32_t kABytes = 128 * 128 * 4;
-  static constexpr uint32_t kBBytes = kLaNC * 128 * 4;
-  static constexpr uint32_t kYBytes = 128 * kLaNC * 2;
-  static constexpr uint32_t kBarOff = kABytes + kBBytes + kYBytes;
-  static constexpr uint32_t kBytes = kBarOff + 64 + 128;
+  static constexpr uint32_t kABytes = 128 * 128 * 4;      // D_b^{-1} tableau, K-major cores
+  static constexpr uint32_t kUBytes = 128 * kLaNC * 8;    // FP64 U tile [column][row]
+  static constexpr uint32_t kBBytes = kLaNC * 128 * 4;    // TF32 operand, K-major, 128-byte swizzle
+  static constexpr uint32_t kYBytes = 128 * kLaNC * 2;    // BF16 Y tile [column][row]
+  static constexpr uint32_t kUOff = kABytes;
+  static constexpr uint32_t kBOff = kUOff + kLaStages * kUBytes;
+  static constexpr uint32_t kYOff = kBOff + 2 * kBBytes;
+  static constexpr uint32_t kBarOff = kYOff + 2 * kYBytes;
+  static constexpr uint32_t kBytes = kBarOff + 256 + 1024;  // barriers, TMEM slot, flag; + alignment slack
+  static_assert(kBOff % 1024 == 0, "swizzled operand atoms are 1024-byte aligned");
+  static_assert(8 * (2 * kLaStages + 11) + 8 <= 256, "barrier area");
+  static_assert(kBytes <= 227 * 1024, "shared memory per CTA");
 };
+
+// FP64 tensor map over the column-major N x cols matrix U (ld elements):
+// box = 128 rows x kLaNC columns, no swizzle ([column][row] in shared memory).
+bool make_map_u64(CUtensorMap* map, const double* base, int64_t rows, int64_t cols, int64_t ld) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 8};
+  cuuint32_t box[2] = {128, (cuuint32_t)kLaNC};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 
 }  // namespace
 
-__global__ void __launch_bounds__(256, 2) leaf_apply_tc_kernel(const __grid_constant__ CUtensorMap mapY,
-                                                               int64_t nleaf, int rL,
-                                                               const float* __restrict__ Acore,
-                                                               const int* __restrict__ perm,
-                                                               const double* __restrict__ U, int64_t ldu,
-                                                               DevStatus* st) {
+// Persistent, warp-specialized (320 threads, one CTA per SM); every role walks
+// the same sequence of (leaf, chunk) pairs:
+//   warp 8, lane 0 (producer): TMA loads of the FP64 U tiles (128 rows x 32
+//     columns) into a ring of kLaStages stages, running ahead across leaves;
+//   warps 0-3 (converters): U tile -> B operand of the chunk (double
+//     buffered): thread (warp w, lane q) forms rows 4q..4q+3 of B for columns
+//     w, w + 4, ...: B(c, j) = U(p_c, j) read from the staged tile, FP64 ->
+//     FP32 on the integer pipe, one 16-byte store in the 128-byte swizzled
+//     K-major layout (the 8 lanes of one 128-byte row hit 8 distinct chunks);
+//   warp 9, lane 0 (MMA issuer): per leaf the bulk copy of A (and an L2
+//     prefetch of the CTA's next A), per chunk 16 tcgen05.mma kind::tf32 (K =
+//     8 each) into one of two TMEM accumulators (M = 128, N = 32);
+//   warps 4-7 (epilogue, TMEM lane quarter = warp % 4): accumulator -> BF16
+//     rows scattered by step into a [column][row] tile (double buffered),
+//     stored by TMA.
+// Hand-offs are mbarriers; every wait is bounded and also gives up when
+// another thread has raised the CTA's abort flag; copies and MMAs in flight
+// are let land (bounded) before the TMEM is freed and the CTA exits.
+__global__ void __launch_bounds__(kLaThreads, 1) leaf_apply_tc_kernel(const __grid_constant__ CUtensorMap mapY,
+                                                                      const __grid_constant__ CUtensorMap mapU,
+                                                                      int64_t nleaf, int rL,
+                                                                      const float* __restrict__ Acore,
+                                                                      const int* __restrict__ perm,
+                                                                      DevStatus* st) {
   using S = LeafTcSmem;
-  constexpr uint32_t kSBO = 4096;  // 32 cores along K x 128 B
-  constexpr uint32_t kTmemCols = kLaNC;
+  constexpr uint32_t kSBO = 4096;  // A: 32 cores along K x 128 B per 8-row group
+  constexpr uint32_t kTmemCols = 2 * kLaNC;
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
-  uint8_t* sB = sA + S::kABytes;
-  __nv_bfloat16* sY = reinterpret_cast<__nv_bfloat16*>(sB + S::kBBytes);
-  uint64_t* bar_a = reinterpret_cast<uint64_t*>(smem + S::kBarOff);
-  uint64_t* bar_mma = bar_a + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_a + 2);
+  const double* sU = reinterpret_cast<const double*>(smem + S::kUOff);
+  uint8_t* sB = smem + S::kBOff;
+  __nv_bfloat16* sY = reinterpret_cast<__nv_bfloat16*>(smem + S::kYOff);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::kBarOff);
+  uint64_t* u_full = bars;                        // [stages] TMA transaction count
+  uint64_t* u_empty = bars + kLaStages;           // [stages] 128 converter threads
+  uint64_t* b_full = bars + 2 * kLaStages;        // [2]      128 converter threads
+  uint64_t* b_empty = b_full + 2;                 // [2]      MMA commit
+  uint64_t* acc_full = b_full + 4;                // [2]      MMA commit
+  uint64_t* acc_empty = b_full + 6;               // [2]      128 epilogue threads
+  uint64_t* a_full = b_full + 8;                  //          TMA transaction count
+  uint64_t* a_empty = b_full + 9;                 //          MMA commit (the leaf's MMAs are done)
+  uint64_t* drain = b_full + 10;                  //          MMA commit at exit
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(b_full + 11);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  __shared__ int s_p[128];  // p_c: column c of A = T is column p_c of D_b^{-1}
 
   if (tid == 0) {
-    tc::mbar_init(bar_a, 1);
-    tc::mbar_init(bar_mma, 1);
+    for (int s = 0; s < kLaStages; ++s) {
+      tc::mbar_init(&u_full[s], 1);
+      tc::mbar_init(&u_empty[s], 128);
+    }
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&b_full[i], 128);
+      tc::mbar_init(&b_empty[i], 1);
+      tc::mbar_init(&acc_full[i], 1);
+      tc::mbar_init(&acc_empty[i], 128);
+    }
+    tc::mbar_init(a_full, 1);
+    tc::mbar_init(a_empty, 1);
+    tc::mbar_init(drain, 1);
+    *abort_flag = 0;
     tc::fence_mbar_init();
     tc::prefetch_tmap(&mapY);
+    tc::prefetch_tmap(&mapU);
   }
-  if (warp == 0) tc::tmem_alloc(tmem_slot, kTmemCols);
+  if (warp == 9) tc::tmem_alloc(tmem_slot, kTmemCols);
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  const int nch = rL / kLaNC;
 
-  const int nchunks = rL / kLaNC + (rL % kLaNC ? 1 : 0);
-  bool ok = true;
-  uint32_t ph_a = 0, ph_mma = 0;
-  bool a_pending = false, mma_pending = false;  // thread 0's view
-  for (int64_t b = blockIdx.x; b < nleaf && ok; b += gridDim.x) {
-    const int64_t row0 = b * 128;
-    if (tid == 0) {
-      tc::mbar_expect_tx(bar_a, S::kABytes);
-      bulk_load_1d(sA, Acore + (size_t)b * 128 * 128, S::kABytes, bar_a);
-      a_pending = true;
-    }
-    // A = T with D_b^{-1}(step(r), p_c) = T(r, c): B takes U's rows in the
-    // order p (row c of B = row p_c of U) and row r of the product is row
-    // step(r) of Y
-    __syncthreads();  // the previous leaf's s_p / my_out readers are done
-    if (tid < 128) s_p[tid] = perm[(size_t)b * 128 + tid];
-    const int my_out = perm[(size_t)nleaf * 128 + (size_t)b * 128 + ((warp & 3) * 32 + lane)];
-    __syncthreads();
-    for (int ch = 0; ch < nchunks && ok; ++ch) {
-      const int col0 = ch * kLaNC;
-      const int nc = (rL - col0) < kLaNC ? (rL - col0) : kLaNC;  // multiple of 32
-      // B: nc columns x 128 rows; item = (8-column group, k quad, column in group)
-      {
-        constexpr int kItems = kLaNC * 32;  // 16-byte core rows of a full chunk
-        constexpr int kPer = kItems / 256;
-        double2 v0[kPer], v1[kPer];
-#pragma unroll
-        for (int u = 0; u < kPer; ++u) {
-          const int it = tid + u * 256;
-          const int jl = it & 7, kq = (it >> 3) & 31, jg = it >> 8;
-          const int j = jg * 8 + jl;
-          if (j < nc) {
-            const double* src = U + (int64_t)(col0 + j) * ldu + row0;
-            v0[u] = make_double2(src[s_p[kq * 4]], src[s_p[kq * 4 + 1]]);
-            v1[u] = make_double2(src[s_p[kq * 4 + 2]], src[s_p[kq * 4 + 3]]);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kPer; ++u) {
-          const int it = tid + u * 256;
-          const int jl = it & 7, kq = (it >> 3) & 31, jg = it >> 8;
-          if (jg * 8 + jl < nc)
-            *reinterpret_cast<uint4*>(sB + jg * kSBO + kq * 128 + jl * 16) =
-                make_uint4(f64_to_f32_trunc_bits(v0[u].x), f64_to_f32_trunc_bits(v0[u].y),
-                           f64_to_f32_trunc_bits(v1[u].x), f64_to_f32_trunc_bits(v1[u].y));
+  if (warp == 8) {
+    // ---------------------------------------------------------------- producer
+    if (lane == 0) {
+      uint32_t g = 0;  // chunks issued
+      bool ok = true;
+      for (int64_t b = blockIdx.x; b < nleaf && ok; b += gridDim.x) {
+        for (int ch = 0; ch < nch; ++ch, ++g) {
+          const int s = (int)(g % kLaStages);
+          if (g >= (uint32_t)kLaStages &&
+              !(ok = wait_or_abort(&u_empty[s], ((g / kLaStages) - 1) & 1, abort_flag)))
+            break;
+          tc::mbar_expect_tx(&u_full[s], S::kUBytes);
+          tc::tma_load_2d(smem + S::kUOff + s * S::kUBytes, &mapU, (int32_t)(b * 128), ch * kLaNC, &u_full[s]);
         }
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      tc::tc_fence_before();
-      if (ch == 0) {
-        ok = __syncthreads_and(tc::mbar_wait(bar_a, ph_a)) != 0;
-        if (!ok) break;
-        ph_a ^= 1;
+      // let the last copies land before the CTA can exit (bounded)
+      for (uint32_t q = 0; q < (uint32_t)kLaStages && q < g; ++q) {
+        const uint32_t u = g - 1 - q;
+        tc::mbar_wait(&u_full[u % kLaStages], (u / kLaStages) & 1);
+      }
+    }
+  } else if (warp == 9) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_tf32_f32(128, kLaNC);
+      const uint32_t a0 = tc::smem_u32(sA);
+      uint32_t g = 0, i = 0;
+      bool ok = true, issued = false, a_pending = false;
+      for (int64_t b = blockIdx.x; b < nleaf && ok; b += gridDim.x, ++i) {
+        // A of this leaf once the previous leaf's MMAs have read the buffer
+        if (i >= 1 && !(ok = wait_or_abort(a_empty, (i - 1) & 1, abort_flag))) break;
+        tc::mbar_expect_tx(a_full, S::kABytes);
+        bulk_load_1d(sA, Acore + (size_t)b * 128 * 128, S::kABytes, a_full);
+        a_pending = true;
+        if (b + gridDim.x < nleaf) bulk_prefetch_l2(Acore + (size_t)(b + gridDim.x) * 128 * 128, S::kABytes);
+        if (!(ok = wait_or_abort(a_full, i & 1, abort_flag))) break;
         a_pending = false;
-      } else {
-        __syncthreads();
-      }
-      tc::tc_fence_after();
-      if (tid == 0) {
-        const uint32_t idesc = tc::idesc_tf32_f32(128, nc);
-        const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+        tc::tc_fence_after();
+        for (int ch = 0; ch < nch; ++ch, ++g) {
+          const uint32_t bb = g & 1;
+          if (!(ok = wait_or_abort(&b_full[bb], (g >> 1) & 1, abort_flag))) break;
+          if (g >= 2 && !(ok = wait_or_abort(&acc_empty[bb], ((g >> 1) - 1) & 1, abort_flag))) break;
+          tc::tc_fence_after();
+          const uint32_t b0 = tc::smem_u32(sB + bb * S::kBBytes);
 #pragma unroll
-        for (int ks = 0; ks < 16; ++ks)  // K = 8 per MMA: two cores along K
-          tc::mma_tf32(tmem, tc::desc_noswz_kmajor(a0 + ks * 256, 128, kSBO),
-                   tc::desc_noswz_kmajor(b0 + ks * 256, 128, kSBO), idesc, ks != 0);
-        tc::mma_commit(bar_mma);
-        mma_pending = true;
-        bulk_wait_read0();  // the previous chunk's store has left sY
+          for (int ks = 0; ks < 16; ++ks)  // K = 8 per MMA; B: 4 swizzle atoms of 32 K, 32 bytes per MMA
+            tc::mma_tf32(tmem + bb * kLaNC, tc::desc_noswz_kmajor(a0 + ks * 256, 128, kSBO),
+                         tc::desc_sw128_kmajor(b0 + (ks >> 2) * 4096) + 2 * (ks & 3), idesc, ks != 0);
+          issued = true;
+          tc::mma_commit(&b_empty[bb]);
+          tc::mma_commit(&acc_full[bb]);
+        }
+        if (!ok) break;
+        tc::mma_commit(a_empty);
       }
-      ok = __syncthreads_and(tc::mbar_wait(bar_mma, ph_mma)) != 0;
-      if (!ok) break;
-      ph_mma ^= 1;
-      mma_pending = false;
-      tc::tc_fence_after();
-      // warps w and w+4 share TMEM lanes 32 (w % 4) .. +31 and split the columns
-      for (int cb = (warp >> 2) * 32; cb < nc; cb += 64) {
-        float v[32];
-        tc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + cb, v);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) sY[(cb + j) * 128 + my_out] = __float2bfloat16_rn(v[j]);
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      tc::tc_fence_before();
-      __syncthreads();
-      tc::tc_fence_after();
-      if (tid == 0) {
-        for (int bx = 0; bx < nc / kFuBox; ++bx)
-          tma_store_2d(&mapY, sY + bx * 128 * kFuBox, (int32_t)row0, col0 + bx * kFuBox);
-        bulk_commit();
+      if (a_pending) tc::mbar_wait(a_full, i & 1);  // the copy into sA lands before the CTA exits
+      if (issued) {                                 // every MMA issued has finished (bounded)
+        tc::mma_commit(drain);
+        tc::mbar_wait(drain, 0);
       }
     }
-  }
-  if (tid == 0) {
-    if (a_pending) tc::mbar_wait(bar_a, ph_a);
-    if (mma_pending) tc::mbar_wait(bar_mma, ph_mma);
-    bulk_wait0();
-    if (!ok) set_status(st, HODLR_ERR_TIMEOUT, 0, 3);
+  } else if (warp < 4) {
+    // ---------------------------------------------------------------- converters
+    // lane q forms rows 4q..4q+3 of B: swizzle atom q / 8, 16-byte chunk q % 8
+    const int at = lane >> 3, cq = lane & 7;
+    uint32_t g = 0;
+    bool ok = true;
+    for (int64_t b = blockIdx.x; b < nleaf && ok; b += gridDim.x) {
+      const int4 pq = *reinterpret_cast<const int4*>(perm + (size_t)b * 128 + 4 * lane);  // p_{4q} .. p_{4q+3}
+      for (int ch = 0; ch < nch; ++ch, ++g) {
+        const int s = (int)(g % kLaStages);
+        const uint32_t bb = g & 1;
+        if (!(ok = warp_wait(&u_full[s], (g / kLaStages) & 1, abort_flag))) break;
+        if (g >= 2 && !(ok = warp_wait(&b_empty[bb], ((g >> 1) - 1) & 1, abort_flag))) break;
+        const double* u = sU + (size_t)s * 128 * kLaNC;
+        uint8_t* bt = sB + bb * S::kBBytes;
+#pragma unroll
+        for (int jj = 0; jj < kLaNC / 4; ++jj) {
+          const int j = warp + 4 * jj;
+          const double* uc = u + j * 128;
+          *reinterpret_cast<uint4*>(bt + at * 4096 + (j >> 3) * 1024 + (j & 7) * 128 + ((cq ^ (j & 7)) << 4)) =
+              make_uint4(f64_to_f32_trunc_bits(uc[pq.x]), f64_to_f32_trunc_bits(uc[pq.y]),
+                         f64_to_f32_trunc_bits(uc[pq.z]), f64_to_f32_trunc_bits(uc[pq.w]));
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc::mbar_arrive(&b_full[bb]);
+        tc::mbar_arrive(&u_empty[s]);
+      }
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    const int q4 = warp & 3;
+    const int row = q4 * 32 + lane;  // row r of the leaf product = TMEM lane
+    const bool storer = warp == 4 && lane == 0;
+    uint32_t g = 0;
+    bool ok = true;
+    for (int64_t b = blockIdx.x; b < nleaf && ok; b += gridDim.x) {
+      const int my_out = perm[(size_t)nleaf * 128 + (size_t)b * 128 + row];  // step(r): row of Y
+      for (int ch = 0; ch < nch; ++ch, ++g) {
+        const uint32_t ab = g & 1;
+        const bool w = warp_wait(&acc_full[ab], (g >> 1) & 1, abort_flag);
+        // uniform over the epilogue warps; also orders the storer's read-wait
+        // for this Y buffer before the writes below
+        if (!(ok = named_bar_and(1, 128, w))) break;
+        tc::tc_fence_after();
+        float v[32];
+        tc::tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + ab * kLaNC, v);
+        tc::tc_fence_before();
+        tc::mbar_arrive(&acc_empty[ab]);
+        __nv_bfloat16* yt = sY + (size_t)ab * 128 * kLaNC;
+#pragma unroll
+        for (int j = 0; j < kLaNC; ++j) yt[j * 128 + my_out] = __float2bfloat16_rn(v[j]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        named_bar_sync(1, 128);
+        if (storer) {
+          tma_store_2d(&mapY, yt, (int32_t)(b * 128), ch * kLaNC);
+          bulk_commit();
+          bulk_wait_read1();  // the previous chunk's store has read the other buffer
+        }
+      }
+    }
+    if (storer) bulk_wait0();
   }
   tc::tc_fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+  if (tid == 0 && *abort_flag) set_status(st, HODLR_ERR_TIMEOUT, 0, 3);
+  if (warp == 9) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
 bool leaf_apply_tc_supported(const Factor& F) {
-  return g_use_tc && F.prec == HODLR_PREC_BF16 && F.d.m == 128 && (F.d.r * F.d.L) % 32 == 0 &&
+  return g_use_tc && F.prec == HODLR_PREC_BF16 && F.d.m == 128 && (F.d.r * F.d.L) % kLaNC == 0 &&
          encode_fn() != nullptr;
 }
 
@@ -1037,16 +1172,16 @@ cudaError_t launch_leaf_apply_tc(const Factor& F, const double* U, int64_t ldu, 
   const int64_t nleaf = (int64_t)1 << F.d.L;
   note_work(8.0 * (double)N * rL + 2.0 * (double)N * rL + 4.0 * (double)nleaf * 128 * 128,
             2.0 * (double)N * 128 * rL);
-  CUtensorMap mY;
+  CUtensorMap mY, mU;
   if (!make_map_plain(&mY, F.Y, N, rL, N)) return cudaErrorInvalidValue;
+  if (!make_map_u64(&mU, U, N, rL, ldu)) return cudaErrorInvalidValue;
   using S = LeafTcSmem;
-  const int per_sm = (int)((227 * 1024) / (S::kBytes + 1024));
-  int64_t grid = (int64_t)sm_count() * (per_sm < 1 ? 1 : per_sm);
+  int64_t grid = sm_count();  // one CTA per SM
   if (grid > nleaf) grid = nleaf;
   cudaFuncSetAttribute(leaf_apply_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kBytes);
   {
-    leaf_apply_tc_kernel<<<(unsigned)grid, 256, S::kBytes, s>>>(mY, nleaf, rL, reinterpret_cast<const float*>(F.P),
-                                                                 F.perm, U, ldu, F.status);
+    leaf_apply_tc_kernel<<<(unsigned)grid, kLaThreads, S::kBytes, s>>>(
+        mY, mU, nleaf, rL, reinterpret_cast<const float*>(F.P), F.perm, F.status);
     note_launches(1);
   }
   return cudaGetLastError();

@@ -274,6 +274,8 @@ def bie_hodlr(shape: HodlrShape, device="cpu", seed=2, stats=None):
     shape.validate()
     N, m = shape.N, shape.m
     x, nrm, w, kappa = star_curve(N, device=device, dtype=torch.float64)
+    n32, w32 = nrm.float(), w.float()
+    band = max(256, N // 128)
     diag = (-0.5 - w * kappa / (4 * math.pi))
 
     def leaf_fn(b0, b1):
@@ -284,11 +286,27 @@ def bie_hodlr(shape: HodlrShape, device="cpu", seed=2, stats=None):
         return blk
 
     def entries(rows, cols):
-        # FP64 geometry: for neighbouring points n(y).(x - y) is second order
-        # in the spacing while x - y is first order, so FP32 coordinates lose
-        # most of its digits (the whole entry at N = 2^16); the compression
-        # then runs on the FP32-rounded entries.
-        return bie_block(x, nrm, w, rows, cols).float()
+        # For nearby points n(y).(x - y) is second order in the distance while
+        # x - y is first order. Entries whose curve-order distance is below
+        # `band` come from the FP64 geometry; the others from x - y formed in
+        # FP64 and the rest in FP32 (error relative to the block's largest
+        # entry about 1.2e-7 / (kappa |x - y|), <= 1.1e-6 beyond the band at
+        # N = 2^16; from FP32 coordinates it would be ~1.6e-7 / (kappa |x - y|^2),
+        # the whole entry for neighbours). rows and cols are contiguous,
+        # disjoint index ranges per batch entry.
+        b = cols.shape[-1]
+        if 2 * band >= b:
+            return bie_block(x, nrm, w, rows, cols).float()
+        dx = (x[rows, 0][..., :, None] - x[cols, 0][..., None, :]).float()
+        dy = (x[rows, 1][..., :, None] - x[cols, 1][..., None, :]).float()
+        nd = dx * n32[cols, 0][..., None, :] + dy * n32[cols, 1][..., None, :]
+        out = nd / ((2 * math.pi) * (dx * dx + dy * dy)) * w32[cols][..., None, :]
+        lo, hi = rows[:, :1], rows[:, -1:]
+        dist = torch.minimum(torch.remainder(cols - hi, N), torch.remainder(lo - cols, N))
+        e, j = (dist < band).nonzero(as_tuple=True)
+        if e.numel():
+            out[e, :, j] = bie_block(x, nrm, w, rows[e], cols[e, j][:, None])[..., 0].float()
+        return out
 
     return _assemble(shape, leaf_fn, entries, seed, device, symmetric=False, stats=stats)
 
@@ -304,6 +322,7 @@ def kernel_hodlr(shape: HodlrShape, dim: int, kind: str, scale: float, nugget: f
     g.manual_seed(seed)
     pts = torch.rand(N, dim, generator=g, device=device, dtype=torch.float64)
     pts = pts[kd_order(pts, m)].contiguous()
+    p32 = pts.float()
 
     def kfun(d2):
         if kind == "gaussian":
@@ -321,9 +340,8 @@ def kernel_hodlr(shape: HodlrShape, dim: int, kind: str, scale: float, nugget: f
         return K
 
     def entries(rows, cols):
-        # squared distances from the FP64 points, the kernel in FP32
-        d2 = ((pts[rows][:, :, None, :] - pts[cols][:, None, :, :]) ** 2).sum(-1)
-        return kfun(d2.float())
+        d2 = ((p32[rows][:, :, None, :] - p32[cols][:, None, :, :]) ** 2).sum(-1)
+        return kfun(d2)
 
     D, U, V = _assemble(shape, leaf_fn, entries, seed, device, symmetric=True, stats=stats)
     return D, U, V, pts

@@ -8,18 +8,23 @@ experiments), at N = 4096:
 * every off-diagonal block's factors interpolate the dense block on their
   pivot rows and columns (the cross property, any pivot sequence);
 * given the GPU's pivots, the oracle's FP64 cross approximation produces the
-  same block approximation (the pivots are discrete choices made in FP32;
-  the rest of the computation is then fixed);
-* the first pivots are maxima of the oracle's residuals (within FP32 rounding);
-* the assembled HODLR matrix approximates the dense matrix as well as the
-  oracle's own cross approximation (its own pivots, FP64) does;
+  same steps (the pivots are discrete choices made in FP32; the rest of the
+  computation is then fixed) up to the first step whose FP64 residual at
+  the pivot is at the FP32 rounding level of the entries (below 1e-5 of the
+  block's largest entry): later GPU pivots are chosen among rounding noise,
+  where the FP64 residual can vanish;
+* the first pivots are maxima of the oracle's residual rows, within 1e-4 of
+  the block's largest entry (near-ties are decided in FP32);
+* every block's approximation error is within 1.5x that of the oracle's own
+  cross approximation (its own pivots, FP64; or 1e-5 of the block's largest
+  entry), and the assembled HODLR matrix's within 5%;
 * for a kernel matrix U = V (one cross per sibling pair).
-Tolerances: entries and residual updates are FP32 on the GPU. The steps
-whose pivot is at least 1e-4 of the first one agree with the FP64 oracle to
-2e-5 of the block's largest entry (an FP32 emulation of the same pivots on
-the CPU stays below 1e-5); the later steps work on residuals near the FP32
-rounding of the entries, where the skeleton is ill-conditioned and the same
-emulation differs by up to 7e-5, so the whole approximation is held to 2e-4.
+Tolerances (entries rounded to FP32, FP32 residual updates): the replayed
+steps agree with the FP64 oracle to 1e-4 of the block's largest entry, the
+cross property holds to 2e-5. An FP32 emulation of the algorithm on the CPU
+(BIE N = 4096, rank 16) gives 3.1e-5 for the first, pivots within 1.7e-5 of
+the residual maxima, a per-block error ratio of 1.0013 and an assembled
+error of 6.714e-5 against the oracle's 6.708e-5.
 """
 import math
 
@@ -32,9 +37,10 @@ from synth.kernels import bie_dense, kd_order
 
 pytestmark = pytest.mark.gpu
 
-TOL = 2e-5        # steps with pivots >= TAU |pivot_0|
-TOL_ALL = 2e-4    # every step
-TAU = 1e-4
+TOL = 2e-5        # cross property
+TOL_REP = 1e-4    # replayed steps
+NOISE = 1e-5      # FP64 residual at a pivot below NOISE x block max: replay ends
+PIVOT_GAP = 1e-4  # pivot |residual| below the residual row's maximum, x block max
 
 
 def _kernel_dense(pts, kind, scale, nugget):
@@ -100,22 +106,24 @@ def test_compress_against_dense_and_oracle(cuda_lib, kind):
             for k in live:   # the cross property
                 np.testing.assert_allclose(Ag[rows[k], :], M[rows[k], :], rtol=0, atol=TOL * bmax)
                 np.testing.assert_allclose(Ag[:, cls[k]], M[:, cls[k]], rtol=0, atol=TOL * bmax)
-            Uo, Vo, _, _ = cross_approximation(M, r, rows=rows, cols=cls)
-            np.testing.assert_allclose(Ag, Uo @ Vo.T, rtol=0, atol=TOL_ALL * bmax)
-            piv0 = abs(Uo[rows[0], 0]) if live else 0.0   # u_k(i_k) is the pivot of step k
-            kt = next((k for k in range(r) if k not in live or abs(Uo[rows[k], k]) < TAU * piv0), r)
+            with np.errstate(all="ignore"):   # replayed steps past the noise level may divide by zero
+                Uo, Vo, _, _ = cross_approximation(M, len(live), rows=rows[:len(live)], cols=cls[:len(live)])
+            kt = next((k for k in range(len(live))
+                       if not np.isfinite(Uo[rows[k], k]) or abs(Uo[rows[k], k]) < NOISE * bmax), len(live))
             np.testing.assert_allclose(Ug[:, :kt] @ Vg[:, :kt].T, Uo[:, :kt] @ Vo[:, :kt].T, rtol=0,
-                                       atol=TOL * bmax)
+                                       atol=TOL_REP * bmax)
             Ua, Va, _, _ = cross_approximation(M, r)
+            err_g = np.abs(Ag - M).max()
+            err_a = np.abs(Ua @ Va.T - M).max()
+            assert err_g <= 1.5 * max(err_a, NOISE * bmax), (c, a, err_g / bmax, err_a / bmax)
             Uown[a * n:(a + 1) * n, cols], Vown[be * n:(be + 1) * n, cols] = Ua, Va
             if sym:
                 Uown[be * n:(be + 1) * n, cols], Vown[a * n:(a + 1) * n, cols] = Va, Ua
-            for k in live[:8]:   # the first pivots are maxima of the residual rows
+            for k in live[:min(8, kt)]:   # the first pivots are maxima of the residual rows
                 rho = M[rows[k], :] - Uo[rows[k], :k] @ Vo[:, :k].T
                 cand = np.abs(rho)
                 cand[cls[:k]] = 0.0
-                if cand.max() > 1e-3 * bmax:
-                    assert abs(rho[cls[k]]) >= (1 - 1e-3) * cand.max()
+                assert (cand.max() - abs(rho[cls[k]])) / bmax <= PIVOT_GAP, (c, a, k)
     # the assembled approximation
     nA = np.linalg.norm(A)
     err = np.linalg.norm(assemble_dense(Dh, Uh, Vh, L) - A) / nA
