@@ -115,10 +115,6 @@ HODLR_API const char* hodlr_strerror(hodlr_status s);
  *   using V: the caller must keep V unchanged while the factor is in use. The
  *   workspace holds the factor and must stay allocated until hodlr_free.
  *   *out receives a host handle (owned by the caller, release with hodlr_free).
- *   In BF16 / FP32 / TF32 the copy of V into the panel type runs on a
- *   library-owned stream of the current device, forked from and joined back
- *   into `stream` by events within the call's own enqueued work, so the call
- *   stays ordered on `stream` alone.
  */
 HODLR_API hodlr_status hodlr_factor_workspace_size(const hodlr_desc* desc, hodlr_prec prec, size_t* bytes);
 HODLR_API hodlr_status hodlr_factor(const hodlr_desc* desc, const double* D, const double* U, const double* V,

@@ -316,40 +316,6 @@ hodlr_status matvec_core(const hodlr_desc& d, const double* D, const double* U, 
 
 bool valid_factor(const Factor* F) { return F != nullptr; }
 
-// Per-device auxiliary stream with fork / join events, for independent work
-// of one call that can overlap the main stream's (created on first use; a
-// device without one runs that work on the main stream).
-struct AuxStream {
-  cudaStream_t s = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
-  std::mutex use;  // held from the fork until the join is waited on (the events are shared)
-};
-constexpr int kMaxAuxDevices = 64;
-std::mutex g_aux_mu;
-AuxStream g_aux[kMaxAuxDevices];
-
-AuxStream* aux_stream() {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxAuxDevices) return nullptr;
-  std::lock_guard<std::mutex> g(g_aux_mu);
-  AuxStream& a = g_aux[dev];
-  if (!a.s) {
-    cudaStream_t st = nullptr;
-    cudaEvent_t f = nullptr, j = nullptr;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
-    if (cudaEventCreateWithFlags(&f, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&j, cudaEventDisableTiming) != cudaSuccess) {
-      cudaStreamDestroy(st);
-      if (f) cudaEventDestroy(f);
-      return nullptr;
-    }
-    a.s = st;
-    a.fork = f;
-    a.join = j;
-  }
-  return &a;
-}
-
 }  // namespace
 
 size_t factor_workspace_bytes(const hodlr_desc& d, hodlr_prec prec) { return factor_layout(d, prec).total; }
@@ -438,30 +404,6 @@ static hodlr_status factor_entry(const hodlr_desc* desc, const double* D, const 
   if (cudaMemsetAsync(F->status, 0, sizeof(DevStatus), s) != cudaSuccess) return fail(HODLR_ERR_CUDA);
   F->leaf_tc = leaf_apply_tc_supported(*F) && aligned(U, 16) && d.ldu % 2 == 0;
   const int rL = d.r * d.L;
-  // low precision: the copy of V in the panel type depends on nothing the leaf
-  // stage writes and nothing reads it before the level loop, so it runs on the
-  // auxiliary stream (forked after the status reset, joined before the levels)
-  // while the leaf inverse and leaf apply run on the main stream
-  AuxStream* ax = prec == HODLR_PREC_FP64 ? nullptr : aux_stream();
-  std::unique_lock<std::mutex> ax_lock;
-  cudaStream_t cs = s;
-  if (ax) {
-    ax_lock = std::unique_lock<std::mutex>(ax->use);
-    if (cudaEventRecord(ax->fork, s) != cudaSuccess || cudaStreamWaitEvent(ax->s, ax->fork, 0) != cudaSuccess)
-      return fail(HODLR_ERR_CUDA);
-    cs = ax->s;
-  }
-  if (prec == HODLR_PREC_FP32 || prec == HODLR_PREC_TF32) {
-    if (launch_copy_cols<float, double>(d.N, rL, V, d.ldv, static_cast<float*>(const_cast<void*>(F->Vp)), d.N, cs) !=
-        cudaSuccess)
-      return fail(HODLR_ERR_CUDA);
-  } else if (prec == HODLR_PREC_BF16) {
-    if (launch_copy_cols<__nv_bfloat16, double>(d.N, rL, V, d.ldv,
-                                                static_cast<__nv_bfloat16*>(const_cast<void*>(F->Vp)), d.N,
-                                                cs) != cudaSuccess)
-      return fail(HODLR_ERR_CUDA);
-  }
-  if (ax && cudaEventRecord(ax->join, ax->s) != cudaSuccess) return fail(HODLR_ERR_CUDA);
   if (launch_leaf_lu(*F, D, s) != cudaSuccess) return fail(HODLR_ERR_CUDA);
   hodlr_status r = HODLR_OK;
   if (prec == HODLR_PREC_FP64) {
@@ -469,19 +411,22 @@ static hodlr_status factor_entry(const hodlr_desc* desc, const double* D, const 
       return fail(HODLR_ERR_CUDA);
     r = factor_levels<double>(*F, s);
   } else if (prec == HODLR_PREC_FP32 || prec == HODLR_PREC_TF32) {
+    if (launch_copy_cols<float, double>(d.N, rL, V, d.ldv, static_cast<float*>(const_cast<void*>(F->Vp)), d.N, s) !=
+        cudaSuccess)
+      return fail(HODLR_ERR_CUDA);
     if (launch_leaf_solve<double, float>(*F, U, d.ldu, static_cast<float*>(F->Y), d.N, rL, 0, s) != cudaSuccess)
       return fail(HODLR_ERR_CUDA);
-    if (ax && cudaStreamWaitEvent(s, ax->join, 0) != cudaSuccess) return fail(HODLR_ERR_CUDA);
-    if (ax) ax_lock.unlock();
     r = factor_levels<float>(*F, s);
   } else {
+    if (launch_copy_cols<__nv_bfloat16, double>(d.N, rL, V, d.ldv,
+                                                static_cast<__nv_bfloat16*>(const_cast<void*>(F->Vp)), d.N,
+                                                s) != cudaSuccess)
+      return fail(HODLR_ERR_CUDA);
     const cudaError_t e =
         F->leaf_tc ? launch_leaf_apply_tc(*F, U, d.ldu, s)
                    : launch_leaf_solve<double, __nv_bfloat16>(*F, U, d.ldu, static_cast<__nv_bfloat16*>(F->Y), d.N,
                                                               rL, 0, s);
     if (e != cudaSuccess) return fail(HODLR_ERR_CUDA);
-    if (ax && cudaStreamWaitEvent(s, ax->join, 0) != cudaSuccess) return fail(HODLR_ERR_CUDA);
-    if (ax) ax_lock.unlock();
     r = factor_levels<__nv_bfloat16>(*F, s);
   }
   if (r != HODLR_OK) return fail(r);

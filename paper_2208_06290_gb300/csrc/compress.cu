@@ -54,6 +54,7 @@ __device__ __forceinline__ bool step_live(unsigned long long ck, int k, float to
 }
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr int kGeo = 6;  // BIE geometry per point: x, y, normal (2), weight, curvature
 constexpr size_t kWsAlign = 256;  // every workspace piece starts 256-byte aligned
 inline size_t ws_align(size_t x) { return (x + kWsAlign - 1) / kWsAlign * kWsAlign; }
 
@@ -84,8 +85,8 @@ __device__ __forceinline__ void star_point(int64_t i, int64_t N, double& x, doub
 __device__ __forceinline__ float kernel_entry(const Kern& K, const double* __restrict__ g, int64_t i, int64_t j) {
   if (K.kind == HODLR_KERNEL_BIE_STAR) {
     // double layer: n(y).(x - y) / (2 pi |x - y|^2) w_y   (x = point i, y = point j)
-    const double* gi = g + 5 * i;
-    const double* gj = g + 5 * j;
+    const double* gi = g + kGeo * i;
+    const double* gj = g + kGeo * j;
     const double dx = gi[0] - gj[0], dy = gi[1] - gj[1];
     return (float)((gj[2] * dx + gj[3] * dy) / (kTwoPi * (dx * dx + dy * dy)) * gj[4]);
   }
@@ -104,21 +105,24 @@ __global__ void geometry_kernel(Kern K, double* __restrict__ g) {
     if (K.kind == HODLR_KERNEL_BIE_STAR) {
       double x, y, nx, ny, w, kap;
       star_point(i, K.N, x, y, nx, ny, w, kap);
-      g[5 * i] = x;
-      g[5 * i + 1] = y;
-      g[5 * i + 2] = nx;
-      g[5 * i + 3] = ny;
-      g[5 * i + 4] = w;
+      double* gi = g + kGeo * i;
+      gi[0] = x;
+      gi[1] = y;
+      gi[2] = nx;
+      gi[3] = ny;
+      gi[4] = w;
+      gi[5] = kap;
     } else {
       for (int a = 0; a < K.dim; ++a) g[(size_t)K.dim * i + a] = K.pts[(size_t)K.dim * i + a];
     }
   }
 }
 
-// Leaf blocks D_b (column-major m x m), FP64: BIE: the kernel off the
-// diagonal and the smooth-quadrature diagonal -1/2 - w_i kappa_i / (4 pi);
-// kernel matrices: k(|x_i - x_j|) + nugget on the diagonal.
-__global__ void leaf_eval_kernel(Kern K, int m, double* __restrict__ D) {
+// Leaf blocks D_b (column-major m x m), FP64, from the FP64 geometry: BIE:
+// the kernel off the diagonal and the smooth-quadrature diagonal
+// -1/2 - w_i kappa_i / (4 pi); kernel matrices: k(|x_i - x_j|) + nugget on
+// the diagonal.
+__global__ void leaf_eval_kernel(Kern K, const double* __restrict__ g, int m, double* __restrict__ D) {
   const int64_t total = K.N * (int64_t)m;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = e / ((int64_t)m * m);
@@ -127,19 +131,18 @@ __global__ void leaf_eval_kernel(Kern K, int m, double* __restrict__ D) {
     const int64_t i = b * m + ii, j = b * m + jj;
     double v;
     if (K.kind == HODLR_KERNEL_BIE_STAR) {
-      double xi, yi, nxi, nyi, wi, ki, xj, yj, nxj, nyj, wj, kj;
-      star_point(i, K.N, xi, yi, nxi, nyi, wi, ki);
+      const double* gi = g + kGeo * i;
+      const double* gj = g + kGeo * j;
       if (i == j) {
-        v = -0.5 - wi * ki / (2.0 * kTwoPi);
+        v = -0.5 - gi[4] * gi[5] / (2.0 * kTwoPi);
       } else {
-        star_point(j, K.N, xj, yj, nxj, nyj, wj, kj);
-        const double dx = xi - xj, dy = yi - yj;
-        v = (nxj * dx + nyj * dy) / (kTwoPi * (dx * dx + dy * dy)) * wj;
+        const double dx = gi[0] - gj[0], dy = gi[1] - gj[1];
+        v = (gj[2] * dx + gj[3] * dy) / (kTwoPi * (dx * dx + dy * dy)) * gj[4];
       }
     } else {
       double d2 = 0.0;
       for (int a = 0; a < K.dim; ++a) {
-        const double d = K.pts[(size_t)K.dim * i + a] - K.pts[(size_t)K.dim * j + a];
+        const double d = g[(size_t)K.dim * i + a] - g[(size_t)K.dim * j + a];
         d2 += d * d;
       }
       if (K.kind == HODLR_KERNEL_GAUSSIAN) {
@@ -188,7 +191,7 @@ __device__ __forceinline__ void key_max(unsigned long long* keys, int64_t blk, u
 // Step (1): residual rows rho of every block's current pivot row, and the
 // pivot columns. Thread per column position g (node beta = g / n is the
 // column set of block beta ^ 1).
-__global__ void aca_row_kernel(Kern K, const double* __restrict__ g32, int64_t n, int c, int r, int k, int sym,
+__global__ void aca_row_kernel(Kern K, const double* __restrict__ geo, int64_t n, int c, int r, int k, int sym,
                                const float* __restrict__ U32, const float* __restrict__ V32, float* __restrict__ rho,
                                const int* __restrict__ prow, const int* __restrict__ pcol,
                                unsigned long long* __restrict__ colkey) {
@@ -206,7 +209,7 @@ __global__ void aca_row_kernel(Kern K, const double* __restrict__ g32, int64_t n
       const int ik = prow[(size_t)blk * r + k];  // local pivot row of this step; -1: block exhausted
       if (ik >= 0) {
         const int64_t gi = blk * n + ik;
-        x = kernel_entry(K, g32, gi, gg);
+        x = kernel_entry(K, geo, gi, gg);
         for (int l = 0; l < k; ++l) x -= U32[(size_t)l * N + gi] * V32[(size_t)l * N + gg];
         bool used = false;
         for (int l = 0; l < k; ++l) used |= pcol[(size_t)blk * r + l] == (int)jl;
@@ -222,7 +225,7 @@ __global__ void aca_row_kernel(Kern K, const double* __restrict__ g32, int64_t n
 // column at the pivot column) and the next pivot rows. Thread per position g:
 // as a row of node alpha = g / n (block alpha) it forms u_k(g); as a column
 // of node beta = g / n (block beta ^ 1) it forms v_k(g).
-__global__ void aca_col_kernel(Kern K, const double* __restrict__ g32, int64_t n, int c, int r, int k, int sym,
+__global__ void aca_col_kernel(Kern K, const double* __restrict__ geo, int64_t n, int c, int r, int k, int sym,
                                float* __restrict__ U32, float* __restrict__ V32, const float* __restrict__ rho,
                                int* __restrict__ prow, int* __restrict__ pcol,
                                const unsigned long long* __restrict__ colkey, unsigned long long* __restrict__ rowkey,
@@ -265,7 +268,7 @@ __global__ void aca_col_kernel(Kern K, const double* __restrict__ g32, int64_t n
       const int64_t il = gg - blk * n;
       float u = 0.f;
       if (live) {  // rows and columns of an off-diagonal block are disjoint
-        u = kernel_entry(K, g32, gg, gj);
+        u = kernel_entry(K, geo, gg, gj);
         for (int l = 0; l < k; ++l) u -= U32[(size_t)l * N + gg] * V32[(size_t)l * N + gj];
       }
       U32[(size_t)k * N + gg] = u;
@@ -313,7 +316,7 @@ size_t compress_workspace_bytes(const hodlr_desc& d) {
   const size_t N = (size_t)d.N, r = (size_t)d.r;
   size_t off = 0;
   auto take = [&](size_t bytes) { off += ws_align(bytes); };
-  take(N * 5 * sizeof(double));         // FP64 geometry / points
+  take(N * kGeo * sizeof(double));      // FP64 geometry / points
   take(2 * N * r * sizeof(float));      // FP32 working copies of one level's U, V columns
   take(N * sizeof(float));              // residual rows
   take(2 * r * ((size_t)1 << d.L) * sizeof(unsigned long long));  // column / row keys of every step
@@ -356,7 +359,7 @@ extern "C" hodlr_status hodlr_compress(const hodlr_desc* desc, const hodlr_kerne
   char* w = static_cast<char*>(workspace);
   size_t off = 0;
   auto take = [&](size_t bytes) { char* p = w + off; off += ws_align(bytes); return p; };
-  double* g32 = reinterpret_cast<double*>(take((size_t)N * 5 * sizeof(double)));
+  double* geo = reinterpret_cast<double*>(take((size_t)N * kGeo * sizeof(double)));
   float* U32 = reinterpret_cast<float*>(take((size_t)N * r * sizeof(float)));
   float* V32 = reinterpret_cast<float*>(take((size_t)N * r * sizeof(float)));
   float* rho = reinterpret_cast<float*>(take((size_t)N * sizeof(float)));
@@ -369,13 +372,13 @@ extern "C" hodlr_status hodlr_compress(const hodlr_desc* desc, const hodlr_kerne
   const int sym = kern->kind == HODLR_KERNEL_BIE_STAR ? 0 : 1;
   ProfScope prof_(KC_COMPRESS, s);
   note_work(8.0 * (double)N * d.m + 16.0 * (double)N * r * L, 2.0 * (double)N * r * r * L);
-  geometry_kernel<<<grid_n(N), 256, 0, s>>>(K, g32);
+  geometry_kernel<<<grid_n(N), 256, 0, s>>>(K, geo);
   note_launches(1);
   {
     const int64_t tot = N * (int64_t)d.m;
     int64_t gb = (tot + 255) / 256;
     if (gb > 152 * 32) gb = 152 * 32;
-    leaf_eval_kernel<<<(unsigned)gb, 256, 0, s>>>(K, d.m, D);
+    leaf_eval_kernel<<<(unsigned)gb, 256, 0, s>>>(K, geo, d.m, D);
     note_launches(1);
   }
   if (cudaGetLastError() != cudaSuccess) return HODLR_ERR_CUDA;
@@ -390,9 +393,9 @@ extern "C" hodlr_status hodlr_compress(const hodlr_desc* desc, const hodlr_kerne
         cudaMemsetAsync(piv, 0, 2 * (size_t)r * nblk * sizeof(int), s) != cudaSuccess)
       return HODLR_ERR_CUDA;
     for (int k = 0; k < r; ++k) {
-      aca_row_kernel<<<grid_n(N), 256, 0, s>>>(K, g32, n, c, r, k, sym, U32, V32, rho, prow, pcol,
+      aca_row_kernel<<<grid_n(N), 256, 0, s>>>(K, geo, n, c, r, k, sym, U32, V32, rho, prow, pcol,
                                                colkey + (size_t)k * nblk);
-      aca_col_kernel<<<grid_n(N), 256, 0, s>>>(K, g32, n, c, r, k, sym, U32, V32, rho, prow, pcol,
+      aca_col_kernel<<<grid_n(N), 256, 0, s>>>(K, geo, n, c, r, k, sym, U32, V32, rho, prow, pcol,
                                                colkey + (size_t)k * nblk, rowkey + (size_t)k * nblk, U, V, d.ldu,
                                                d.ldv, delta0);
       note_launches(2);

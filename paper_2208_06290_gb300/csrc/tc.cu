@@ -433,8 +433,17 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void*
                : "memory");
 }
 
+// Y(x.., y..) += tile, element-wise in the L2 (BF16 add, round to nearest).
+__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap* map, const void* src, int32_t x, int32_t y) {
+  asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(tc::smem_u32(src))
+               : "memory");
+}
+
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // 2-D BF16 tensor map without swizzle over the column-major N x cols matrix Y
@@ -457,31 +466,34 @@ bool make_map_plain(CUtensorMap* map, const void* base, int64_t rows, int64_t co
 // Pipelined, warp-specialized form of step 2 (320 threads, persistent over
 // 128-row tiles; every CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 // and chunks of kFuNC ancestor columns inside each tile in the same order):
-//   warp 4, lane 0 (producer): TMA / bulk copies into double-buffered stages:
-//     per tile the own block Y_own (128 x r) and the FP32 rows
-//     K~^{-1}(rows of alpha, :) (precomputed per node, see kf32_kernel); per
-//     chunk the parent's Rhs^T chunk and the old Y tile;
+//   warp 4, lane 0 (producer): TMA / bulk copies: per tile the own block
+//     Y_own (128 x r) and the FP32 rows K~^{-1}(rows of alpha, :)
+//     (precomputed per node, see kf32_kernel); per chunk the parent's Rhs^T
+//     chunk into a ring of stages;
 //   warps 0-3 (Z warps, thread per row): Y_own and K~^{-1}(alpha rows, :)^T
 //     into BF16 K-major operands; after the Z product, Z from TMEM rounded to
 //     BF16 into the A operand;
 //   warp 5, lane 0 (MMA issuer): per tile the Z product (K = r) into TMEM
 //     columns 128.., per chunk one tcgen05.mma chain (K = 2r) into one of two
 //     TMEM accumulators;
-//   warps 6-9 (epilogue, TMEM lane quarter = warp % 4): accumulator subtracted
-//     from the staged old Y tile, which one thread stores by TMA; the stage is
-//     handed back to the producer once the store has read it.
+//   warps 6-9 (epilogue, TMEM lane quarter = warp % 4): the accumulator,
+//     negated and rounded to BF16, into one of two [column][row] tiles, which
+//     one thread adds to Y by a TMA reduction (cp.reduce.async.bulk.tensor
+//     .add: the L2 forms Y + (-Z Rhs) and rounds it to BF16), so the old Y
+//     never passes through the SM.
 // Hand-offs are mbarriers (full / empty pairs). Every wait is bounded and also
 // gives up when another thread has raised the CTA's abort flag; on the way out
 // thread 0 of each role lets its own copies and MMAs land (bounded) before the
 // TMEM is freed.
 namespace {
 
-// Rhs^T / old-Y stages and A (Z) buffers. Two stages and one A buffer keep
-// r = 32 at two CTAs per SM (99 KB of shared memory each), which measured
-// faster than four stages and a double-buffered A at one CTA per SM.
-template <int RK> constexpr int fu_stages() { return 2; }
+// Rhs^T stages, Z (A operand) and output buffers: four stages, one A buffer,
+// one own-block buffer and two output tiles keep r = 32 at two CTAs per SM
+// (109 KB of shared memory each).
+template <int RK> constexpr int fu_stages() { return 4; }
 template <int RK> constexpr int fu_abufs() { return 1; }
-template <int RK> constexpr int fu_obufs() { return RK == 32 ? 2 : 1; }  // own-block / K~ rows buffers
+template <int RK> constexpr int fu_obufs() { return 1; }  // own-block / K~ rows buffers
+constexpr int kFuOut = 2;                                  // output tiles (TMA reductions in flight)
 constexpr int kFuThreads = 320;  // 10 warps
 
 template <int RK>
@@ -492,7 +504,7 @@ struct FusedSmem {
   static constexpr uint32_t kKfBytes = RK * kKLd * 4;
   static constexpr uint32_t kABytes = 128 * K2 * 2;       // Z, K-major cores
   static constexpr uint32_t kBBytes = kFuNC * K2 * 2;     // Rhs^T chunk
-  static constexpr uint32_t kYBytes = 128 * kFuNC * 2;    // old / new Y tile [j][m]
+  static constexpr uint32_t kYBytes = 128 * kFuNC * 2;    // output tile -Z Rhs [j][m]
   static constexpr int NS = fu_stages<RK>();
   static constexpr int NA = fu_abufs<RK>();
   static constexpr int NO = fu_obufs<RK>();
@@ -505,9 +517,9 @@ struct FusedSmem {
   static constexpr uint32_t kAOff = kKbOff + kKbBytes;
   static constexpr uint32_t kBOff = kAOff + NA * kABytes;
   static constexpr uint32_t kYOff = kBOff + NS * kBBytes;
-  static constexpr uint32_t kBarOff = kYOff + NS * kYBytes;
+  static constexpr uint32_t kBarOff = kYOff + kFuOut * kYBytes;
   static constexpr uint32_t kBytes = kBarOff + 256 + 128;  // barriers, TMEM slot, flag, + alignment slack
-  static_assert(8 * (14 + 3 * NS) + 16 <= 256, "barrier area");
+  static_assert(8 * (14 + 2 * NS) + 16 <= 256, "barrier area");
   static_assert(kBytes <= 227 * 1024, "shared memory per CTA");
 };
 
@@ -552,7 +564,7 @@ __global__ void __launch_bounds__(kFuThreads, RK == 32 ? 2 : 1) update_coupled_t
   uint8_t* sKb = smem + S::kKbOff;
   uint8_t* sA = smem + S::kAOff;                                               // [NA]
   uint8_t* sB = smem + S::kBOff;                                               // [stages]
-  __nv_bfloat16* sY = reinterpret_cast<__nv_bfloat16*>(smem + S::kYOff);      // [stages][kFuNC][128]
+  __nv_bfloat16* sY = reinterpret_cast<__nv_bfloat16*>(smem + S::kYOff);      // [kFuOut][kFuNC][128]
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::kBarOff);
   uint64_t* own_full = bars;                        // [2]
   uint64_t* own_empty = bars + 2;                   // [2]   count 128 (Z threads)
@@ -564,9 +576,8 @@ __global__ void __launch_bounds__(kFuThreads, RK == 32 ? 2 : 1) update_coupled_t
   uint64_t* z_done = bars + 13;                     //       MMA commit of the Z product
   uint64_t* ld_full = bars + 14;                    // [stages]
   uint64_t* b_empty = bars + 14 + S::NS;        // [stages] MMA commit
-  uint64_t* y_empty = bars + 14 + 2 * S::NS;    // [stages] epilogue storer
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 14 + 3 * S::NS);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 15 + 3 * S::NS);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 14 + 2 * S::NS);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 15 + 2 * S::NS);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
@@ -583,7 +594,6 @@ __global__ void __launch_bounds__(kFuThreads, RK == 32 ? 2 : 1) update_coupled_t
     for (int i = 0; i < S::NS; ++i) {
       tc::mbar_init(&ld_full[i], 1);
       tc::mbar_init(&b_empty[i], 1);
-      tc::mbar_init(&y_empty[i], 1);
     }
     *abort_flag = 0;
     tc::fence_mbar_init();
@@ -625,18 +635,11 @@ __global__ void __launch_bounds__(kFuThreads, RK == 32 ? 2 : 1) update_coupled_t
         const int col0 = ch * kFuNC;
         const int nc = (anc - col0) < kFuNC ? (anc - col0) : kFuNC;
         const int s = g % S::NS;
-        if (g >= (uint32_t)S::NS) {
-          const uint32_t ph = ((g / S::NS) - 1) & 1;
-          if (!(ok = warp_wait(&b_empty[s], ph, abort_flag))) break;
-          if (!(ok = warp_wait(&y_empty[s], ph, abort_flag))) break;
-        }
+        if (g >= (uint32_t)S::NS && !(ok = warp_wait(&b_empty[s], ((g / S::NS) - 1) & 1, abort_flag))) break;
         if (lane == 0) {
-          tc::mbar_expect_tx(&ld_full[s], (uint32_t)nc * K2 * 2 + (uint32_t)nc * 128 * 2);
+          tc::mbar_expect_tx(&ld_full[s], (uint32_t)nc * K2 * 2);
           bulk_load_1d(sB + (size_t)s * S::kBBytes, rhs_j + (size_t)col0 * K2 * 2, (uint32_t)nc * K2 * 2,
                        &ld_full[s]);
-          for (int b = 0; b < nc / kFuBox; ++b)
-            tc::tma_load_2d(sY + (size_t)s * 128 * kFuNC + b * 128 * kFuBox, &mapY, (int32_t)row0,
-                            col0 + b * kFuBox, &ld_full[s]);
         }
         pend_ld = g + 1;
         __syncwarp();
@@ -775,20 +778,18 @@ __global__ void __launch_bounds__(kFuThreads, RK == 32 ? 2 : 1) update_coupled_t
       for (int ch = 0; ch < nch; ++ch, ++g) {
         const int col0 = ch * kFuNC;
         const int nc = (anc - col0) < kFuNC ? (anc - col0) : kFuNC;
-        const int s = g % S::NS, a = g & 1;
-        bool w = wait_or_abort(&acc_full[a], (g >> 1) & 1, abort_flag);
-        w = w && wait_or_abort(&ld_full[s], (g / S::NS) & 1, abort_flag);
-        if (!(ok = named_bar_and(1, 128, w))) break;  // uniform over the epilogue warps
+        const int a = g & 1, ob = (int)(g % kFuOut);
+        const bool w = wait_or_abort(&acc_full[a], (g >> 1) & 1, abort_flag);
+        // uniform over the epilogue warps; also orders the storer's read-wait
+        // for this output tile before the writes below
+        if (!(ok = named_bar_and(1, 128, w))) break;
         tc::tc_fence_after();
-        __nv_bfloat16* ys = sY + (size_t)s * 128 * kFuNC;
+        __nv_bfloat16* ys = sY + (size_t)ob * 128 * kFuNC;
         for (int cb = 0; cb < nc; cb += 32) {
           float v[32];
           tc::tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + a * kFuNC + cb, v);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            __nv_bfloat16* p = ys + (cb + j) * 128 + row;
-            *p = __float2bfloat16_rn(__bfloat162float(*p) - v[j]);
-          }
+          for (int j = 0; j < 32; ++j) ys[(cb + j) * 128 + row] = __float2bfloat16_rn(-v[j]);
         }
         tc::tc_fence_before();
         tc::mbar_arrive(&acc_empty[a]);
@@ -796,11 +797,9 @@ __global__ void __launch_bounds__(kFuThreads, RK == 32 ? 2 : 1) update_coupled_t
         named_bar_sync(1, 128);
         if (storer) {
           for (int b = 0; b < nc / kFuBox; ++b)
-            tma_store_2d(&mapY, ys + b * 128 * kFuBox, (int32_t)row0, col0 + b * kFuBox);
+            tma_reduce_add_2d(&mapY, ys + b * 128 * kFuBox, (int32_t)row0, col0 + b * kFuBox);
           bulk_commit();
-          // hand the stage back as soon as the store has read it
-          bulk_wait_read0();
-          tc::mbar_arrive(&y_empty[s]);
+          bulk_wait_read1();  // the previous chunk's reduction has read the other output tile
         }
       }
     }
@@ -954,7 +953,6 @@ bool make_map_u64(CUtensorMap* map, const double* base, int64_t rows, int64_t co
 __device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 
 }  // namespace
 
