@@ -157,6 +157,10 @@ cudaError_t launch_leaf_lu(const Factor& F, const double* D, cudaStream_t s) {
 // SMEM: the CTA first copies the leaf's LU factor and permutation to shared
 // memory and its warps then sweep all column groups of the leaf (one LU load
 // per leaf instead of one per column group).
+// The divisions by the pivots u_kk are multiplications by their reciprocals,
+// formed once per CTA (within an ulp of the quotient): a double division is a
+// multi-instruction sequence on the FP64 pipe, and one per column and pivot
+// cost several times the substitutions' own FMAs.
 template <typename TL, typename TIN, typename TOUT, int RPL, int CPW, bool SMEM>
 __global__ void __launch_bounds__(256) leaf_solve_kernel(int m, const TL* __restrict__ LU,
                                                          const int* __restrict__ perm, const TIN* in,
@@ -168,6 +172,9 @@ __global__ void __launch_bounds__(256) leaf_solve_kernel(int m, const TL* __rest
   const int nwarps = blockDim.x >> 5;
   const TL* A = LU + (size_t)b * m * m;
   const int* pb = perm + (size_t)b * m;
+  __shared__ TL s_rcp[256];  // 1 / u_kk (m <= 256)
+  for (int e = threadIdx.x; e < m; e += blockDim.x) s_rcp[e] = TL(1) / A[(size_t)e * m + e];
+  __syncthreads();
   if (SMEM) {
     TL* sA = reinterpret_cast<TL*>(smem_raw);
     int* sp = reinterpret_cast<int*>(sA + (size_t)m * m);
@@ -219,11 +226,11 @@ __global__ void __launch_bounds__(256) leaf_solve_kernel(int m, const TL* __rest
       for (int kk = 31; kk >= 0; --kk) {
         const int k = kb * 32 + kk;
         if (k >= m) continue;
-        const TL ukk = A[(size_t)k * m + k];
+        const TL rk = s_rcp[k];
         TL xk[CPW];
 #pragma unroll
         for (int c = 0; c < CPW; ++c) {
-          const TL v = __shfl_sync(0xffffffffu, x[c][kb], kk) / ukk;
+          const TL v = __shfl_sync(0xffffffffu, x[c][kb], kk) * rk;
           if (lane == kk) x[c][kb] = v;
           xk[c] = v;
         }
@@ -255,11 +262,11 @@ __global__ void __launch_bounds__(256) leaf_solve_kernel(int m, const TL* __rest
       for (int kk = 0; kk < 32; ++kk) {
         const int k = kb * 32 + kk;
         if (k >= m) break;
-        const TL ukk = A[(size_t)k * m + k];
+        const TL rk = s_rcp[k];
         TL xk[CPW];
 #pragma unroll
         for (int c = 0; c < CPW; ++c) {
-          const TL v = __shfl_sync(0xffffffffu, x[c][kb], kk) / ukk;
+          const TL v = __shfl_sync(0xffffffffu, x[c][kb], kk) * rk;
           if (lane == kk) x[c][kb] = v;
           xk[c] = v;
         }

@@ -358,6 +358,62 @@ __global__ void __launch_bounds__(128) leaf_apply_narrow_kernel(int m, const flo
     if (c < ncols) out[(int64_t)c * ldout + row0 + oi] = conv<TOUT>(acc[c]);
 }
 
+// m = 128, D^{-1} (not transposed), at most 8 columns: warp w takes the K
+// range 32w .. 32w+31 and lane l rows 4l .. 4l+3, one 16-byte load of T per
+// column k (each warp reads 512 contiguous bytes per load); the four warps'
+// partial sums are added in shared memory.
+template <typename TIN, typename TOUT, int KC>
+__global__ void __launch_bounds__(128) leaf_apply_n128_kernel(const float* __restrict__ Dinv,
+                                                              const int* __restrict__ perm, int64_t N, const TIN* in,
+                                                              int64_t ldin, TOUT* out, int64_t ldout, int ncols) {
+  constexpr int m = 128;
+  __shared__ float sx[m * KC];
+  __shared__ float4 sp[4][32][KC];
+  const int b = blockIdx.x;
+  const float4* A4 = reinterpret_cast<const float4*>(Dinv + (size_t)b * m * m);
+  const int64_t row0 = (int64_t)b * m;
+  const int* pg = perm + (size_t)b * m;       // inputs gathered by p
+  const int* ps = perm + (size_t)N + (size_t)b * m;  // outputs scattered by step
+  for (int e = threadIdx.x; e < m * KC; e += blockDim.x) {
+    const int k = e % m, c = e / m;
+    sx[k * KC + c] = c < ncols ? conv<float>(in[(int64_t)c * ldin + row0 + pg[k]]) : 0.f;
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float4 acc[KC];
+#pragma unroll
+  for (int c = 0; c < KC; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 8
+  for (int kk = 0; kk < 32; ++kk) {
+    const int k = w * 32 + kk;
+    const float4 a = __ldg(A4 + k * 32 + lane);  // T(4 lane .. 4 lane + 3, k)
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      const float x = sx[k * KC + c];
+      acc[c].x += a.x * x;
+      acc[c].y += a.y * x;
+      acc[c].z += a.z * x;
+      acc[c].w += a.w * x;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < KC; ++c) sp[w][lane][c] = acc[c];
+  __syncthreads();
+  const int i = threadIdx.x, ln = i >> 2, cp = i & 3;
+  const int oi = ps[i];
+#pragma unroll
+  for (int c = 0; c < KC; ++c) {
+    if (c >= ncols) break;
+    float v = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 t = sp[q][ln][c];
+      v += cp == 0 ? t.x : cp == 1 ? t.y : cp == 2 ? t.z : t.w;
+    }
+    out[(int64_t)c * ldout + row0 + oi] = conv<TOUT>(v);
+  }
+}
+
 template <typename TIN, typename TOUT>
 cudaError_t launch_leaf_apply_inv(const Factor& F, const TIN* in, int64_t ldin, TOUT* out, int64_t ldout, int ncols,
                                   int trans, cudaStream_t s) {
@@ -368,7 +424,16 @@ cudaError_t launch_leaf_apply_inv(const Factor& F, const TIN* in, int64_t ldin, 
   // the scaled Gauss-Jordan tableau T with D^{-1}(step(r), p_c) = T(r, c); p and
   // step in F.perm (see the leaf inverse kernels)
   note_work((sizeof(TIN) + sizeof(TOUT)) * Nd * ncols + 4.0 * Nd * m, 2.0 * m * Nd * ncols);
-  if (ncols <= 8) {
+  if (ncols <= 8 && m == 128 && !trans) {
+    if (ncols == 1)
+      { leaf_apply_n128_kernel<TIN, TOUT, 1><<<nleaf, 128, 0, s>>>(Dinv, F.perm, F.d.N, in, ldin, out, ldout, ncols); note_launches(1); }
+    else if (ncols <= 2)
+      { leaf_apply_n128_kernel<TIN, TOUT, 2><<<nleaf, 128, 0, s>>>(Dinv, F.perm, F.d.N, in, ldin, out, ldout, ncols); note_launches(1); }
+    else if (ncols <= 4)
+      { leaf_apply_n128_kernel<TIN, TOUT, 4><<<nleaf, 128, 0, s>>>(Dinv, F.perm, F.d.N, in, ldin, out, ldout, ncols); note_launches(1); }
+    else
+      { leaf_apply_n128_kernel<TIN, TOUT, 8><<<nleaf, 128, 0, s>>>(Dinv, F.perm, F.d.N, in, ldin, out, ldout, ncols); note_launches(1); }
+  } else if (ncols <= 8) {
     const int th = ((m + 31) / 32) * 32;
     if (ncols == 1)
       { leaf_apply_narrow_kernel<TIN, TOUT, 1><<<nleaf, th, 0, s>>>(m, Dinv, F.perm, F.d.N, in, ldin, out, ldout, ncols, trans); note_launches(1); }

@@ -310,7 +310,9 @@ cudaError_t project_tc_go(const T* Vp, int64_t ldv, const T* Y, int64_t N, int r
   constexpr bool f32 = sizeof(T) == 4;
   constexpr int kRows = 128 / (int)sizeof(T);
   CUtensorMap mY, mV;
-  if (!make_map(&mY, Y, N, rL, N, kRows, kBM, f32)) return cudaErrorInvalidValue;
+  // only the r c columns the level projects: the column tiles past them are
+  // out of bounds for the copy engine (filled with zeros, not read)
+  if (!make_map(&mY, Y, N, rc, N, kRows, kBM, f32)) return cudaErrorInvalidValue;
   if (!make_map(&mV, Vp, N, rL, ldv, kRows, RN, f32)) return cudaErrorInvalidValue;
   const int64_t ch = chunk_rows(N, c);
   const int64_t nch = num_chunks(N, c);
