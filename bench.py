@@ -93,11 +93,11 @@ def fp32_peak_tflops(sm_mhz):
 # captured again.
 TRAFFIC_RATIO = {
     "matvec": 812.6 / 808.5,      # mv1_leaf_project_g8 + mv1_run_sum + mv1_node_sum + mv1_leaf_apply, one matvec
-    "project_tc": 656.4 / 615.5,  # project_tc_kernel, the ten levels of one factorization
     "leaf_lu": 259.6 / 268.4,     # leaf_inv_tc_kernel
+    "project_tc": 550.3 / 615.5,  # project_tc_kernel, the ten levels of one factorization
 }
-# (update_coupled_tc_kernel is left out: at N = 2^17 most of Y stays in L2
-# between its load and store, so the small case's ratio (0.60) does not scale.)
+# (update_coupled_tc_kernel is left out: at N = 2^17 most of Y stays in L2,
+# so the small case's ratio does not scale.)
 
 
 def class_bound(cls, prec, m=128):
