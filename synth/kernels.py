@@ -269,31 +269,24 @@ def _assemble(shape: HodlrShape, leaf_fn, entries, seed, device, symmetric, stat
     return D, Ut.T, Vt.T
 
 
-def bie_hodlr(shape: HodlrShape, device="cpu", seed=2, stats=None):
-    """HODLR operator of the star-curve Laplace BIE (see module doc)."""
-    shape.validate()
-    N, m = shape.N, shape.m
-    x, nrm, w, kappa = star_curve(N, device=device, dtype=torch.float64)
+def bie_offdiag_entries(N: int, device="cpu"):
+    """Evaluator entries(rows, cols) -> FP32 (batch, a, b) of the BIE's
+    off-diagonal entries A(rows, cols), for index tensors rows (batch, a) and
+    cols (batch, b) that are contiguous, disjoint index ranges per batch entry
+    (the sibling blocks the compression evaluates tile by tile).
+
+    For nearby points n(y).(x - y) is second order in the distance while
+    x - y is first order. Entries whose curve-order distance is below
+    `band` = max(256, N / 128) come from the FP64 geometry; the others from
+    x - y formed in FP64 and the rest in FP32 (error relative to the block's
+    largest entry about 1.2e-7 / (kappa |x - y|), <= 1.1e-6 beyond the band at
+    N = 2^16; from FP32 coordinates it would be ~1.6e-7 / (kappa |x - y|^2),
+    the whole entry for neighbours)."""
+    x, nrm, w, _ = star_curve(N, device=device, dtype=torch.float64)
     n32, w32 = nrm.float(), w.float()
     band = max(256, N // 128)
-    diag = (-0.5 - w * kappa / (4 * math.pi))
-
-    def leaf_fn(b0, b1):
-        idx = torch.arange(b0 * m, b1 * m, device=device).view(b1 - b0, m)
-        blk = bie_block(x, nrm, w, idx, idx)
-        ii = torch.arange(m, device=device)
-        blk[:, ii, ii] = diag[idx]
-        return blk
 
     def entries(rows, cols):
-        # For nearby points n(y).(x - y) is second order in the distance while
-        # x - y is first order. Entries whose curve-order distance is below
-        # `band` come from the FP64 geometry; the others from x - y formed in
-        # FP64 and the rest in FP32 (error relative to the block's largest
-        # entry about 1.2e-7 / (kappa |x - y|), <= 1.1e-6 beyond the band at
-        # N = 2^16; from FP32 coordinates it would be ~1.6e-7 / (kappa |x - y|^2),
-        # the whole entry for neighbours). rows and cols are contiguous,
-        # disjoint index ranges per batch entry.
         b = cols.shape[-1]
         if 2 * band >= b:
             return bie_block(x, nrm, w, rows, cols).float()
@@ -308,6 +301,24 @@ def bie_hodlr(shape: HodlrShape, device="cpu", seed=2, stats=None):
             out[e, :, j] = bie_block(x, nrm, w, rows[e], cols[e, j][:, None])[..., 0].float()
         return out
 
+    return entries
+
+
+def bie_hodlr(shape: HodlrShape, device="cpu", seed=2, stats=None):
+    """HODLR operator of the star-curve Laplace BIE (see module doc)."""
+    shape.validate()
+    N, m = shape.N, shape.m
+    x, nrm, w, kappa = star_curve(N, device=device, dtype=torch.float64)
+    diag = (-0.5 - w * kappa / (4 * math.pi))
+
+    def leaf_fn(b0, b1):
+        idx = torch.arange(b0 * m, b1 * m, device=device).view(b1 - b0, m)
+        blk = bie_block(x, nrm, w, idx, idx)
+        ii = torch.arange(m, device=device)
+        blk[:, ii, ii] = diag[idx]
+        return blk
+
+    entries = bie_offdiag_entries(N, device)
     return _assemble(shape, leaf_fn, entries, seed, device, symmetric=False, stats=stats)
 
 

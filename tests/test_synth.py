@@ -75,3 +75,24 @@ def test_kernel_hodlr_symmetric(dim, kind, scale, nugget):
         np.testing.assert_allclose(Ah[sl, sl], K.numpy()[sl, sl], rtol=0, atol=1e-12)
     # fixed rank 32 on 512-point blocks: a few percent in 3D, far less in 2D
     assert np.linalg.norm(Ah - K.numpy()) / np.linalg.norm(K.numpy()) < (5e-3 if dim == 2 else 5e-2)
+
+
+@pytest.mark.parametrize("N", [1 << 14, 1 << 16])
+def test_bie_offdiag_entries_match_fp64(N):
+    """The generator's mixed-precision entries (FP64 within the band, FP64
+    differences elsewhere, FP32 rest) against the FP64 formula on sibling
+    blocks of several levels, both ends of each block (the periodic wrap
+    included): within 2e-6 of the block's largest entry (FP32 output rounding
+    alone is 6e-8 of an entry; coordinates in FP32 would give 1e-2 and more)."""
+    from synth.kernels import bie_block, bie_offdiag_entries
+    x, nrm, w, _ = star_curve(N)
+    ent = bie_offdiag_entries(N)
+    for c in (1, 2, 4, 6):
+        n = N >> c
+        for blk in (0, 1, (1 << c) - 1):
+            cols = torch.arange((blk ^ 1) * n, ((blk ^ 1) + 1) * n)
+            for lo in (blk * n, blk * n + n - min(n, 256)):
+                rows = torch.arange(lo, lo + min(n, 256))
+                got = ent(rows[None, :], cols[None, :])[0].double()
+                ref = bie_block(x, nrm, w, rows[None, :], cols[None, :])[0]
+                assert ((got - ref).abs().max() / ref.abs().max()).item() <= 2e-6, (N, c, blk, lo)
