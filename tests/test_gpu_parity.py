@@ -7,7 +7,7 @@ calls getrf/getrs), so their solutions differ by about cond(A) * u with
 u = 2^-53; the synthetic operators here have cond(A) < 1e2, hence the bound
 1e-11 on the relative solution difference (1e3 margin) and on the log-det
 difference relative to max(1, |log det|). Refined mixed-precision solves must
-reach the spec residual 1e-10, measured with the oracle's own matvec.
+reach the target residual 1e-10, measured with the oracle's own matvec.
 """
 import numpy as np
 import pytest
@@ -136,7 +136,7 @@ def test_tf32_factor_projects_on_tensor_cores(cuda_lib, N, L, r):
     every level's projection on the tensor cores and agrees with the FP32
     factor to TF32 rounding (operands with a 10-bit significand: products
     within 2^-11 relative, FP32 accumulation): solutions within 1e-2 of each
-    other and of the oracle's exact solve, refined to the spec residual."""
+    other and of the oracle's exact solve, refined to the target residual (1e-10)."""
     hb = cuda_lib
     (Dm, Um, Vm, Bm), (D, U, V, B) = make_case(N, L, r, seed=91 + r, k=2)
     F32 = hb.hodlr_factor(D, U, V, L, r, "fp32")
@@ -338,7 +338,7 @@ def test_gmres_lockstep_columns_reach_1e10(cuda_lib, prec, k, restart):
     """FGMRES on k right-hand sides in lockstep (one k-column preconditioner
     solve and one k-column FP64 matvec per inner iteration); restart 2 forces
     several cycles, each continuing from r - (A Z) y. Every column reaches
-    the spec residual measured by the oracle's matvec, and agrees with
+    the target residual (1e-10) measured by the oracle's matvec, and agrees with
     the oracle's exact solve to cond(A) * 1e-10."""
     hb = cuda_lib
     N, L, r = 4096, 5, 16
