@@ -73,7 +73,9 @@ typedef enum {
  *         projections V^T Y run on the tensor cores with TF32 operands (the
  *         FP32 values' top 10 significand bits) and FP32 accumulation.
  *   BF16: as FP32, but Y_big and V_big are stored in bfloat16 and the panel
- *         products read them as such (FP32 accumulate).
+ *         products read them as such (FP32 accumulate); with r = 32 or 64 and
+ *         node sizes that are multiples of 128 an ancestor update is added to
+ *         the stored Y_big in bfloat16 (the update rounded, then the sum).
  * In every precision the 2r x 2r coupling matrices are formed, factored and
  * solved in FP64, and log-determinants are accumulated in FP64. A low-precision
  * factor is meant as the preconditioner of hodlr_solve_refined / hodlr_gmres. */
